@@ -1,0 +1,437 @@
+/*
+ * dgs_oracle.c -- plain single-threaded CPU oracle for Deep Greedy Switching.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the CUDA library.  Written for
+ * readability against the paper, not for speed: no blocking, no fusion, no
+ * incremental tricks.  Every function names the part of the paper it follows.
+ *
+ * Storage: a[i*n + j] = benefit of agent i doing job j (int32, |a| < 2^29).
+ * sigma[j] = agent holding job j, tau[i] = job held by agent i (Section 3.3).
+ */
+#include "dgs_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_ERR_INTERNAL 99
+#define A(i, j) ((int64_t)a[(int64_t)(i) * n + (j)])
+
+/* Section 3: f(sigma) = sum over agents of the benefit of their job. */
+int64_t oracle_objective(const int32_t* a, int32_t n, const int32_t* tau)
+{
+    int64_t f = 0;
+    for (int32_t i = 0; i < n; ++i) f += A(i, tau[i]);
+    return f;
+}
+
+int oracle_range_ok(const int32_t* a, int32_t n)
+{
+    const int64_t lim = (int64_t)1 << 29;
+    for (int64_t e = 0; e < (int64_t)n * n; ++e)
+        if (a[e] >= lim || a[e] <= -lim) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.1, reading R1: global greedy.  Visit all (i, j) pairs by
+ * decreasing benefit (ties: lower agent first, then lower job) and take a
+ * pair whenever both its agent and its job are still free.  The order is
+ * encoded in one unsigned 64-bit sort key per pair:
+ *   bits 34..63: (2^30 - 1) - (a + 2^29)   (larger benefit -> smaller key)
+ *   bits 17..33: agent i,  bits 0..16: job j          (n <= 2^17)       */
+static int cmp_u64(const void* x, const void* y)
+{
+    uint64_t u = *(const uint64_t*)x, v = *(const uint64_t*)y;
+    return (u > v) - (u < v);
+}
+
+void oracle_greedy_init(const int32_t* a, int32_t n, int32_t* tau_out)
+{
+    int64_t m = (int64_t)n * n;
+    uint64_t* keys = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+    uint8_t* agent_used = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* job_used = (uint8_t*)calloc((size_t)n, 1);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < n; ++j) {
+            uint64_t rank = (uint64_t)(((int64_t)1 << 30) - 1 - (A(i, j) + ((int64_t)1 << 29)));
+            keys[(int64_t)i * n + j] = (rank << 34) | ((uint64_t)i << 17) | (uint64_t)j;
+        }
+    qsort(keys, (size_t)m, sizeof(uint64_t), cmp_u64);
+    int32_t taken = 0;
+    for (int64_t e = 0; e < m && taken < n; ++e) {
+        int32_t i = (int32_t)((keys[e] >> 17) & 0x1FFFF);
+        int32_t j = (int32_t)(keys[e] & 0x1FFFF);
+        if (!agent_used[i] && !job_used[j]) {
+            agent_used[i] = 1;
+            job_used[j] = 1;
+            tau_out[i] = j;
+            ++taken;
+        }
+    }
+    free(keys);
+    free(agent_used);
+    free(job_used);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 2 (ADE) for agent i.  j = tau(i).  For every other job j'
+ * (ascending, reading R2) with holder i' = sigma(j'), the candidate
+ * assignment gives j' to i and j to i'; it is kept when its objective is
+ * strictly larger than the best kept so far (initially sigma itself).  The
+ * objective difference of that candidate against sigma is the four-term
+ * expression below (only agents i and i' change jobs). */
+void oracle_ade(const int32_t* a, int32_t n, const int32_t* sigma,
+                const int32_t* tau, int32_t i, int32_t* gain, int32_t* job)
+{
+    int32_t j = tau[i];
+    int64_t best = 0;
+    int32_t best_job = -1;
+    for (int32_t jp = 0; jp < n; ++jp) {
+        if (jp == j) continue;
+        int32_t ip = sigma[jp];
+        int64_t diff = A(i, jp) + A(ip, j) - A(i, j) - A(ip, jp);
+        if (diff > best) {
+            best = diff;
+            best_job = jp;
+        }
+    }
+    *gain = (int32_t)best;
+    *job = best_job;
+}
+
+/* JDE for job j (Section 3.2): job j, held by i = sigma(j), tries every
+ * other agent i' (ascending, reading R2); the candidate gives j to i' and
+ * i's partner job j' = tau(i') to i. */
+void oracle_jde(const int32_t* a, int32_t n, const int32_t* sigma,
+                const int32_t* tau, int32_t j, int32_t* gain, int32_t* agent)
+{
+    int32_t i = sigma[j];
+    int64_t best = 0;
+    int32_t best_agent = -1;
+    for (int32_t ip = 0; ip < n; ++ip) {
+        if (ip == i) continue;
+        int32_t jp = tau[ip];
+        int64_t diff = A(ip, j) + A(i, jp) - A(i, j) - A(ip, jp);
+        if (diff > best) {
+            best = diff;
+            best_agent = ip;
+        }
+    }
+    *gain = (int32_t)best;
+    *agent = best_agent;
+}
+
+void oracle_evaluate_all(const int32_t* a, int32_t n, const int32_t* tau,
+                         int32_t* agent_gain, int32_t* agent_job,
+                         int32_t* job_gain, int32_t* job_agent)
+{
+    int32_t* sigma = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    for (int32_t i = 0; i < n; ++i) sigma[tau[i]] = i;
+    for (int32_t i = 0; i < n; ++i) oracle_ade(a, n, sigma, tau, i, &agent_gain[i], &agent_job[i]);
+    for (int32_t j = 0; j < n; ++j) oracle_jde(a, n, sigma, tau, j, &job_gain[j], &job_agent[j]);
+    free(sigma);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 4 (CC), reading R3.  CR collects claimed agents.  Agent slots
+ * are visited first (ascending i), then job slots (ascending j); a slot
+ * with a candidate claims the two agents its exchange touches -- for agent
+ * slot i: i and i' = sigma(j_i); for job slot j: sigma(j) and i_j -- unless
+ * one of them is already claimed, in which case the slot goes into C.
+ * Partners are looked up in the current sigma. */
+void oracle_check_conflicts(int32_t n, const int32_t* sigma,
+                            const int32_t* agent_gain, const int32_t* agent_job,
+                            const int32_t* job_gain, const int32_t* job_agent,
+                            uint8_t* in_ca, uint8_t* in_cj)
+{
+    uint8_t* cr = (uint8_t*)calloc((size_t)n, 1);
+    for (int32_t i = 0; i < n; ++i) {
+        in_ca[i] = 0;
+        if (agent_gain[i] <= 0) continue; /* NA_i = 0 */
+        int32_t ip = sigma[agent_job[i]];
+        if (cr[i] || cr[ip]) {
+            in_ca[i] = 1;
+        } else {
+            cr[i] = 1;
+            cr[ip] = 1;
+        }
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        in_cj[j] = 0;
+        if (job_gain[j] <= 0) continue; /* NJ_j = 0 */
+        int32_t owner = sigma[j];
+        int32_t partner = job_agent[j];
+        if (cr[owner] || cr[partner]) {
+            in_cj[j] = 1;
+        } else {
+            cr[owner] = 1;
+            cr[partner] = 1;
+        }
+    }
+    free(cr);
+}
+
+/* Literal Algorithm 4: C is a set of AGENTS; a conflicted job slot adds its
+ * owner sigma(j).  Kept only to demonstrate that this reading never lets the
+ * switching loop finish (see the tests). */
+static void cc_literal_agents(int32_t n, const int32_t* sigma,
+                              const int32_t* agent_gain, const int32_t* agent_job,
+                              const int32_t* job_gain, const int32_t* job_agent,
+                              uint8_t* in_c_agent)
+{
+    uint8_t* cr = (uint8_t*)calloc((size_t)n, 1);
+    memset(in_c_agent, 0, (size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        if (agent_gain[i] <= 0) continue;
+        int32_t ip = sigma[agent_job[i]];
+        if (cr[i] || cr[ip]) in_c_agent[i] = 1;
+        else { cr[i] = 1; cr[ip] = 1; }
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        if (job_gain[j] <= 0) continue;
+        int32_t owner = sigma[j];
+        if (cr[owner] || cr[job_agent[j]]) in_c_agent[owner] = 1;
+        else { cr[owner] = 1; cr[job_agent[j]] = 1; }
+    }
+    free(cr);
+}
+
+/* Objective change of exchanging the jobs of agents u and v under tau. */
+static int64_t exchange_gain(const int32_t* a, int32_t n, const int32_t* tau,
+                             int32_t u, int32_t v)
+{
+    return A(u, tau[v]) + A(v, tau[u]) - A(u, tau[u]) - A(v, tau[v]);
+}
+
+static void do_exchange(int32_t* sigma, int32_t* tau, int32_t u, int32_t v)
+{
+    int32_t ju = tau[u], jv = tau[v];
+    tau[u] = jv;
+    tau[v] = ju;
+    sigma[jv] = u;
+    sigma[ju] = v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 (parallel DGS). */
+int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
+                        const int32_t* init_tau, int32_t max_sweeps,
+                        int32_t cc_rule, int32_t* tau_out, int64_t* f_out,
+                        oracle_stats* stats, int32_t trace_cap,
+                        int32_t* trace_accepted, int32_t* trace_applied,
+                        int64_t* trace_objective)
+{
+    if (n <= 0 || a == NULL || tau_out == NULL || f_out == NULL) return ORACLE_ERR_INVALID;
+    if (n > (1 << 17)) return ORACLE_ERR_INVALID;
+    if (!oracle_range_ok(a, n)) return ORACLE_ERR_RANGE;
+
+    size_t nb = (size_t)n * sizeof(int32_t);
+    int32_t* sigma = (int32_t*)malloc(nb);
+    int32_t* tau = (int32_t*)malloc(nb);
+    int32_t* tau0 = (int32_t*)malloc(nb);
+    int32_t* ag_gain = (int32_t*)malloc(nb);
+    int32_t* ag_job = (int32_t*)malloc(nb);
+    int32_t* jb_gain = (int32_t*)malloc(nb);
+    int32_t* jb_agent = (int32_t*)malloc(nb);
+    uint8_t* in_ca = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* in_cj = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* in_c_agent = (uint8_t*)calloc((size_t)n, 1);
+    oracle_stats st = {0, 0, 0, 0};
+    int status = ORACLE_OK;
+
+    /* Section 3.1: initial solution. */
+    if (init_mode == ORACLE_INIT_GREEDY) {
+        oracle_greedy_init(a, n, tau);
+    } else if (init_mode == ORACLE_INIT_IDENTITY) {
+        for (int32_t i = 0; i < n; ++i) tau[i] = i;
+    } else if (init_mode == ORACLE_INIT_USER && init_tau != NULL) {
+        memset(in_ca, 0, (size_t)n);
+        for (int32_t i = 0; i < n; ++i) {
+            if (init_tau[i] < 0 || init_tau[i] >= n || in_ca[init_tau[i]]) {
+                status = ORACLE_ERR_INVALID;
+                goto out;
+            }
+            in_ca[init_tau[i]] = 1;
+            tau[i] = init_tau[i];
+        }
+        memset(in_ca, 0, (size_t)n);
+    } else {
+        status = ORACLE_ERR_INVALID;
+        goto out;
+    }
+    for (int32_t i = 0; i < n; ++i) sigma[tau[i]] = i;
+    int64_t f = oracle_objective(a, n, tau);
+
+    for (;;) { /* outer repeat ... until f(sigma_start) = f(sigma') (R5) */
+        st.passes++;
+        int64_t f_start = f;
+        memset(in_ca, 0, (size_t)n);
+        memset(in_cj, 0, (size_t)n);
+        memset(in_c_agent, 0, (size_t)n);
+
+        /* Difference evaluation phase: every agent and every job. */
+        for (int32_t i = 0; i < n; ++i) oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]);
+        for (int32_t j = 0; j < n; ++j) oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]);
+        st.evaluations += 2 * (int64_t)n;
+
+        for (;;) { /* switching phase: while some delta > 0 */
+            int any = 0;
+            for (int32_t t = 0; t < n && !any; ++t) any = ag_gain[t] > 0 || jb_gain[t] > 0;
+            if (!any) break;
+            if (max_sweeps > 0 && st.sweeps >= max_sweeps) {
+                status = ORACLE_TIMEOUT;
+                goto finish;
+            }
+
+            /* CC, then delta_t = candidate gain of every slot not in C. */
+            if (cc_rule == ORACLE_CC_SLOTS) {
+                oracle_check_conflicts(n, sigma, ag_gain, ag_job, jb_gain, jb_agent, in_ca, in_cj);
+            } else {
+                cc_literal_agents(n, sigma, ag_gain, ag_job, jb_gain, jb_agent, in_c_agent);
+                for (int32_t i = 0; i < n; ++i) in_ca[i] = in_c_agent[i];
+                for (int32_t j = 0; j < n; ++j) in_cj[j] = in_c_agent[sigma[j]];
+            }
+
+            /* Parallel switch: every slot with delta_t > 0 performs its
+             * exchange if that raises f under the current sigma.  The
+             * accepted slots touch disjoint agents, so applying them in slot
+             * order equals applying them all against the sigma of the CC;
+             * the snapshot comparison checks exactly that. */
+            memcpy(tau0, tau, nb);
+            int32_t accepted = 0, applied = 0;
+            for (int32_t t = 0; t < 2 * n; ++t) {
+                int32_t u, v;
+                if (t < n) {
+                    if (in_ca[t] || ag_gain[t] <= 0) continue;
+                    u = t;
+                    v = sigma[ag_job[t]];
+                } else {
+                    int32_t j = t - n;
+                    if (in_cj[j] || jb_gain[j] <= 0) continue;
+                    u = jb_agent[j];
+                    v = sigma[j];
+                }
+                accepted++;
+                int64_t g = exchange_gain(a, n, tau, u, v);
+                if (g != exchange_gain(a, n, tau0, u, v)) {
+                    status = ORACLE_ERR_INTERNAL;
+                    goto finish;
+                }
+                if (g > 0) {
+                    do_exchange(sigma, tau, u, v);
+                    f += g;
+                    applied++;
+                }
+            }
+            st.swaps_applied += applied;
+
+            /* Re-evaluation of the agents and jobs not in C (reading R4). */
+            for (int32_t i = 0; i < n; ++i)
+                if (!in_ca[i]) { oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]); st.evaluations++; }
+            for (int32_t j = 0; j < n; ++j)
+                if (!in_cj[j]) { oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]); st.evaluations++; }
+
+            if (st.sweeps < trace_cap) {
+                if (trace_accepted) trace_accepted[st.sweeps] = accepted;
+                if (trace_applied) trace_applied[st.sweeps] = applied;
+                if (trace_objective) trace_objective[st.sweeps] = f;
+            }
+            st.sweeps++;
+        }
+        if (f == f_start) break;
+    }
+
+finish:
+    memcpy(tau_out, tau, nb);
+    *f_out = oracle_objective(a, n, tau);
+    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;
+out:
+    if (stats) *stats = st;
+    free(sigma); free(tau); free(tau0);
+    free(ag_gain); free(ag_job); free(jb_gain); free(jb_agent);
+    free(in_ca); free(in_cj); free(in_c_agent);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact optimum, Hungarian method (Kuhn 1955) in its shortest augmenting
+ * path form: rows are inserted one at a time; a Dijkstra-like scan over
+ * reduced costs c[i][j] - u[i] - v[j] (c = -a, minimised) finds the
+ * cheapest augmenting path, the potentials are shifted by the scan's
+ * minimum at each step and the path is flipped.  1-based internally;
+ * column 0 is the virtual root. */
+int64_t oracle_hungarian(const int32_t* a, int32_t n, int32_t* tau_out)
+{
+    const int64_t INF = (int64_t)1 << 62;
+    size_t m = (size_t)n + 1;
+    int64_t* u = (int64_t*)calloc(m, sizeof(int64_t));
+    int64_t* v = (int64_t*)calloc(m, sizeof(int64_t));
+    int64_t* min_slack = (int64_t*)malloc(m * sizeof(int64_t));
+    int32_t* row_of_col = (int32_t*)calloc(m, sizeof(int32_t));
+    int32_t* prev_col = (int32_t*)calloc(m, sizeof(int32_t));
+    uint8_t* visited = (uint8_t*)malloc(m);
+
+    for (int32_t r = 1; r <= n; ++r) {
+        row_of_col[0] = r;
+        int32_t col = 0;
+        for (size_t c = 0; c < m; ++c) { min_slack[c] = INF; visited[c] = 0; }
+        do {
+            visited[col] = 1;
+            int32_t row = row_of_col[col];
+            int64_t step = INF;
+            int32_t next_col = 0;
+            for (int32_t c = 1; c <= n; ++c) {
+                if (visited[c]) continue;
+                int64_t reduced = -A(row - 1, c - 1) - u[row] - v[c];
+                if (reduced < min_slack[c]) { min_slack[c] = reduced; prev_col[c] = col; }
+                if (min_slack[c] < step) { step = min_slack[c]; next_col = c; }
+            }
+            for (int32_t c = 0; c <= n; ++c) {
+                if (visited[c]) { u[row_of_col[c]] += step; v[c] -= step; }
+                else min_slack[c] -= step;
+            }
+            col = next_col;
+        } while (row_of_col[col] != 0);
+        do { /* flip the augmenting path back to the root */
+            int32_t pc = prev_col[col];
+            row_of_col[col] = row_of_col[pc];
+            col = pc;
+        } while (col != 0);
+    }
+    for (int32_t c = 1; c <= n; ++c) tau_out[row_of_col[c] - 1] = c - 1;
+    free(u); free(v); free(min_slack); free(row_of_col); free(prev_col); free(visited);
+    return oracle_objective(a, n, tau_out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact optimum by enumeration of all permutations in lexicographic order
+ * (first optimal permutation kept). */
+static void brute_rec(const int32_t* a, int32_t n, int32_t i, int64_t acc,
+                      int32_t* cur, uint8_t* used, int64_t* best, int32_t* best_tau)
+{
+    if (i == n) {
+        if (acc > *best) {
+            *best = acc;
+            memcpy(best_tau, cur, (size_t)n * sizeof(int32_t));
+        }
+        return;
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        if (used[j]) continue;
+        used[j] = 1;
+        cur[i] = j;
+        brute_rec(a, n, i + 1, acc + A(i, j), cur, used, best, best_tau);
+        used[j] = 0;
+    }
+}
+
+int64_t oracle_brute_force(const int32_t* a, int32_t n, int32_t* tau_out)
+{
+    int32_t cur[16];
+    uint8_t used[16] = {0};
+    int64_t best = INT64_MIN;
+    if (n > 10) return INT64_MIN;
+    brute_rec(a, n, 0, 0, cur, used, &best, tau_out);
+    return best;
+}

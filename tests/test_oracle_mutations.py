@@ -1,0 +1,51 @@
+"""Each plausible mistake planted in a COPY of the oracle's C source (a
+dropped term, a wrong index, a flipped comparison, a transposed lookup) must
+make at least one oracle pin fail (or stop terminating: several mistakes
+turn the switching loop into an endless one).  The copy is compiled to a temporary
+library and the pin suite is run against it in a subprocess."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dgs_oracle.c")
+
+MUTATIONS = {
+    "ade_dropped_term": ("int64_t diff = A(i, jp) + A(ip, j) - A(i, j) - A(ip, jp);",
+                         "int64_t diff = A(i, jp) + A(ip, j) - A(i, j);"),
+    "ade_ties_to_last": ("        if (diff > best) {\n            best = diff;\n            best_job = jp;",
+                         "        if (diff >= best && diff > 0) {\n            best = diff;\n            best_job = jp;"),
+    "jde_wrong_index": ("int64_t diff = A(ip, j) + A(i, jp) - A(i, j) - A(ip, jp);",
+                        "int64_t diff = A(ip, j) + A(i, jp) - A(i, j) - A(ip, j);"),
+    "cc_partner_not_through_sigma": ("int32_t ip = sigma[agent_job[i]];\n        if (cr[i] || cr[ip]) {",
+                                     "int32_t ip = agent_job[i];\n        if (cr[i] || cr[ip]) {"),
+    "cc_job_owner_unchecked": ("if (cr[owner] || cr[partner]) {", "if (cr[partner]) {"),
+    "reevaluate_wrong_set": ("if (!in_ca[i]) { oracle_ade", "if (in_ca[i]) { oracle_ade"),
+    "apply_non_improving": ("                if (g > 0) {\n                    do_exchange",
+                            "                if (g >= 0) {\n                    do_exchange"),
+    "greedy_tie_job_first": ("((uint64_t)i << 17) | (uint64_t)j;", "((uint64_t)j << 17) | (uint64_t)i;"),
+    "hungarian_sign": ("-A(row - 1, c - 1) - u[row] - v[c]", "-A(row - 1, c - 1) - u[row] + v[c]"),
+    "objective_sign": ("f += A(i, tau[i]);", "f -= A(i, tau[i]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(lib), str(mutant)])
+    env = dict(os.environ, DGS_ORACLE_LIB=str(lib))
+    try:
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=20)
+    except subprocess.TimeoutExpired:
+        return  # a pin that no longer terminates has caught the mutation
+    assert r.returncode != 0, f"mutation {name} survived the oracle pins"
