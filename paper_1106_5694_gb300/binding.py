@@ -1,0 +1,211 @@
+"""Thin Python binding of the C ABI in include/dgs.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device arrays are
+torch CUDA tensors (int32, contiguous); the stream defaults to torch's current
+stream on the tensors' device.  There is no fallback: if the CUDA library is
+not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libdgs.so")
+
+DGS_OK = 0
+DGS_ERR_INVALID = 1
+DGS_ERR_RANGE = 2
+DGS_ERR_OOM = 3
+DGS_ERR_CUDA = 4
+DGS_TIMEOUT = 5
+DGS_PENDING = 6
+DGS_ERR_BUSY = 7
+DGS_ERR_INTERNAL = 8
+
+DGS_INIT_GREEDY = 0
+DGS_INIT_IDENTITY = 2
+DGS_INIT_USER = 3
+
+EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
+            "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error"]
+
+
+class dgs_options(ctypes.Structure):
+    _fields_ = [
+        ("init", ctypes.c_int32),
+        ("init_sigma", ctypes.c_void_p),
+        ("max_sweeps", ctypes.c_int32),
+        ("deadline_us", ctypes.c_int64),
+        ("trace_capacity", ctypes.c_int32),
+        ("trace_accepted", ctypes.c_void_p),
+        ("trace_applied", ctypes.c_void_p),
+        ("trace_objective", ctypes.c_void_p),
+    ]
+
+
+class dgs_stats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int32),
+        ("events", ctypes.c_int32),
+        ("swaps_applied", ctypes.c_int64),
+        ("greedy_rounds", ctypes.c_int32),
+        ("full_evaluations", ctypes.c_int32),
+        ("row_updates", ctypes.c_int32),
+        ("rows_recomputed", ctypes.c_int64),
+        ("initial_objective", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libdgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing "
+                           "(run __graft_entry__.build() or paper_1106_5694_gb300/build_ext.py)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.dgs_default_options.argtypes = [ctypes.POINTER(dgs_options)]
+    lib.dgs_default_options.restype = None
+    lib.dgs_solve.argtypes = [P, i32, P, ctypes.POINTER(i64), P]
+    lib.dgs_solve.restype = ctypes.c_int
+    lib.dgs_solve_ex.argtypes = [P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_options),
+                                 ctypes.POINTER(dgs_stats), P]
+    lib.dgs_solve_ex.restype = ctypes.c_int
+    lib.dgs_solve_host.argtypes = [P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_options),
+                                   ctypes.POINTER(dgs_stats), P]
+    lib.dgs_solve_host.restype = ctypes.c_int
+    lib.dgs_evaluate.argtypes = [P, i32, P, P, P, P, P, P]
+    lib.dgs_evaluate.restype = ctypes.c_int
+    lib.dgs_greedy_init.argtypes = [P, i32, P, P]
+    lib.dgs_greedy_init.restype = ctypes.c_int
+    lib.dgs_status_string.argtypes = [ctypes.c_int]
+    lib.dgs_status_string.restype = ctypes.c_char_p
+    lib.dgs_last_cuda_error.argtypes = []
+    lib.dgs_last_cuda_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _dev(t: torch.Tensor, name: str) -> ctypes.c_void_p:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(t: torch.Tensor, stream):
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _n(benefit) -> int:
+    if benefit.ndim != 2 or benefit.shape[0] != benefit.shape[1]:
+        raise ValueError("benefit must be a square n x n matrix")
+    return int(benefit.shape[0])
+
+
+def dgs_status_string(status: int) -> str:
+    return load().dgs_status_string(int(status)).decode()
+
+
+def dgs_last_cuda_error() -> str:
+    return load().dgs_last_cuda_error().decode()
+
+
+def dgs_default_options() -> dgs_options:
+    o = dgs_options()
+    load().dgs_default_options(ctypes.byref(o))
+    return o
+
+
+def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None):
+    o = dgs_default_options()
+    o.init = init
+    o.init_sigma = _dev(init_sigma, "init_sigma") if init_sigma is not None else None
+    o.max_sweeps = max_sweeps
+    o.deadline_us = deadline_us
+    if trace is not None:
+        acc, app, obj = trace
+        o.trace_capacity = int(acc.numel())
+        o.trace_accepted = ctypes.c_void_p(acc.data_ptr())
+        o.trace_applied = ctypes.c_void_p(app.data_ptr())
+        o.trace_objective = ctypes.c_void_p(obj.data_ptr())
+    return o
+
+
+def dgs_solve(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None):
+    """dgs_solve: returns (status, sigma_out, objective)."""
+    n = _n(benefit)
+    if sigma_out is None:
+        sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
+    f = ctypes.c_int64(0)
+    st = load().dgs_solve(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
+                          _stream(benefit, stream))
+    return st, sigma_out, int(f.value)
+
+
+def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, **opts):
+    """dgs_solve_ex: returns (status, sigma_out, objective, stats dict).
+
+    Keyword options: init, init_sigma (int32 CUDA tensor), max_sweeps,
+    deadline_us, trace=(accepted int32, applied int32, objective int64) CUDA
+    tensors of equal length."""
+    n = _n(benefit)
+    if sigma_out is None:
+        sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
+    o = _options(**opts)
+    f = ctypes.c_int64(0)
+    s = dgs_stats()
+    st = load().dgs_solve_ex(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
+                             ctypes.byref(o), ctypes.byref(s), _stream(benefit, stream))
+    return st, sigma_out, int(f.value), s.as_dict()
+
+
+def dgs_solve_host(benefit: np.ndarray, stream=None, device=None, **opts):
+    """dgs_solve_host: benefit is a host (numpy) int32 n x n array; returns
+    (status, sigma_out numpy, objective, stats dict).  Copies are inside the call."""
+    a = np.ascontiguousarray(benefit, dtype=np.int32)
+    n = _n(a)
+    out = np.empty(n, dtype=np.int32)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    s_obj = stream if stream is not None else torch.cuda.current_stream(dev)
+    o = _options(**opts)
+    f = ctypes.c_int64(0)
+    s = dgs_stats()
+    st = load().dgs_solve_host(ctypes.c_void_p(a.ctypes.data), n, ctypes.c_void_p(out.ctypes.data),
+                               ctypes.byref(f), ctypes.byref(o), ctypes.byref(s),
+                               ctypes.c_void_p(s_obj.cuda_stream))
+    return st, out, int(f.value), s.as_dict()
+
+
+def dgs_evaluate(benefit: torch.Tensor, sigma_in: torch.Tensor, stream=None):
+    """dgs_evaluate: returns (status, agent_gain, agent_job, job_gain, job_agent)."""
+    n = _n(benefit)
+    outs = [torch.empty(n, dtype=torch.int32, device=benefit.device) for _ in range(4)]
+    st = load().dgs_evaluate(_dev(benefit, "benefit"), n, _dev(sigma_in, "sigma_in"),
+                             *[_dev(o, "out") for o in outs], _stream(benefit, stream))
+    return (st, *outs)
+
+
+def dgs_greedy_init(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None):
+    """dgs_greedy_init: returns (status, sigma_out)."""
+    n = _n(benefit)
+    if sigma_out is None:
+        sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
+    st = load().dgs_greedy_init(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"),
+                                _stream(benefit, stream))
+    return st, sigma_out

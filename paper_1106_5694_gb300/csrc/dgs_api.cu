@@ -1,0 +1,412 @@
+// dgs_api.cu -- the C ABI of include/dgs.h: argument checks, workspace,
+// and the host loop that enqueues the kernels of one solve.
+//
+// Solve flow (Algorithm 3, Section 5, plus the greedy start of Section 3.1):
+//   pass 1        transpose a -> at, |a| < 2^29 check, first greedy round keys
+//   greedy rounds match mutually-best pairs, rescan rows/columns (device loop,
+//                 checked from the host every few rounds)
+//   start         sigma, D, f from the starting tau
+//   evaluation    full difference evaluation (every slot)
+//   switching     controller (quiet sweeps on one CTA) ->
+//                 [mark rescan rows -> full evaluation | row tasks] -> controller ...
+// The host reads the 100-byte loop state every few launches to learn when the
+// loop has ended; everything else stays on the device.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/dgs.h"
+#include "dgs_internal.cuh"
+
+namespace dgs {
+cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_claimed, uint8_t* g_estate,
+                                   cudaStream_t s);
+}
+
+namespace {
+
+using namespace dgs;
+
+thread_local char g_last_error[512] = "";
+
+dgs_status cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    return DGS_ERR_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// One stream-ordered allocation carved into every array of a solve.
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    template <typename T>
+    T* take(size_t count) {
+        T* p = reinterpret_cast<T*>(base + used);
+        used += align_up(count * sizeof(T), 256);
+        return p;
+    }
+};
+
+struct Plan {
+    bool need_copy = false;   // a must be re-laid out (n % 4 != 0 or misaligned)
+    bool need_at = true;      // transposed copy (greedy start, row tasks)
+    int32_t lda = 0, ldt = 0;
+    size_t bytes = 0;
+};
+
+int32_t round_up32(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
+
+std::vector<int2> evaluation_items(int32_t n) {
+    const int32_t nb = (n + 63) / 64;
+    const int32_t strip = evaluation_strip();
+    std::vector<int2> items;
+    items.reserve((size_t)nb * nb / (2 * strip) + nb + 1);
+    for (int32_t j = 0; j < nb; ++j)
+        for (int32_t k = j; k < nb; k += strip) items.push_back(make_int2(j, k));
+    return items;
+}
+
+// Carve the workspace; sizes first (base == nullptr), then pointers.
+size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, int32_t** ctl_res,
+             uint8_t** ctl_claimed, uint8_t** ctl_estate, uint8_t** seen, int32_t** a_copy) {
+    const size_t nb = align_up((size_t)n, 128);
+    *a_copy = p.need_copy ? ar.take<int32_t>((size_t)n * p.lda) : nullptr;
+    w.at = p.need_at ? ar.take<int32_t>((size_t)n * p.ldt + 64) : nullptr;
+    w.sigma = ar.take<int32_t>(nb);
+    w.tau = ar.take<int32_t>(nb);
+    w.diag = ar.take<int32_t>(nb);
+    w.key_a = ar.take<unsigned long long>(nb);
+    w.key_j = ar.take<unsigned long long>(nb);
+    w.ag_gain = ar.take<int32_t>(nb);
+    w.ag_job = ar.take<int32_t>(nb);
+    w.jb_gain = ar.take<int32_t>(nb);
+    w.jb_agent = ar.take<int32_t>(nb);
+    w.in_ca = ar.take<uint8_t>(nb);
+    w.in_cj = ar.take<uint8_t>(nb);
+    w.in_y = ar.take<uint8_t>(nb);
+    w.moved = ar.take<uint8_t>(nb);
+    w.y_list = ar.take<int32_t>(nb);
+    w.rescan_list = ar.take<int32_t>(nb);
+    w.edges = ar.take<int4>(2 * nb);
+    w.g_row = ar.take<unsigned long long>(nb);
+    w.g_col = ar.take<unsigned long long>(nb);
+    w.free_a = ar.take<uint8_t>(nb);
+    w.free_j = ar.take<uint8_t>(nb);
+    w.items = ar.take<int2>(items ? items : 1);
+    w.st = ar.take<DeviceState>(1);
+    *seen = ar.take<uint8_t>(4 * nb);
+    if (controller_smem_bytes(n) == 0) {
+        *ctl_res = ar.take<int32_t>(nb);
+        *ctl_claimed = ar.take<uint8_t>(nb);
+        *ctl_estate = ar.take<uint8_t>(2 * nb);
+    } else {
+        *ctl_res = nullptr;
+        *ctl_claimed = nullptr;
+        *ctl_estate = nullptr;
+    }
+    return ar.used;
+}
+
+// Everything one call needs, released in the destructor (stream-ordered).
+struct Solve {
+    cudaStream_t s;
+    Arena ar;
+    Workspace w{};
+    Plan plan;
+    int32_t *ctl_res = nullptr, *a_copy = nullptr;
+    uint8_t *ctl_claimed = nullptr, *ctl_estate = nullptr, *seen = nullptr;
+    std::vector<int2> items;
+    explicit Solve(cudaStream_t st) : s(st) {}
+    ~Solve() {
+        if (ar.base) cudaFreeAsync(ar.base, s);
+    }
+
+    dgs_status setup(const int32_t* a, int32_t n, bool need_at, bool need_items) {
+        plan.need_at = need_at;
+        plan.need_copy = (n % 4) != 0 || (reinterpret_cast<uintptr_t>(a) % 16) != 0;
+        plan.lda = plan.need_copy ? round_up32(n, 4) : n;
+        plan.ldt = round_up32(n, 64);
+        if (need_items) items = evaluation_items(n);
+        Arena sizing;
+        Workspace tmp{};
+        carve(sizing, tmp, plan, n, items.size(), &ctl_res, &ctl_claimed, &ctl_estate, &seen, &a_copy);
+        plan.bytes = sizing.used;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            snprintf(g_last_error, sizeof(g_last_error), "workspace of %zu bytes", plan.bytes);
+            ar.base = nullptr;
+            return DGS_ERR_OOM;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        ar.size = plan.bytes;
+        carve(ar, w, plan, n, items.size(), &ctl_res, &ctl_claimed, &ctl_estate, &seen, &a_copy);
+        w.n = n;
+        w.lda = plan.lda;
+        w.ldt = plan.ldt;
+        w.item_count = (int32_t)items.size();
+        if (plan.need_copy) {
+            e = cudaMemsetAsync(a_copy, 0, (size_t)n * plan.lda * sizeof(int32_t), s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+            e = cudaMemcpy2DAsync(a_copy, (size_t)plan.lda * 4, a, (size_t)n * 4, (size_t)n * 4, n,
+                                  cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+            w.a = a_copy;
+        } else {
+            w.a = a;
+        }
+        // zero every small array in one go (they follow a/at in the arena)
+        char* small_begin = reinterpret_cast<char*>(w.sigma);
+        const size_t small_bytes = (size_t)(ar.base + ar.used - small_begin);
+        e = cudaMemsetAsync(small_begin, 0, small_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        const size_t nb = align_up((size_t)n, 128);
+        e = cudaMemsetAsync(w.free_a, 1, nb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.free_j, 1, nb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        if (!items.empty()) {
+            e = cudaMemcpyAsync(w.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(items)");
+        }
+        return DGS_OK;
+    }
+
+    dgs_status init_state(int32_t max_sweeps, const dgs_options* o) {
+        DeviceState h{};
+        h.status = kRunning;
+        h.phase = kPhaseRefreshAll;
+        h.max_sweeps = max_sweeps;
+        h.greedy_remaining = w.n;
+        if (o) {
+            h.trace_capacity = o->trace_capacity > 0 ? o->trace_capacity : 0;
+            h.trace_accepted = o->trace_accepted;
+            h.trace_applied = o->trace_applied;
+            h.trace_objective = o->trace_objective;
+        }
+        cudaError_t e = cudaMemcpyAsync(w.st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(state)");
+        return DGS_OK;
+    }
+
+    dgs_status read_state(DeviceState* h) {
+        cudaError_t e = cudaMemcpyAsync(h, w.st, sizeof(*h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading loop state");
+        return DGS_OK;
+    }
+};
+
+__global__ void arm_deadline_kernel(DeviceState* st, int64_t deadline_us) {
+    uint64_t now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    st->deadline_ns = now + (uint64_t)deadline_us * 1000ull;
+}
+
+__global__ void record_initial_objective_kernel(DeviceState* st) { st->f_initial = st->f; }
+
+dgs_status map_device_status(const DeviceState& h) {
+    if (h.status == kDone) return DGS_OK;
+    if (h.status == kTimeout) return DGS_TIMEOUT;
+    if (h.status == kError) {
+        if (h.error == kErrRange) return DGS_ERR_RANGE;
+        if (h.error == kErrUserInit) return DGS_ERR_INVALID;
+        snprintf(g_last_error, sizeof(g_last_error), "device-side error code %d", h.error);
+        return DGS_ERR_INTERNAL;
+    }
+    return DGS_OK;
+}
+
+#define DGS_TRY(expr)                          \
+    do {                                       \
+        dgs_status _st = (expr);               \
+        if (_st != DGS_OK) return _st;         \
+    } while (0)
+#define DGS_CUDA(expr, what)                               \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// Greedy rounds until every agent is matched (or an error).
+dgs_status run_greedy(Solve& S) {
+    DGS_CUDA(launch_greedy_pass1(S.w, S.s), "greedy pass 1");
+    const int32_t batch = 8;
+    for (int32_t launched = 0; launched <= S.w.n + batch; launched += batch) {
+        for (int32_t r = 0; r < batch; ++r) DGS_CUDA(launch_greedy_round(S.w, S.s), "greedy round");
+        DeviceState h;
+        DGS_TRY(S.read_state(&h));
+        if (h.status != kRunning || h.greedy_remaining == 0) return DGS_OK;
+    }
+    snprintf(g_last_error, sizeof(g_last_error), "greedy start did not finish");
+    return DGS_ERR_INTERNAL;
+}
+
+dgs_status check_common(const int32_t* benefit, int32_t n) {
+    if (benefit == nullptr || n <= 0 || n > kMaxN) return DGS_ERR_INVALID;
+    return DGS_OK;
+}
+
+dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
+                      const dgs_options* opt, dgs_stats* stats, cudaStream_t stream) {
+    DGS_TRY(check_common(benefit, n));
+    if (sigma_out == nullptr || objective_out == nullptr) return DGS_ERR_INVALID;
+    dgs_options o;
+    dgs_default_options(&o);
+    if (opt) o = *opt;
+    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY && o.init != DGS_INIT_USER) return DGS_ERR_INVALID;
+    if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
+
+    Solve S(stream);
+    DGS_TRY(S.setup(benefit, n, true, true));
+    DGS_TRY(S.init_state(o.max_sweeps, &o));
+    if (o.deadline_us > 0) {
+        arm_deadline_kernel<<<1, 1, 0, stream>>>(S.w.st, o.deadline_us);
+        DGS_CUDA(cudaGetLastError(), "arm deadline");
+    }
+    if (o.init == DGS_INIT_GREEDY) {
+        DGS_TRY(run_greedy(S));
+    } else {
+        DGS_CUDA(launch_greedy_pass1(S.w, stream), "pass 1");  // transpose + range check
+    }
+    DGS_CUDA(launch_start_from_tau(S.w, o.init_sigma, o.init, S.seen, stream), "start");
+    record_initial_objective_kernel<<<1, 1, 0, stream>>>(S.w.st);
+    DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
+    DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+    DeviceState h;
+    const int32_t batch = 4;
+    const int64_t max_iterations = 16 * (int64_t)n + 4096;
+    bool ended = false;
+    for (int64_t it = 0; it < max_iterations; it += batch) {
+        DGS_TRY(S.read_state(&h));
+        if (h.status != kRunning) {
+            ended = true;
+            break;
+        }
+        for (int32_t b = 0; b < batch; ++b) {
+            DGS_CUDA(launch_mark_rescan(S.w, stream), "mark");
+            DGS_CUDA(launch_full_evaluation(S.w, 1, stream), "re-evaluation");
+            DGS_CUDA(launch_row_tasks(S.w, stream), "row tasks");
+            DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+        }
+    }
+    if (!ended) {
+        snprintf(g_last_error, sizeof(g_last_error), "switching loop did not finish");
+        return DGS_ERR_INTERNAL;
+    }
+    DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
+    DGS_TRY(S.read_state(&h));
+    const dgs_status status = map_device_status(h);
+    *objective_out = h.f;
+    if (stats) {
+        stats->sweeps = h.sweeps;
+        stats->events = h.events;
+        stats->swaps_applied = h.swaps;
+        stats->greedy_rounds = h.greedy_rounds;
+        stats->full_evaluations = h.full_evals + 1;
+        stats->row_updates = h.row_updates;
+        stats->rows_recomputed = h.rows_recomputed;
+        stats->initial_objective = h.f_initial;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dgs_default_options(dgs_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->init = DGS_INIT_GREEDY;
+}
+
+dgs_status dgs_solve(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
+                     dgs_stream_t stream) {
+    return solve_impl(benefit, n, sigma_out, objective_out, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dgs_status dgs_solve_ex(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
+                        const dgs_options* options, dgs_stats* stats, dgs_stream_t stream) {
+    return solve_impl(benefit, n, sigma_out, objective_out, options, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n, int32_t* sigma_out_host, int64_t* objective_out,
+                          const dgs_options* options, dgs_stats* stats, dgs_stream_t stream) {
+    if (benefit_host == nullptr || sigma_out_host == nullptr || objective_out == nullptr || n <= 0 || n > kMaxN)
+        return DGS_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t abytes = (size_t)n * n * sizeof(int32_t);
+    const size_t obytes = align_up((size_t)n * sizeof(int32_t), 256);
+    char* buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), abytes + obytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return DGS_ERR_OOM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    int32_t* a_dev = reinterpret_cast<int32_t*>(buf + obytes);
+    int32_t* out_dev = reinterpret_cast<int32_t*>(buf);
+    dgs_status st = DGS_OK;
+    e = cudaMemcpyAsync(a_dev, benefit_host, abytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "copy benefit to device");
+    if (st == DGS_OK) st = solve_impl(a_dev, n, out_dev, objective_out, options, stats, s);
+    if (st == DGS_OK || st == DGS_TIMEOUT) {
+        e = cudaMemcpyAsync(sigma_out_host, out_dev, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy result to host");
+    }
+    cudaFreeAsync(buf, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+dgs_status dgs_evaluate(const int32_t* benefit, int32_t n, const int32_t* sigma_in, int32_t* agent_gain,
+                        int32_t* agent_job, int32_t* job_gain, int32_t* job_agent, dgs_stream_t stream) {
+    DGS_TRY(check_common(benefit, n));
+    if (!sigma_in || !agent_gain || !agent_job || !job_gain || !job_agent) return DGS_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Solve S(s);
+    DGS_TRY(S.setup(benefit, n, false, true));
+    DGS_TRY(S.init_state(0, nullptr));
+    DGS_CUDA(launch_range_check(S.w, s), "range check");
+    DGS_CUDA(launch_start_from_tau(S.w, sigma_in, DGS_INIT_USER, S.seen, s), "start");
+    DGS_CUDA(launch_full_evaluation(S.w, 0, s), "evaluation");
+    DGS_CUDA(launch_keys_to_slots(S.w, agent_gain, agent_job, job_gain, job_agent, s), "keys to slots");
+    DeviceState h;
+    DGS_TRY(S.read_state(&h));
+    return map_device_status(h);
+}
+
+dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* sigma_out, dgs_stream_t stream) {
+    DGS_TRY(check_common(benefit, n));
+    if (!sigma_out) return DGS_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Solve S(s);
+    DGS_TRY(S.setup(benefit, n, true, false));
+    DGS_TRY(S.init_state(0, nullptr));
+    DGS_TRY(run_greedy(S));
+    DGS_CUDA(launch_finish(S.w, sigma_out, s), "finish");
+    DeviceState h;
+    DGS_TRY(S.read_state(&h));
+    return map_device_status(h);
+}
+
+const char* dgs_status_string(dgs_status status) {
+    switch (status) {
+        case DGS_OK: return "DGS_OK";
+        case DGS_ERR_INVALID: return "DGS_ERR_INVALID";
+        case DGS_ERR_RANGE: return "DGS_ERR_RANGE";
+        case DGS_ERR_OOM: return "DGS_ERR_OOM";
+        case DGS_ERR_CUDA: return "DGS_ERR_CUDA";
+        case DGS_TIMEOUT: return "DGS_TIMEOUT";
+        case DGS_PENDING: return "DGS_PENDING";
+        case DGS_ERR_BUSY: return "DGS_ERR_BUSY";
+        case DGS_ERR_INTERNAL: return "DGS_ERR_INTERNAL";
+    }
+    return "DGS_UNKNOWN";
+}
+
+const char* dgs_last_cuda_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// dgs_internal.cuh -- device-side state, key packing and PTX helpers shared
+// by the DGS kernels (greedy start, difference evaluation, switching
+// control).  Internal to the library; the public interface is include/dgs.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgs {
+
+// ----------------------------------------------------------------- limits
+constexpr int32_t kMaxN = 1 << 17;           // index fields are 17 bits in places
+constexpr int32_t kBenefitLimit = 1 << 29;   // |a| < 2^29 keeps gains exact in int32
+constexpr uint32_t kSpinLimit = 1u << 26;    // bound on every device-side wait loop
+
+// Loop status (DeviceState::status).
+enum : int32_t { kRunning = 0, kDone = 1, kTimeout = 2, kError = 3 };
+// Device-side error codes (DeviceState::error).
+enum : int32_t { kErrNone = 0, kErrRange = 1, kErrUserInit = 2, kErrWaitTimeout = 3, kErrInternal = 4 };
+// Controller entry phase.
+enum : int32_t { kPhaseRefreshAll = 0, kPhaseQuiet = 1 };
+
+// All scalar loop state of one solve, resident in device memory.
+struct DeviceState {
+    int32_t status;          // kRunning / kDone / kTimeout / kError
+    int32_t error;           // kErr*
+    int32_t phase;           // controller entry phase
+    int32_t need_update;     // 1: the last sweep committed exchanges
+    int32_t sweeps;          // switching sweeps done
+    int32_t max_sweeps;      // <= 0: none
+    int32_t events;          // sweeps with >= 1 committed exchange
+    int32_t y_count;         // jobs whose holder changed in the last event sweep
+    int32_t rescan_count;    // rows needing a full re-evaluation
+    int32_t edge_count;      // live candidate slots in the edge list
+    int32_t greedy_remaining;// unmatched agents during the greedy start
+    int32_t greedy_rounds;
+    int32_t full_evals;
+    int32_t row_updates;
+    int32_t trace_capacity;
+    int32_t greedy_matched;  // the last match kernel matched >= 1 pair
+    int64_t f;               // current objective
+    int64_t f_initial;
+    int64_t swaps;           // committed exchanges
+    int64_t rows_recomputed;
+    uint64_t deadline_ns;    // %globaltimer deadline, 0: none
+    int32_t* trace_accepted;
+    int32_t* trace_applied;
+    int64_t* trace_objective;
+};
+
+// Pointers to every array of one solve (passed by value to kernels).
+struct Workspace {
+    const int32_t* a;   // benefit, row pitch lda (elements), lda % 4 == 0, 16-B aligned
+    int32_t* at;        // transposed benefit, row pitch ldt, at[j*ldt + i] = a[i*lda + j]
+    int32_t n, lda, ldt, pad;
+    int32_t* sigma;     // job -> agent
+    int32_t* tau;       // agent -> job
+    int32_t* diag;      // D[j] = a[sigma[j]][j]
+    unsigned long long* key_a;  // row best, agent-slot tie-break (lowest column)
+    unsigned long long* key_j;  // row best, job-slot tie-break (lowest partner agent)
+    int32_t* ag_gain; int32_t* ag_job;    // agent slot candidates
+    int32_t* jb_gain; int32_t* jb_agent;  // job slot candidates
+    uint8_t* in_ca; uint8_t* in_cj;       // conflict set C (reading R3: slots)
+    uint8_t* in_y; uint8_t* moved;        // jobs changed / agents moved in the last event
+    int32_t* y_list;                      // jobs changed in the last event
+    int32_t* rescan_list;                 // rows to re-evaluate fully
+    int4* edges;                          // live candidate slots {prio, u, v, 0}
+    // greedy start
+    unsigned long long* g_row;  // best free job per agent   (biased value, ~j)
+    unsigned long long* g_col;  // best free agent per job   (biased value, ~i)
+    uint8_t* free_a; uint8_t* free_j;
+    // evaluation work items (row-block, first column tile) of the tile-pair sweep
+    int2* items; int32_t item_count; int32_t pad2;
+    DeviceState* st;
+};
+
+// ------------------------------------------------------------- key packing
+// A candidate (gain > 0, index) packs into 64 bits so that unsigned max picks
+// the larger gain and, among equal gains, the LOWER index.
+__device__ __forceinline__ unsigned long long pack_gain(int32_t gain, uint32_t idx) {
+    return ((unsigned long long)(uint32_t)gain << 32) | (unsigned long long)(~idx);
+}
+__device__ __forceinline__ int32_t key_gain(unsigned long long k) { return (int32_t)(k >> 32); }
+__device__ __forceinline__ int32_t key_index(unsigned long long k) { return (int32_t)(~(uint32_t)k); }
+
+// Greedy order key: larger benefit first, then lower index.  Benefits are
+// biased by 2^29 into [1, 2^30) so that the key is never 0 (0 = "none").
+__device__ __forceinline__ unsigned long long pack_benefit(int32_t a, uint32_t idx) {
+    return ((unsigned long long)(uint32_t)(a + kBenefitLimit) << 32) | (unsigned long long)(~idx);
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsigned long long y) {
+    return x > y ? x : y;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------ mbarrier / bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: returns false when the spin limit is reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------ host-side launchers
+// Each returns the launch error (cudaSuccess on success).
+cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s);
+cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s);
+cudaError_t launch_range_check(const Workspace& w, cudaStream_t s);
+cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, int32_t mode, uint8_t* seen,
+                                  cudaStream_t s);
+cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
+cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
+                                 cudaStream_t s);
+cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_claimed, uint8_t* g_estate,
+                                   cudaStream_t s);
+size_t controller_smem_bytes(int32_t n);
+size_t full_evaluation_smem_bytes();
+int32_t evaluation_strip();
+cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s);
+cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
+cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
+
+// Raise a kernel's dynamic shared memory limit once per device (slot = one
+// small integer per kernel).
+inline cudaError_t ensure_smem_limit(const void* func, int slot, size_t bytes) {
+    static int done[8][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 8) return cudaErrorInvalidValue;
+    if (done[slot][dev] >= (int)bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[slot][dev] = (int)bytes;
+    return e;
+}
+
+// Decision rule shared by the conditional update kernels: re-evaluate all
+// rows with the tile-pair sweep when the row tasks would touch more bytes.
+__host__ __device__ __forceinline__ bool use_full_update(int32_t rescans, int32_t n) {
+    return (int64_t)rescans * 2 > (int64_t)n;
+}
+
+}  // namespace dgs

@@ -1,0 +1,221 @@
+"""GPU path (C ABI, sm_103a kernels) against the CPU oracle, element by element.
+
+Integer work throughout, so the bar is bit-exactness: assignment, objective,
+sweep count, per-sweep trace and every slot of a fresh evaluation.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1106_5694_gb300 import binding as B
+from paper_1106_5694_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_traces.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1106_5694_gb300 import build_ext
+    build_ext.build()
+    oracle.build()
+    B.load()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def _make(kind, n, seed):
+    if kind == "uniform":
+        return inputs.uniform(n, 0, 1000, seed)
+    if kind == "wide":
+        return inputs.uniform(n, -(10**8), 10**8, seed)
+    if kind == "peer":
+        return inputs.peer_shaped(n, seed)
+    if kind == "ties":
+        return inputs.uniform(n, 0, 4, seed)
+    if kind == "geom":
+        return inputs.geom(n, 1000.0, seed)
+    if kind == "constant":
+        return np.full((n, n), 5, np.int32)
+    raise ValueError(kind)
+
+
+# ------------------------------------------------------- difference evaluation
+EVAL_CASES = [(k, n, s) for k in ("uniform", "ties", "peer", "wide")
+              for n in (1, 2, 3, 5, 63, 64, 65, 130, 257, 301) for s in (0, 1)]
+
+
+@pytest.mark.parametrize("kind,n,seed", EVAL_CASES)
+def test_evaluate_matches_oracle(kind, n, seed):
+    a = _make(kind, n, seed)
+    tau = inputs.random_permutation(n, 1000 + seed)
+    st, ag, aj, jg, ja = B.dgs_evaluate(_cuda(a), _cuda(tau))
+    assert st == B.DGS_OK, B.dgs_status_string(st)
+    want = oracle.evaluate_all(a, tau)
+    for got, exp, name in zip((ag, aj, jg, ja), want, ("agent_gain", "agent_job", "job_gain", "job_agent")):
+        np.testing.assert_array_equal(got.cpu().numpy(), exp, err_msg=name)
+
+
+# --------------------------------------------------------------- greedy start
+GREEDY_CASES = [(k, n, s) for k in ("uniform", "ties", "peer", "constant")
+                for n in (1, 7, 64, 100, 256, 513) for s in (0, 1)]
+
+
+@pytest.mark.parametrize("kind,n,seed", GREEDY_CASES)
+def test_greedy_matches_oracle(kind, n, seed):
+    a = _make(kind, n, seed)
+    st, sig = B.dgs_greedy_init(_cuda(a))
+    assert st == B.DGS_OK
+    np.testing.assert_array_equal(sig.cpu().numpy(), oracle.greedy_init(a))
+
+
+# ------------------------------------------------------------------ full solve
+SOLVE_CASES = [(k, n, s) for k in ("uniform", "ties", "peer", "geom", "wide")
+               for n in (2, 3, 9, 33, 64, 129, 200) for s in (0, 1)] + \
+              [("uniform", 512, 0), ("peer", 512, 1), ("ties", 401, 2), ("uniform", 1024, 3), ("peer", 1024, 0)]
+
+
+def _trace_tensors(cap):
+    return (torch.zeros(cap, dtype=torch.int32, device="cuda"), torch.zeros(cap, dtype=torch.int32, device="cuda"),
+            torch.zeros(cap, dtype=torch.int64, device="cuda"))
+
+
+@pytest.mark.parametrize("kind,n,seed", SOLVE_CASES)
+def test_solve_matches_oracle(kind, n, seed):
+    a = _make(kind, n, seed)
+    ref = oracle.dgs_parallel(a, trace_cap=100000)
+    assert ref.status == oracle.OK
+    tr = _trace_tensors(max(ref.sweeps, 1))
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), trace=tr)
+    assert st == B.DGS_OK, B.dgs_status_string(st)
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective
+    assert stats["sweeps"] == ref.sweeps
+    assert stats["swaps_applied"] == ref.swaps_applied
+    k = ref.sweeps
+    np.testing.assert_array_equal(tr[0][:k].cpu().numpy(), ref.trace_accepted)
+    np.testing.assert_array_equal(tr[1][:k].cpu().numpy(), ref.trace_applied)
+    np.testing.assert_array_equal(tr[2][:k].cpu().numpy(), ref.trace_objective)
+
+
+@pytest.mark.parametrize("name", ["n3_identity", "n2_antidiagonal"])
+def test_hand_traces_on_gpu(name):
+    with open(GOLDEN) as fh:
+        t = {x["name"]: x for x in json.load(fh)["traces"]}[name]
+    a = np.array(t["a"], np.int32)
+    tr = _trace_tensors(16)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_IDENTITY, trace=tr)
+    assert st == B.DGS_OK
+    assert sig.cpu().tolist() == t["tau"] and f == t["objective"] and stats["sweeps"] == t["sweeps"]
+    k = t["sweeps"]
+    assert tr[0][:k].cpu().tolist() == t["accepted"]
+    assert tr[1][:k].cpu().tolist() == t["applied"]
+
+
+@pytest.mark.parametrize("init", ["identity", "user"])
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 150, 4), ("peer", 97, 5), ("ties", 64, 6)])
+def test_other_starts_match_oracle(init, kind, n, seed):
+    a = _make(kind, n, seed)
+    if init == "identity":
+        ref = oracle.dgs_parallel(a, init=oracle.INIT_IDENTITY)
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_IDENTITY)
+    else:
+        p = inputs.random_permutation(n, seed)
+        ref = oracle.dgs_parallel(a, init=oracle.INIT_USER, init_tau=p)
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_USER, init_sigma=_cuda(p))
+    assert st == B.DGS_OK
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective and stats["sweeps"] == ref.sweeps
+
+
+@pytest.mark.parametrize("cap", [1, 2, 5, 17])
+def test_sweep_cap_matches_oracle_prefix(cap):
+    a = _make("uniform", 300, 9)
+    ref = oracle.dgs_parallel(a, max_sweeps=cap)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), max_sweeps=cap)
+    expect = B.DGS_TIMEOUT if ref.status == oracle.TIMEOUT else B.DGS_OK
+    assert st == expect
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective and stats["sweeps"] == ref.sweeps
+
+
+def test_errors():
+    a = _make("uniform", 20, 0)
+    bad = a.copy()
+    bad[3, 4] = 1 << 29
+    st, _, _ = B.dgs_solve(_cuda(bad))
+    assert st == B.DGS_ERR_RANGE
+    neg = a.copy()
+    neg[0, 0] = -(1 << 29)
+    assert B.dgs_solve(_cuda(neg))[0] == B.DGS_ERR_RANGE
+    dup = np.arange(20, dtype=np.int32)
+    dup[5] = 6
+    st, _, _, _ = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_USER, init_sigma=_cuda(dup))
+    assert st == B.DGS_ERR_INVALID
+    empty = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
+    assert B.dgs_solve(empty)[0] == B.DGS_ERR_INVALID
+    # library stays usable after errors
+    st, sig, f = B.dgs_solve(_cuda(a))
+    assert st == B.DGS_OK and f == oracle.dgs_parallel(a).objective
+
+
+def test_single_agent():
+    st, sig, f = B.dgs_solve(_cuda(np.array([[-7]], np.int32)))
+    assert st == B.DGS_OK and sig.cpu().tolist() == [0] and f == -7
+
+
+def test_host_entry_point_matches_device():
+    a = _make("peer", 210, 3)
+    st_h, sig_h, f_h, _ = B.dgs_solve_host(a)
+    st_d, sig_d, f_d = B.dgs_solve(_cuda(a))
+    assert st_h == st_d == B.DGS_OK
+    np.testing.assert_array_equal(sig_h, sig_d.cpu().numpy())
+    assert f_h == f_d
+
+
+def test_deterministic_repeat():
+    a = _make("uniform", 700, 11)
+    outs = [B.dgs_solve(_cuda(a)) for _ in range(3)]
+    for st, sig, f in outs:
+        assert st == B.DGS_OK and f == outs[0][2]
+        assert torch.equal(sig, outs[0][1])
+
+
+# ------------------------------------------ larger sizes: prefix + properties
+def _local_opt_gpu(a_t, sig):
+    n = a_t.shape[0]
+    a64 = a_t.to(torch.int64)
+    d = a64[torch.arange(n, device="cuda"), sig.long()]
+    cross = a64[:, sig.long()]
+    g = cross + cross.T - d[:, None] - d[None, :]
+    return int(g.max().item())
+
+
+@pytest.mark.parametrize("kind,n", [("peer", 4096), ("uniform", 4096)])
+def test_workload_4096_prefix_and_properties(kind, n):
+    a = inputs.peer_shaped(n, 0) if kind == "peer" else inputs.uniform(n, 0, 10**6, 0)
+    at = _cuda(a)
+    # exact prefix: the first sweeps equal the oracle's
+    cap = 3
+    ref = oracle.dgs_parallel(a, max_sweeps=cap, trace_cap=cap)
+    tr = _trace_tensors(cap)
+    st, sig, f, stats = B.dgs_solve_ex(at, max_sweeps=cap, trace=tr)
+    assert st == (B.DGS_TIMEOUT if ref.status == oracle.TIMEOUT else B.DGS_OK)
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective
+    np.testing.assert_array_equal(tr[0][:ref.sweeps].cpu().numpy(), ref.trace_accepted)
+    # full solve: permutation, exact objective, no improving 2-exchange
+    st, sig, f, stats = B.dgs_solve_ex(at)
+    assert st == B.DGS_OK
+    s = sig.cpu().numpy()
+    assert np.array_equal(np.sort(s), np.arange(n))
+    assert f == int(a[np.arange(n), s].astype(np.int64).sum())
+    assert _local_opt_gpu(at, sig) <= 0
+    assert f >= stats["initial_objective"]
