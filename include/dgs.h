@@ -77,6 +77,9 @@ typedef struct {
     int32_t* trace_accepted;
     int32_t* trace_applied;
     int64_t* trace_objective;
+    /* 1: time the first full difference evaluation with CUDA events on the
+     * call's stream (dgs_stats.evaluation_ms); 0: no timing. */
+    int32_t profile;
 } dgs_options;
 
 typedef struct {
@@ -88,6 +91,8 @@ typedef struct {
     int32_t row_updates;      /* incremental re-evaluations (row tasks) */
     int64_t rows_recomputed;  /* rows re-evaluated by those row tasks */
     int64_t initial_objective;/* objective of the starting assignment */
+    int64_t kernel_launches;  /* kernels this call launched */
+    double evaluation_ms;     /* first full evaluation, when options.profile */
 } dgs_stats;
 
 /* Fill *opt with the defaults (GREEDY start, no cap, no deadline, no trace). */

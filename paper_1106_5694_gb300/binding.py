@@ -43,6 +43,7 @@ class dgs_options(ctypes.Structure):
         ("trace_accepted", ctypes.c_void_p),
         ("trace_applied", ctypes.c_void_p),
         ("trace_objective", ctypes.c_void_p),
+        ("profile", ctypes.c_int32),
     ]
 
 
@@ -56,10 +57,12 @@ class dgs_stats(ctypes.Structure):
         ("row_updates", ctypes.c_int32),
         ("rows_recomputed", ctypes.c_int64),
         ("initial_objective", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("evaluation_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
-        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+        return {name: (float if name.endswith("_ms") else int)(getattr(self, name)) for name, _ in self._fields_}
 
 
 _lib = None
@@ -132,9 +135,10 @@ def dgs_default_options() -> dgs_options:
     return o
 
 
-def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None):
+def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None, profile=0):
     o = dgs_default_options()
     o.init = init
+    o.profile = int(profile)
     o.init_sigma = _dev(init_sigma, "init_sigma") if init_sigma is not None else None
     o.max_sweeps = max_sweeps
     o.deadline_us = deadline_us

@@ -117,6 +117,7 @@ struct Solve {
     int32_t *ctl_res = nullptr, *a_copy = nullptr;
     uint8_t *ctl_claimed = nullptr, *ctl_estate = nullptr, *seen = nullptr;
     std::vector<int2> items;
+    int64_t launches = 0;
     explicit Solve(cudaStream_t st) : s(st) {}
     ~Solve() {
         if (ar.base) cudaFreeAsync(ar.base, s);
@@ -197,6 +198,30 @@ struct Solve {
     }
 };
 
+// CUDA events around one launch on the call's stream (options.profile).
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    dgs_status begin(cudaStream_t s) {
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        return e == cudaSuccess ? DGS_OK : cuda_fail(e, "profile event");
+    }
+    dgs_status end(cudaStream_t s) {
+        cudaError_t e = cudaEventRecord(b, s);
+        return e == cudaSuccess ? DGS_OK : cuda_fail(e, "profile event");
+    }
+    double elapsed_ms() const {
+        float ms = 0.f;
+        if (a && b && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) return ms;
+        return 0.0;
+    }
+};
+
 __global__ void arm_deadline_kernel(DeviceState* st, int64_t deadline_us) {
     uint64_t now;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
@@ -231,9 +256,11 @@ dgs_status map_device_status(const DeviceState& h) {
 // Greedy rounds until every agent is matched (or an error).
 dgs_status run_greedy(Solve& S) {
     DGS_CUDA(launch_greedy_pass1(S.w, S.s), "greedy pass 1");
+    S.launches += 1;
     const int32_t batch = 8;
     for (int32_t launched = 0; launched <= S.w.n + batch; launched += batch) {
         for (int32_t r = 0; r < batch; ++r) DGS_CUDA(launch_greedy_round(S.w, S.s), "greedy round");
+        S.launches += 3 * batch;
         DeviceState h;
         DGS_TRY(S.read_state(&h));
         if (h.status != kRunning || h.greedy_remaining == 0) return DGS_OK;
@@ -263,16 +290,22 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.deadline_us > 0) {
         arm_deadline_kernel<<<1, 1, 0, stream>>>(S.w.st, o.deadline_us);
         DGS_CUDA(cudaGetLastError(), "arm deadline");
+        S.launches += 1;
     }
     if (o.init == DGS_INIT_GREEDY) {
         DGS_TRY(run_greedy(S));
     } else {
         DGS_CUDA(launch_greedy_pass1(S.w, stream), "pass 1");  // transpose + range check
+        S.launches += 1;
     }
     DGS_CUDA(launch_start_from_tau(S.w, o.init_sigma, o.init, S.seen, stream), "start");
     record_initial_objective_kernel<<<1, 1, 0, stream>>>(S.w.st);
+    EventPair ev;
+    if (o.profile) DGS_TRY(ev.begin(stream));
     DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
+    if (o.profile) DGS_TRY(ev.end(stream));
     DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+    S.launches += 4;
     DeviceState h;
     const int32_t batch = 4;
     const int64_t max_iterations = 16 * (int64_t)n + 4096;
@@ -288,6 +321,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
             DGS_CUDA(launch_full_evaluation(S.w, 1, stream), "re-evaluation");
             DGS_CUDA(launch_row_tasks(S.w, stream), "row tasks");
             DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+            S.launches += 4;
         }
     }
     if (!ended) {
@@ -295,6 +329,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         return DGS_ERR_INTERNAL;
     }
     DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
+    S.launches += 1;
     DGS_TRY(S.read_state(&h));
     const dgs_status status = map_device_status(h);
     *objective_out = h.f;
@@ -307,6 +342,8 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         stats->row_updates = h.row_updates;
         stats->rows_recomputed = h.rows_recomputed;
         stats->initial_objective = h.f_initial;
+        stats->kernel_launches = S.launches;
+        stats->evaluation_ms = o.profile ? ev.elapsed_ms() : 0.0;
     }
     return status;
 }
