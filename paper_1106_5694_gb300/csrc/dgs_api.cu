@@ -12,16 +12,32 @@
 // The host reads the 100-byte loop state every few launches to learn when the
 // loop has ended; everything else stays on the device.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
 
+
 namespace dgs {
-cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_claimed, uint8_t* g_estate,
-                                   cudaStream_t s);
+int32_t env_update_policy() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_UPDATE_POLICY");
+        const int32_t x = e ? std::atoi(e) : 0;
+        return (x >= 0 && x <= 2) ? x : 0;
+    }();
+    return v;
 }
+int32_t env_controller_mode_cap() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_CTL_MODE");
+        const int32_t x = e ? std::atoi(e) : 2;
+        return (x >= 0 && x <= 2) ? x : 2;
+    }();
+    return v;
+}
+}  // namespace dgs
 
 namespace {
 
@@ -69,7 +85,7 @@ std::vector<int2> evaluation_items(int32_t n) {
 
 // Carve the workspace; sizes first (base == nullptr), then pointers.
 size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, int32_t** ctl_res,
-             uint8_t** ctl_claimed, uint8_t** ctl_estate, uint8_t** seen, int32_t** a_copy) {
+             unsigned long long** ctl_edges, uint8_t** ctl_estate, uint8_t** seen, int32_t** a_copy) {
     const size_t nb = align_up((size_t)n, 128);
     *a_copy = p.need_copy ? ar.take<int32_t>((size_t)n * p.lda) : nullptr;
     w.at = p.need_at ? ar.take<int32_t>((size_t)n * p.ldt + 64) : nullptr;
@@ -88,7 +104,10 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, in
     w.moved = ar.take<uint8_t>(nb);
     w.y_list = ar.take<int32_t>(nb);
     w.rescan_list = ar.take<int32_t>(nb);
-    w.edges = ar.take<int4>(2 * nb);
+    w.ctl_slot = ar.take<int32_t>(2 * nb);
+    w.ctl_rkey = ar.take<unsigned long long>(2 * nb);
+    w.ctl_ru = ar.take<int32_t>(2 * nb);
+    w.ctl_rv = ar.take<int32_t>(2 * nb);
     w.g_row = ar.take<unsigned long long>(nb);
     w.g_col = ar.take<unsigned long long>(nb);
     w.free_a = ar.take<uint8_t>(nb);
@@ -96,15 +115,10 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, in
     w.items = ar.take<int2>(items ? items : 1);
     w.st = ar.take<DeviceState>(1);
     *seen = ar.take<uint8_t>(4 * nb);
-    if (controller_smem_bytes(n) == 0) {
-        *ctl_res = ar.take<int32_t>(nb);
-        *ctl_claimed = ar.take<uint8_t>(nb);
-        *ctl_estate = ar.take<uint8_t>(2 * nb);
-    } else {
-        *ctl_res = nullptr;
-        *ctl_claimed = nullptr;
-        *ctl_estate = nullptr;
-    }
+    const int32_t mode = controller_smem_mode(n);
+    *ctl_edges = mode < 2 ? ar.take<unsigned long long>(2 * nb) : nullptr;
+    *ctl_res = mode < 1 ? ar.take<int32_t>(nb) : nullptr;
+    *ctl_estate = mode < 1 ? ar.take<uint8_t>(2 * nb) : nullptr;
     return ar.used;
 }
 
@@ -115,7 +129,8 @@ struct Solve {
     Workspace w{};
     Plan plan;
     int32_t *ctl_res = nullptr, *a_copy = nullptr;
-    uint8_t *ctl_claimed = nullptr, *ctl_estate = nullptr, *seen = nullptr;
+    unsigned long long* ctl_edges = nullptr;
+    uint8_t *ctl_estate = nullptr, *seen = nullptr;
     std::vector<int2> items;
     int64_t launches = 0;
     explicit Solve(cudaStream_t st) : s(st) {}
@@ -131,7 +146,7 @@ struct Solve {
         if (need_items) items = evaluation_items(n);
         Arena sizing;
         Workspace tmp{};
-        carve(sizing, tmp, plan, n, items.size(), &ctl_res, &ctl_claimed, &ctl_estate, &seen, &a_copy);
+        carve(sizing, tmp, plan, n, items.size(), &ctl_res, &ctl_edges, &ctl_estate, &seen, &a_copy);
         plan.bytes = sizing.used;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
         if (e == cudaErrorMemoryAllocation) {
@@ -142,7 +157,7 @@ struct Solve {
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
         ar.size = plan.bytes;
-        carve(ar, w, plan, n, items.size(), &ctl_res, &ctl_claimed, &ctl_estate, &seen, &a_copy);
+        carve(ar, w, plan, n, items.size(), &ctl_res, &ctl_edges, &ctl_estate, &seen, &a_copy);
         w.n = n;
         w.lda = plan.lda;
         w.ldt = plan.ldt;
@@ -179,6 +194,7 @@ struct Solve {
         h.phase = kPhaseRefreshAll;
         h.max_sweeps = max_sweeps;
         h.greedy_remaining = w.n;
+        h.update_policy = env_update_policy();
         if (o) {
             h.trace_capacity = o->trace_capacity > 0 ? o->trace_capacity : 0;
             h.trace_accepted = o->trace_accepted;
@@ -304,7 +320,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.profile) DGS_TRY(ev.begin(stream));
     DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
     if (o.profile) DGS_TRY(ev.end(stream));
-    DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+    DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_estate, S.ctl_edges, stream), "controller");
     S.launches += 4;
     DeviceState h;
     const int32_t batch = 4;
@@ -320,7 +336,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
             DGS_CUDA(launch_mark_rescan(S.w, stream), "mark");
             DGS_CUDA(launch_full_evaluation(S.w, 1, stream), "re-evaluation");
             DGS_CUDA(launch_row_tasks(S.w, stream), "row tasks");
-            DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_claimed, S.ctl_estate, stream), "controller");
+            DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_estate, S.ctl_edges, stream), "controller");
             S.launches += 4;
         }
     }

@@ -38,6 +38,8 @@ struct DeviceState {
     int32_t row_updates;
     int32_t trace_capacity;
     int32_t greedy_matched;  // the last match kernel matched >= 1 pair
+    int32_t update_policy;   // 0: by cost, 1: always full evaluation, 2: always row tasks
+    int32_t pad1;
     int64_t f;               // current objective
     int64_t f_initial;
     int64_t swaps;           // committed exchanges
@@ -64,7 +66,12 @@ struct Workspace {
     uint8_t* in_y; uint8_t* moved;        // jobs changed / agents moved in the last event
     int32_t* y_list;                      // jobs changed in the last event
     int32_t* rescan_list;                 // rows to re-evaluate fully
-    int4* edges;                          // live candidate slots {prio, u, v, 0}
+    // controller: per edge position (priority order) the slot, and the
+    // re-evaluated candidate of that slot (key, exchange agents)
+    int32_t* ctl_slot;
+    unsigned long long* ctl_rkey;
+    int32_t* ctl_ru;
+    int32_t* ctl_rv;
     // greedy start
     unsigned long long* g_row;  // best free job per agent   (biased value, ~j)
     unsigned long long* g_col;  // best free agent per job   (biased value, ~i)
@@ -149,8 +156,9 @@ cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, i
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s);
-cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_claimed, uint8_t* g_estate,
+cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_estate, unsigned long long* g_edges,
                                    cudaStream_t s);
+int32_t controller_smem_mode(int32_t n);
 size_t controller_smem_bytes(int32_t n);
 size_t full_evaluation_smem_bytes();
 int32_t evaluation_strip();
@@ -173,9 +181,17 @@ inline cudaError_t ensure_smem_limit(const void* func, int slot, size_t bytes) {
 }
 
 // Decision rule shared by the conditional update kernels: re-evaluate all
-// rows with the tile-pair sweep when the row tasks would touch more bytes.
-__host__ __device__ __forceinline__ bool use_full_update(int32_t rescans, int32_t n) {
+// rows with the tile-pair sweep when the row tasks would touch more bytes
+// (policy 1 / 2 force one path; both give identical keys).
+__host__ __device__ __forceinline__ bool use_full_update(int32_t rescans, int32_t n, int32_t policy) {
+    if (policy == 1) return true;
+    if (policy == 2) return false;
     return (int64_t)rescans * 2 > (int64_t)n;
 }
+
+// Test knobs read from the environment once: DGS_UPDATE_POLICY (0/1/2) and
+// DGS_CTL_MODE (cap on the controller's shared-memory placement, 0..2).
+int32_t env_update_policy();
+int32_t env_controller_mode_cap();
 
 }  // namespace dgs

@@ -14,22 +14,27 @@
 // Design (HBM-bound, no tensor cores): G is symmetric, so one 64x64 block
 // G[J][K] (J <= K) serves the rows of J (over columns K) and the rows of K
 // (over columns J).  The block needs the tiles X = R[J,K] and Y = R[K,J]:
-// 64 row segments of 256 B each, gathered through sigma and copied into
-// shared memory by the TMA engine (1-D cp.async.bulk, mbarrier completion).
-// Every element of a is read exactly once per evaluation.  A CTA walks a
-// strip of tiles with the same J, keeping the row-side maxima of its 64 rows
-// in registers; column-side maxima are committed per tile with 64-bit
-// atomicMax, which is order independent and therefore deterministic.
+// 64 row segments of 256 B each, gathered through sigma.  All 512 threads
+// stage them into shared memory with 16-byte cp.async copies in a 5-deep
+// pipeline (one barrier per tile).  Every element of a is read exactly once
+// per evaluation.  (One-dimensional TMA bulk copies of the same 256-byte
+// segments were measured request-rate bound at about 1.5 TB/s on GB300, which
+// is why the copies are issued by the threads.)  A CTA walks a strip of tiles
+// with the same J, keeping the row-side maxima of its 64 rows in registers;
+// column-side maxima of each tile are combined across the CTA in shared
+// memory at the next barrier and committed with 64-bit atomicMax, which is
+// order independent and therefore deterministic.
 #include "dgs_internal.cuh"
 
 namespace dgs {
 namespace {
 
-constexpr int kT = 64;        // tile edge
-constexpr int kYP = kT + 4;   // Y row pitch (ints): 16-B aligned and int4-conflict-free
-constexpr int kStages = 3;
-constexpr int kThreads = 256; // 4 row groups x 64 columns
-constexpr int kRows = 16;     // rows per thread
+constexpr int kT = 64;         // tile edge
+constexpr int kYP = kT + 4;    // Y row pitch (ints): 16-B aligned and int4-conflict-free
+constexpr int kStages = 5;
+constexpr int kThreads = 512;  // 8 row groups x 64 columns
+constexpr int kRows = 8;       // rows per thread
+constexpr int kGroups = kThreads / kT;
 
 struct Stage {
     int32_t x[kT * kT];
@@ -54,28 +59,47 @@ __device__ __forceinline__ bool cursor_load(TileCursor& c, const Workspace& w, i
     return true;
 }
 
-// Issue the bulk copies of tile (J, K) into stage s (warp 0, all lanes).
-__device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, uint64_t* bar, int32_t J, int32_t K) {
-    const int lane = threadIdx.x & 31;
-    const int32_t n = w.n;
+__device__ __forceinline__ bool cursor_next(TileCursor& c, const Workspace& w, int32_t nb, int32_t strip) {
+    if (++c.k < c.kend) return true;
+    return cursor_load(c, w, c.item + gridDim.x, nb, strip);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// sigma of the rows this thread copies for tile (J, K): X rows J0+rq, J0+rq+32
+// and Y rows K0+rq, K0+rq+32 (row rq = threadIdx.x / 16).
+struct CopyRows {
+    int32_t x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ CopyRows copy_rows(const Workspace& w, int32_t J, int32_t K) {
+    const int32_t rq = threadIdx.x >> 4;
+    const int32_t J0 = J * kT, K0 = K * kT, n = w.n;
+    CopyRows c;
+    c.x0 = (J0 + rq < n) ? w.sigma[J0 + rq] : -1;
+    c.x1 = (J0 + rq + 32 < n) ? w.sigma[J0 + rq + 32] : -1;
+    c.y0 = (K0 + rq < n) ? w.sigma[K0 + rq] : -1;
+    c.y1 = (K0 + rq + 32 < n) ? w.sigma[K0 + rq + 32] : -1;
+    return c;
+}
+
+// Issue this thread's four 16-byte copies of tile (J, K) into stage.
+__device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int32_t J, int32_t K,
+                                           const CopyRows& c) {
+    const int32_t chunk = (threadIdx.x & 15) * 4;  // first int of the 16-byte chunk
+    const int32_t rq = threadIdx.x >> 4;
     const int32_t J0 = J * kT, K0 = K * kT;
-    const int32_t rows_x = min(kT, n - J0), rows_y = min(kT, n - K0);
-    const uint32_t bytes_x = 4u * (uint32_t)min(kT, w.lda - K0);  // row segment of X (columns K)
-    const uint32_t bytes_y = 4u * (uint32_t)min(kT, w.lda - J0);  // row segment of Y (columns J)
-    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)rows_x * bytes_x + (uint32_t)rows_y * bytes_y);
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int r = lane + 32 * h;
-        if (r < rows_x) {
-            const int32_t src_row = w.sigma[J0 + r];
-            bulk_g2s(stage->x + r * kT, w.a + (size_t)src_row * w.lda + K0, bytes_x, bar);
-        }
-        if (r < rows_y) {
-            const int32_t src_row = w.sigma[K0 + r];
-            bulk_g2s(stage->y + r * kYP, w.a + (size_t)src_row * w.lda + J0, bytes_y, bar);
-        }
-    }
+    const bool in_x = chunk < w.lda - K0;  // X rows hold columns K0.. (row pitch lda)
+    const bool in_y = chunk < w.lda - J0;  // Y rows hold columns J0..
+    if (in_x && c.x0 >= 0) cp_async16(stage->x + rq * kT + chunk, w.a + (size_t)c.x0 * w.lda + K0 + chunk);
+    if (in_x && c.x1 >= 0) cp_async16(stage->x + (rq + 32) * kT + chunk, w.a + (size_t)c.x1 * w.lda + K0 + chunk);
+    if (in_y && c.y0 >= 0) cp_async16(stage->y + rq * kYP + chunk, w.a + (size_t)c.y0 * w.lda + J0 + chunk);
+    if (in_y && c.y1 >= 0) cp_async16(stage->y + (rq + 32) * kYP + chunk, w.a + (size_t)c.y1 * w.lda + J0 + chunk);
 }
 
 struct RowState {
@@ -84,52 +108,72 @@ struct RowState {
     int32_t s[kRows];  // lowest partner agent among the columns reaching g
 };
 
+// One tile: thread (ty, tx) covers column k = K0 + tx and rows J0 + ty*8 .. +7.
+// Column-side partial keys go to colbuf (combined at the next barrier).
 template <bool kRagged>
 __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, const int32_t (&dj)[kRows],
                                              const int32_t (&sj)[kRows], int32_t J0, int32_t K0, int32_t n,
-                                             const Workspace& w) {
+                                             const Workspace& w, unsigned long long* col_a,
+                                             unsigned long long* col_j) {
     const int tx = threadIdx.x & 63;
     const int ty = threadIdx.x >> 6;
     const int32_t k = K0 + tx;
-    if (kRagged && k >= n) return;
-    const int32_t sk = w.sigma[k];
-    const int32_t dk = w.diag[k];
-    int32_t cg = 0, cc = -1, cs = 0x7fffffff;
-    const int32_t* xrow = stage->x + (ty * kRows) * kT + tx;
-    const int4* yrow = reinterpret_cast<const int4*>(stage->y + tx * kYP + ty * kRows);
+    unsigned long long ka = 0ull, kj = 0ull;
+    if (!kRagged || k < n) {
+        const int32_t sk = w.sigma[k];
+        const int32_t dk = w.diag[k];
+        int32_t cg = 0, cc = -1, cs = 0x7fffffff;
+        const int32_t* xrow = stage->x + (ty * kRows) * kT + tx;
+        const int4* yrow = reinterpret_cast<const int4*>(stage->y + tx * kYP + ty * kRows);
 #pragma unroll
-    for (int q = 0; q < kRows / 4; ++q) {
-        const int4 y4 = yrow[q];
-        const int32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+        for (int q = 0; q < kRows / 4; ++q) {
+            const int4 y4 = yrow[q];
+            const int32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int r = q * 4 + e;
-            const int32_t jr = J0 + ty * kRows + r;
-            if (kRagged && jr >= n) continue;
-            const int32_t x = xrow[r * kT];
-            const int32_t g = x + yv[e] - dj[r] - dk;
-            // row side: row jr, partner column k (ascending in this thread)
-            {
-                const bool gt = g > rs.g[r];
-                const bool eq = g == rs.g[r];
-                rs.s[r] = gt ? sk : (eq ? min(rs.s[r], sk) : rs.s[r]);
-                rs.c[r] = gt ? k : rs.c[r];
-                rs.g[r] = max(rs.g[r], g);
-            }
-            // column side: row k, partner column jr (ascending in this loop)
-            {
-                const bool gt = g > cg;
-                const bool eq = g == cg;
-                cs = gt ? sj[r] : (eq ? min(cs, sj[r]) : cs);
-                cc = gt ? jr : cc;
-                cg = max(cg, g);
+            for (int e = 0; e < 4; ++e) {
+                const int r = q * 4 + e;
+                const int32_t jr = J0 + ty * kRows + r;
+                if (kRagged && jr >= n) continue;
+                const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
+                // row side: row jr, partner column k (ascending in this thread)
+                {
+                    const bool gt = g > rs.g[r];
+                    const bool eq = g == rs.g[r];
+                    rs.s[r] = gt ? sk : (eq ? min(rs.s[r], sk) : rs.s[r]);
+                    rs.c[r] = gt ? k : rs.c[r];
+                    rs.g[r] = max(rs.g[r], g);
+                }
+                // column side: row k, partner column jr (ascending in this loop)
+                {
+                    const bool gt = g > cg;
+                    const bool eq = g == cg;
+                    cs = gt ? sj[r] : (eq ? min(cs, sj[r]) : cs);
+                    cc = gt ? jr : cc;
+                    cg = max(cg, g);
+                }
             }
         }
+        if (cg > 0) {
+            ka = pack_gain(cg, (uint32_t)cc);
+            kj = pack_gain(cg, (uint32_t)cs);
+        }
     }
-    if (cg > 0) {
-        atomicMax(&w.key_a[k], pack_gain(cg, (uint32_t)cc));
-        atomicMax(&w.key_j[k], pack_gain(cg, (uint32_t)cs));
-    }
+    col_a[ty * kT + tx] = ka;
+    col_j[ty * kT + tx] = kj;
+}
+
+// Combine the 8 row-group partials of the previous tile's columns.
+__device__ __forceinline__ void commit_columns(const unsigned long long* col_a, const unsigned long long* col_j,
+                                               int32_t K0, int32_t n, const Workspace& w) {
+    const int t = threadIdx.x;
+    if (t >= 2 * kT) return;
+    const int q = t & 63;
+    const unsigned long long* src = (t < kT) ? col_a : col_j;
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) m = umax64(m, src[g * kT + q]);
+    const int32_t k = K0 + q;
+    if (m != 0ull && k < n) atomicMax((t < kT) ? &w.key_a[k] : &w.key_j[k], m);
 }
 
 __device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int32_t n, const Workspace& w) {
@@ -152,45 +196,39 @@ __device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int3
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) full_evaluation_kernel(Workspace w, int32_t conditional,
+__global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
                                                                       int32_t strip) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
-    if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n))) return;
+    if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
     if (conditional && blockIdx.x == 0 && threadIdx.x == 0) st->full_evals += 1;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* stages = reinterpret_cast<Stage*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(Stage) * kStages);
+    unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(Stage) * kStages);
+    // colbuf[b][0: agent keys 8x64 | 1: job keys 8x64], b = tile parity
 
     const int32_t n = w.n;
     const int32_t nb = (n + kT - 1) / kT;
-    const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
 
-    // producer cursor (warp 0) runs kStages tiles ahead of the consumer
+    // producer cursor: kStages - 1 tiles ahead of the consumer
     TileCursor prod;
     bool prod_ok = cursor_load(prod, w, blockIdx.x, nb, strip);
-    int32_t issued = 0;
-    if (warp == 0) {
-        for (int s = 0; s < kStages && prod_ok; ++s) {
-            issue_tile(w, &stages[s], &bars[s], prod.j, prod.k);
-            ++issued;
-            if (++prod.k >= prod.kend) prod_ok = cursor_load(prod, w, prod.item + gridDim.x, nb, strip);
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (prod_ok) {
+            issue_tile(w, &stages[s], prod.j, prod.k, copy_rows(w, prod.j, prod.k));
+            prod_ok = cursor_next(prod, w, nb, strip);
         }
+        cp_async_commit();
     }
+    CopyRows next_rows = prod_ok ? copy_rows(w, prod.j, prod.k) : CopyRows{-1, -1, -1, -1};
 
     TileCursor cons;
     bool cons_ok = cursor_load(cons, w, blockIdx.x, nb, strip);
-    int32_t consumed = 0;
-    bool failed = false;
     RowState rs;
     int32_t dj[kRows], sj[kRows];
     bool item_start = true;
+    int32_t t = 0, prev_k0 = -1;
     while (cons_ok) {
         const int32_t J0 = cons.j * kT;
         if (item_start) {
@@ -206,39 +244,36 @@ __global__ void __launch_bounds__(kThreads, 2) full_evaluation_kernel(Workspace 
             }
             item_start = false;
         }
-        const int s = consumed % kStages;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((consumed / kStages) & 1));
-        if (__syncthreads_or(!ok)) {  // block-uniform decision
-            failed = true;
-            break;
+        cp_async_wait<kStages - 2>();
+        __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
+        if (prev_k0 >= 0) {
+            const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
+            commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
         }
+        if (prod_ok) {
+            issue_tile(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, next_rows);
+            prod_ok = cursor_next(prod, w, nb, strip);
+            if (prod_ok) next_rows = copy_rows(w, prod.j, prod.k);
+        }
+        cp_async_commit();
         const int32_t K0 = cons.k * kT;
-        const bool ragged = (J0 + kT > n) || (K0 + kT > n);
-        if (ragged) compute_tile<true>(&stages[s], rs, dj, sj, J0, K0, n, w);
-        else compute_tile<false>(&stages[s], rs, dj, sj, J0, K0, n, w);
-        ++consumed;
-        const bool last_of_item = (cons.k + 1 >= cons.kend);
-        if (last_of_item) commit_rows(rs, J0, n, w);
-        __syncthreads();  // stage s fully read
-        if (warp == 0 && prod_ok) {
-            issue_tile(w, &stages[s], &bars[s], prod.j, prod.k);
-            ++issued;
-            if (++prod.k >= prod.kend) prod_ok = cursor_load(prod, w, prod.item + gridDim.x, nb, strip);
-        }
+        unsigned long long* cb = colbuf + (t & 1) * 2 * kGroups * kT;
+        const Stage* stage = &stages[t % kStages];
+        if ((J0 + kT > n) || (K0 + kT > n)) compute_tile<true>(stage, rs, dj, sj, J0, K0, n, w, cb, cb + kGroups * kT);
+        else compute_tile<false>(stage, rs, dj, sj, J0, K0, n, w, cb, cb + kGroups * kT);
+        if (cons.k + 1 >= cons.kend) commit_rows(rs, J0, n, w);
+        prev_k0 = K0;
+        ++t;
         if (++cons.k >= cons.kend) {
             cons_ok = cursor_load(cons, w, cons.item + gridDim.x, nb, strip);
             item_start = true;
         }
     }
-    if (failed) {
-        // drain this CTA's own copies still in flight (bounded), then report
-        if (threadIdx.x == 0) {
-            for (int32_t t = consumed; t < issued; ++t)
-                (void)mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1));
-            atomicExch(&st->error, kErrWaitTimeout);
-            atomicExch(&st->status, kError);
-        }
-        __syncthreads();
+    cp_async_wait<0>();
+    __syncthreads();
+    if (prev_k0 >= 0) {
+        const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
+        commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
     }
 }
 
@@ -258,13 +293,13 @@ __global__ void keys_to_slots_kernel(Workspace w, int32_t* ag, int32_t* aj, int3
 
 constexpr int kStrip = 8;
 
-size_t full_evaluation_smem_bytes() { return sizeof(Stage) * kStages + 64; }
+size_t full_evaluation_smem_bytes() { return sizeof(Stage) * kStages + 2 * 2 * kGroups * kT * sizeof(unsigned long long); }
 
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s) {
     const size_t smem = full_evaluation_smem_bytes();
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel), 0, smem);
     if (e != cudaSuccess) return e;
-    int grid = w.item_count < 152 * 2 ? w.item_count : 152 * 2;
+    int grid = w.item_count < 152 ? w.item_count : 152;
     if (grid < 1) grid = 1;
     full_evaluation_kernel<<<grid, kThreads, smem, s>>>(w, conditional, kStrip);
     return cudaGetLastError();

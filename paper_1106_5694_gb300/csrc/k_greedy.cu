@@ -120,7 +120,7 @@ __global__ void greedy_match_kernel(Workspace w) {
 
 // Rescan: for each free "owner" whose best partner was taken, find the best
 // free partner in its row of mat (a for agents over jobs, at for jobs over
-// agents).  One warp per owner.
+// agents).  One CTA per owner; 16-byte loads, several in flight per thread.
 __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const int32_t* mat, int32_t ld,
                                                             unsigned long long* keys, const uint8_t* owner_free,
                                                             const uint8_t* partner_free, int32_t count_round) {
@@ -130,17 +130,17 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
         st->greedy_matched = 0;
     }
     if (st->status != kRunning || st->greedy_remaining == 0) return;
+    __shared__ unsigned long long red[8];
     const int32_t n = w.n;
-    const int lane = threadIdx.x & 31;
-    const int32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int32_t o = warp; o < n; o += nwarps) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int32_t o = blockIdx.x; o < n; o += gridDim.x) {
         if (!owner_free[o]) continue;
         const int32_t b = key_index(keys[o]);
         if (b >= 0 && b < n && partner_free[b]) continue;  // best partner still free
         const int32_t* row = mat + (size_t)o * ld;
         unsigned long long best = 0;
-        for (int32_t c = lane * 4; c < n; c += 128) {
+#pragma unroll 4
+        for (int32_t c = tid * 4; c < n; c += 1024) {
             const int4 v = *reinterpret_cast<const int4*>(row + c);
             const uint32_t fr = *reinterpret_cast<const uint32_t*>(partner_free + c);
             const int32_t vals[4] = {v.x, v.y, v.z, v.w};
@@ -150,7 +150,14 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
-        if (lane == 0) keys[o] = best;
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long m = 0;
+            for (int q = 0; q < 8; ++q) m = umax64(m, red[q]);
+            keys[o] = m;
+        }
+        __syncthreads();
     }
 }
 
@@ -191,8 +198,7 @@ cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s) {
 cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
     const int32_t nb = (w.n + 255) / 256;
     greedy_match_kernel<<<nb < 152 * 4 ? nb : 152 * 4, 256, 0, s>>>(w);
-    const int32_t wb = (w.n + 7) / 8;  // 8 warps per block, one owner per warp
-    const int32_t g = wb < 152 * 8 ? wb : 152 * 8;
+    const int32_t g = w.n < 152 * 8 ? w.n : 152 * 8;  // one owner per CTA at a time
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1);
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0);
     return cudaGetLastError();

@@ -219,3 +219,39 @@ def test_workload_4096_prefix_and_properties(kind, n):
     assert f == int(a[np.arange(n), s].astype(np.int64).sum())
     assert _local_opt_gpu(at, sig) <= 0
     assert f >= stats["initial_objective"]
+
+
+# ------------------------------- every internal path gives the same result
+_KNOB_SCRIPT = r"""
+import sys, json, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1106_5694_gb300 import binding as B, inputs
+out = []
+for kind, n, seed in {cases!r}:
+    a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
+    st, sig, f, stats = B.dgs_solve_ex(torch.from_numpy(a).cuda())
+    out.append([st, f, stats["sweeps"], sig.cpu().tolist()])
+print(json.dumps(out))
+"""
+
+
+@pytest.mark.parametrize("env", [{"DGS_UPDATE_POLICY": "1"}, {"DGS_UPDATE_POLICY": "2"},
+                                 {"DGS_CTL_MODE": "1"}, {"DGS_CTL_MODE": "0"},
+                                 {"DGS_CTL_MODE": "0", "DGS_UPDATE_POLICY": "2"}])
+def test_internal_paths_agree_with_oracle(env):
+    """Forcing the full-evaluation or row-task update path, or placing the
+    controller's scratch in global memory, must not change any result."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cases = [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 640, 4)]
+    code = _KNOB_SCRIPT.format(root=root, cases=cases)
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **env), capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    for (kind, n, seed), (st, f, sweeps, tau) in zip(cases, got):
+        a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
+        ref = oracle.dgs_parallel(a)
+        assert st == B.DGS_OK and f == ref.objective and sweeps == ref.sweeps
+        assert tau == ref.tau.tolist()
