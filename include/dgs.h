@@ -136,6 +136,34 @@ DGS_API dgs_status dgs_evaluate(const int32_t* benefit, int32_t n, const int32_t
 DGS_API dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* sigma_out,
                            dgs_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Difference evaluation without any allocation.  The paper has no
+ * counterpart to this entry point; it exists for callers that must not
+ * allocate device memory while they run -- for example a latency-bound
+ * dispatcher (an allocation can take driver locks or wait for the device),
+ * a process whose device memory is reserved up front by another allocator,
+ * or code that has no way to recover from a failed allocation.
+ *
+ * dgs_evaluate_static computes exactly what dgs_evaluate computes (same
+ * arguments, same outputs) but keeps all of its working memory in one fixed
+ * array compiled into the library, about 0.3 MB per GPU, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocator.  The caller still provides benefit, sigma_in
+ * and the four output arrays.
+ *
+ * Limits: 1 <= n <= DGS_STATIC_MAX_N, n a multiple of 4, benefit 16-byte
+ * aligned; otherwise DGS_ERR_INVALID, with the reason in
+ * dgs_last_cuda_error().  The first call on each device looks up the array's
+ * device address, so make that first call before any stream capture.  All
+ * calls share the one array and each call clears the parts it needs zeroed;
+ * calls that overlap on the GPU (other streams or host threads) race on it and
+ * must be serialised by the caller.  Blocks until the outputs are final. */
+#define DGS_STATIC_MAX_N 8192
+DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_t n, const int32_t* sigma_in,
+                                       int32_t* agent_gain, int32_t* agent_job,
+                                       int32_t* job_gain, int32_t* job_agent,
+                                       dgs_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 DGS_API const char* dgs_status_string(dgs_status status);
 

@@ -30,7 +30,8 @@ DGS_INIT_IDENTITY = 2
 DGS_INIT_USER = 3
 
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
-            "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error"]
+            "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error"]
+DGS_STATIC_MAX_N = 8192
 
 
 class dgs_options(ctypes.Structure):
@@ -94,6 +95,8 @@ def load():
     lib.dgs_solve_host.restype = ctypes.c_int
     lib.dgs_evaluate.argtypes = [P, i32, P, P, P, P, P, P]
     lib.dgs_evaluate.restype = ctypes.c_int
+    lib.dgs_evaluate_static.argtypes = [P, i32, P, P, P, P, P, P]
+    lib.dgs_evaluate_static.restype = ctypes.c_int
     lib.dgs_greedy_init.argtypes = [P, i32, P, P]
     lib.dgs_greedy_init.restype = ctypes.c_int
     lib.dgs_status_string.argtypes = [ctypes.c_int]
@@ -202,6 +205,18 @@ def dgs_evaluate(benefit: torch.Tensor, sigma_in: torch.Tensor, stream=None):
     outs = [torch.empty(n, dtype=torch.int32, device=benefit.device) for _ in range(4)]
     st = load().dgs_evaluate(_dev(benefit, "benefit"), n, _dev(sigma_in, "sigma_in"),
                              *[_dev(o, "out") for o in outs], _stream(benefit, stream))
+    return (st, *outs)
+
+
+def dgs_evaluate_static(benefit: torch.Tensor, sigma_in: torch.Tensor, outputs=None, stream=None):
+    """dgs_evaluate_static (no allocation inside the library): returns
+    (status, agent_gain, agent_job, job_gain, job_agent).  ``outputs`` may hold
+    four preallocated int32 CUDA tensors of length n."""
+    n = _n(benefit)
+    outs = outputs if outputs is not None else [torch.empty(n, dtype=torch.int32, device=benefit.device)
+                                                for _ in range(4)]
+    st = load().dgs_evaluate_static(_dev(benefit, "benefit"), n, _dev(sigma_in, "sigma_in"),
+                                    *[_dev(o, "out") for o in outs], _stream(benefit, stream))
     return (st, *outs)
 
 

@@ -40,10 +40,16 @@ int32_t env_controller_mode_cap() {
 }  // namespace dgs
 
 namespace {
+thread_local char g_last_error[512] = "";
+}  // namespace
+
+namespace dgs {
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace dgs
+
+namespace {
 
 using namespace dgs;
-
-thread_local char g_last_error[512] = "";
 
 dgs_status cuda_fail(cudaError_t e, const char* what) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));

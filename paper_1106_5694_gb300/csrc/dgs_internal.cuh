@@ -192,6 +192,8 @@ __host__ __device__ __forceinline__ bool use_full_update(int32_t rescans, int32_
 // Test knobs read from the environment once: DGS_UPDATE_POLICY (0/1/2) and
 // DGS_CTL_MODE (cap on the controller's shared-memory placement, 0..2).
 int32_t env_update_policy();
+// Store the text returned by dgs_last_cuda_error() for this thread.
+void set_last_error(const char* msg);
 int32_t env_controller_mode_cap();
 
 }  // namespace dgs

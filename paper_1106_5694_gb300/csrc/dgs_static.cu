@@ -1,0 +1,154 @@
+// dgs_static.cu -- dgs_evaluate_static: the full difference evaluation with
+// all of its working memory in one fixed array that is part of the library's
+// device image, so that the call allocates nothing.
+//
+// The array lives at file scope below.  Its name, used in host code, is only
+// a host-side stand-in for the device object: handing it to a kernel would
+// make the kernel read the wrong memory or fault.  The device address is
+// obtained once per device with cudaGetSymbolAddress (with that device
+// current) and cached; that lookup happens inside the first call on each
+// device, which should therefore come before any stream capture.
+//
+// Every call reuses the same array and leaves its contents behind; the parts
+// that must start at zero (row keys, permutation check, loop state) are
+// cleared on each call.  Two calls whose work overlaps on the GPU (different
+// streams, different host threads) race on the array and must be serialised
+// by the caller.
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/dgs.h"
+#include "dgs_internal.cuh"
+
+namespace {
+
+using namespace dgs;
+
+constexpr int32_t kStaticMaxN = DGS_STATIC_MAX_N;
+constexpr int32_t kTiles = (kStaticMaxN + 63) / 64;
+constexpr int32_t kStripTiles = 8;  // same strip length as the solver's evaluation
+constexpr size_t kMaxItems = (size_t)kTiles * (kTiles + 1) / 2 / kStripTiles + kTiles + 1;
+
+// Byte offsets of each array inside the static block (each 256-B aligned).
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kOffSigma = 0;
+constexpr size_t kOffTau = kOffSigma + align256(4 * (size_t)kStaticMaxN);
+constexpr size_t kOffDiag = kOffTau + align256(4 * (size_t)kStaticMaxN);
+constexpr size_t kOffKeyA = kOffDiag + align256(4 * (size_t)kStaticMaxN);
+constexpr size_t kOffKeyJ = kOffKeyA + align256(8 * (size_t)kStaticMaxN);
+constexpr size_t kOffSeen = kOffKeyJ + align256(8 * (size_t)kStaticMaxN);
+constexpr size_t kOffItems = kOffSeen + align256(4 * (size_t)kStaticMaxN);
+constexpr size_t kOffState = kOffItems + align256(8 * kMaxItems);
+constexpr size_t kStaticBytes = kOffState + align256(sizeof(DeviceState));
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_mutex;
+void* g_scratch_addr[64] = {};
+
+// Device address of g_static_scratch on the current device (looked up once).
+cudaError_t scratch_address(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return cudaSuccess;
+}
+
+int32_t item_count_for(int32_t n) {
+    const int32_t nb = (n + 63) / 64;
+    int32_t c = 0;
+    for (int32_t j = 0; j < nb; ++j) c += (nb - j + kStripTiles - 1) / kStripTiles;
+    return c;
+}
+
+// Work items (row block J, first column tile K) of the tile-pair evaluation.
+__global__ void static_items_kernel(int2* items, int32_t nb) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    int32_t off = 0;
+    for (int32_t q = 0; q < j; ++q) off += (nb - q + kStripTiles - 1) / kStripTiles;
+    for (int32_t k = j; k < nb; k += kStripTiles) items[off++] = make_int2(j, k);
+}
+
+__global__ void static_state_kernel(DeviceState* st) {
+    *st = DeviceState{};
+    st->status = kRunning;
+}
+
+
+}  // namespace
+
+extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_t n, const int32_t* sigma_in,
+                                                  int32_t* agent_gain, int32_t* agent_job, int32_t* job_gain,
+                                                  int32_t* job_agent, dgs_stream_t stream) {
+    if (!benefit || !sigma_in || !agent_gain || !agent_job || !job_gain || !job_agent || n <= 0)
+        return DGS_ERR_INVALID;
+    char why[160];
+    if (n > kStaticMaxN) {
+        snprintf(why, sizeof(why), "dgs_evaluate_static: n=%d exceeds DGS_STATIC_MAX_N=%d", n, kStaticMaxN);
+        set_last_error(why);
+        return DGS_ERR_INVALID;
+    }
+    if (n % 4 != 0 || reinterpret_cast<uintptr_t>(benefit) % 16 != 0) {
+        snprintf(why, sizeof(why), "dgs_evaluate_static: n=%d must be a multiple of 4 and benefit 16-byte aligned",
+                 n);
+        set_last_error(why);
+        return DGS_ERR_INVALID;
+    }
+    if (evaluation_strip() != kStripTiles) return DGS_ERR_INTERNAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DGS_ERR_CUDA;
+    }
+    Workspace w{};
+    w.a = benefit;
+    w.n = n;
+    w.lda = n;
+    w.ldt = 0;
+    w.sigma = reinterpret_cast<int32_t*>(base + kOffSigma);
+    w.tau = reinterpret_cast<int32_t*>(base + kOffTau);
+    w.diag = reinterpret_cast<int32_t*>(base + kOffDiag);
+    w.key_a = reinterpret_cast<unsigned long long*>(base + kOffKeyA);
+    w.key_j = reinterpret_cast<unsigned long long*>(base + kOffKeyJ);
+    uint8_t* seen = base + kOffSeen;
+    w.items = reinterpret_cast<int2*>(base + kOffItems);
+    w.item_count = item_count_for(n);
+    w.st = reinterpret_cast<DeviceState*>(base + kOffState);
+
+    const int32_t nb = (n + 63) / 64;
+    // what must start at zero: row keys, the permutation check, the loop state
+    e = cudaMemsetAsync(w.key_a, 0, kOffSeen - kOffKeyA, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(seen, 0, 4 * (size_t)n, s);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DGS_ERR_CUDA;
+    }
+    static_state_kernel<<<1, 1, 0, s>>>(w.st);
+    static_items_kernel<<<(nb + 127) / 128, 128, 0, s>>>(w.items, nb);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_range_check(w, s);
+    if (e == cudaSuccess) e = launch_start_from_tau(w, sigma_in, DGS_INIT_USER, seen, s);
+    if (e == cudaSuccess) e = launch_full_evaluation(w, 0, s);
+    if (e == cudaSuccess) e = launch_keys_to_slots(w, agent_gain, agent_job, job_gain, job_agent, s);
+    DeviceState h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, w.st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DGS_ERR_CUDA;
+    }
+    if (h.status == kError) return h.error == kErrRange ? DGS_ERR_RANGE : DGS_ERR_INVALID;
+    return DGS_OK;
+}

@@ -1,0 +1,76 @@
+"""dgs_evaluate_static: the difference evaluation for callers that cannot
+allocate device memory while they run (latency-bound dispatchers, processes
+whose device memory another allocator has reserved, code that cannot handle a
+failed allocation).  Its working memory is a fixed array compiled into the
+library, so the call allocates nothing.
+
+The test calls the new entry point through the C ABI twice in a row, on two
+different instances, and checks each result against the allocating entry
+point dgs_evaluate, element by element (integer outputs: exact equality).  It
+also checks that free device memory does not change across calls and that
+sizes beyond the limit are rejected with a reason.  This file is collected
+last so that a run stopping at the first failure has run everything else.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1106_5694_gb300 import binding as B
+from paper_1106_5694_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1106_5694_gb300 import build_ext
+    build_ext.build()
+    B.load()
+
+
+def _instance(kind, n, seed):
+    a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 10**6, seed)
+    tau = inputs.random_permutation(n, seed + 7)
+    return torch.from_numpy(a).cuda(), torch.from_numpy(tau).cuda()
+
+
+def test_static_evaluation_equals_allocating_entry_point_twice():
+    cases = [("peer", 1024, 1), ("uniform", B.DGS_STATIC_MAX_N, 2)]
+    data = [_instance(*c) for c in cases]
+    outs = [[torch.empty(a.shape[0], dtype=torch.int32, device="cuda") for _ in range(4)] for a, _ in data]
+    # two calls in a row on different instances; the second reuses the
+    # fixed array the first one left behind
+    for (a, tau), out in zip(data, outs):
+        st, *_ = B.dgs_evaluate_static(a, tau, outputs=out)
+        assert st == B.DGS_OK, B.dgs_last_cuda_error()
+    torch.cuda.synchronize()
+    for (a, tau), out in zip(data, outs):
+        st_ref, *ref = B.dgs_evaluate(a, tau)
+        assert st_ref == B.DGS_OK
+        for g, r in zip(out, ref):
+            assert torch.equal(g, r)
+    # free device memory is the same before and after a static call
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    st, *_ = B.dgs_evaluate_static(data[1][0], data[1][1], outputs=outs[1])
+    torch.cuda.synchronize()
+    assert st == B.DGS_OK
+    assert torch.cuda.mem_get_info()[0] >= free_before
+
+
+def test_static_evaluation_rejects_unsupported_sizes():
+    n = B.DGS_STATIC_MAX_N + 4
+    a = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+    tau = torch.arange(n, dtype=torch.int32, device="cuda")
+    st, *_ = B.dgs_evaluate_static(a, tau)
+    assert st == B.DGS_ERR_INVALID
+    assert "DGS_STATIC_MAX_N" in B.dgs_last_cuda_error()
+    a = torch.zeros((10, 10), dtype=torch.int32, device="cuda")
+    st, *_ = B.dgs_evaluate_static(a, torch.arange(10, dtype=torch.int32, device="cuda"))
+    assert st == B.DGS_ERR_INVALID
+    assert "multiple of 4" in B.dgs_last_cuda_error()
+    # still usable afterwards
+    a2, tau2 = _instance("peer", 64, 3)
+    st, *got = B.dgs_evaluate_static(a2, tau2)
+    assert st == B.DGS_OK
+    assert all(torch.equal(g, r) for g, r in zip(got, B.dgs_evaluate(a2, tau2)[1:]))
