@@ -29,6 +29,20 @@ int32_t env_update_policy() {
     }();
     return v;
 }
+int32_t env_phase_timers() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_PHASE_TIMERS");
+        return (e && std::atoi(e) == 1) ? 1 : 0;
+    }();
+    return v;
+}
+int32_t env_short_wraps() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_SHORT_WRAPS");
+        return (e && std::atoi(e) == 1) ? 1 : 0;
+    }();
+    return v;
+}
 int32_t env_controller_mode_cap() {
     static const int32_t v = [] {
         const char* e = std::getenv("DGS_CTL_MODE");
@@ -90,8 +104,8 @@ std::vector<int2> evaluation_items(int32_t n) {
 }
 
 // Carve the workspace; sizes first (base == nullptr), then pointers.
-size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, int32_t** ctl_res,
-             unsigned long long** ctl_edges, uint8_t** ctl_estate, uint8_t** seen, int32_t** a_copy) {
+size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, CtlGlobal* ctl, uint8_t** seen,
+             int32_t** a_copy) {
     const size_t nb = align_up((size_t)n, 128);
     *a_copy = p.need_copy ? ar.take<int32_t>((size_t)n * p.lda) : nullptr;
     w.at = p.need_at ? ar.take<int32_t>((size_t)n * p.ldt + 64) : nullptr;
@@ -110,21 +124,29 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, in
     w.moved = ar.take<uint8_t>(nb);
     w.y_list = ar.take<int32_t>(nb);
     w.rescan_list = ar.take<int32_t>(nb);
+    w.sl_edge = ar.take<unsigned long long>(2 * nb);
+    w.sl_rkey = ar.take<unsigned long long>(2 * nb);
+    w.sl_ru = ar.take<int32_t>(2 * nb);
+    w.sl_rv = ar.take<int32_t>(2 * nb);
     w.ctl_slot = ar.take<int32_t>(2 * nb);
-    w.ctl_rkey = ar.take<unsigned long long>(2 * nb);
-    w.ctl_ru = ar.take<int32_t>(2 * nb);
-    w.ctl_rv = ar.take<int32_t>(2 * nb);
     w.g_row = ar.take<unsigned long long>(nb);
     w.g_col = ar.take<unsigned long long>(nb);
     w.free_a = ar.take<uint8_t>(nb);
     w.free_j = ar.take<uint8_t>(nb);
+    w.g_free_a = ar.take<uint32_t>(nb / 32);
+    w.g_free_j = ar.take<uint32_t>(nb / 32);
+    w.g_dirty = ar.take<uint32_t>(2 * nb / 32);
     w.items = ar.take<int2>(items ? items : 1);
+    w.phase_ns = env_phase_timers() ? ar.take<unsigned long long>(kPtCount) : nullptr;
     w.st = ar.take<DeviceState>(1);
     *seen = ar.take<uint8_t>(4 * nb);
     const int32_t mode = controller_smem_mode(n);
-    *ctl_edges = mode < 2 ? ar.take<unsigned long long>(2 * nb) : nullptr;
-    *ctl_res = mode < 1 ? ar.take<int32_t>(nb) : nullptr;
-    *ctl_estate = mode < 1 ? ar.take<uint8_t>(2 * nb) : nullptr;
+    ctl->edges = mode < 2 ? static_cast<void*>(ar.take<unsigned long long>(2 * nb)) : nullptr;
+    ctl->res = mode < 1 ? ar.take<uint32_t>(nb) : nullptr;
+    ctl->claimed = mode < 1 ? ar.take<uint8_t>(nb) : nullptr;
+    ctl->estate = mode < 1 ? ar.take<uint8_t>(2 * nb) : nullptr;
+    ctl->acc = ar.take<int32_t>(2 * nb);
+    ctl->und = ar.take<int32_t>(4 * nb);
     return ar.used;
 }
 
@@ -134,9 +156,9 @@ struct Solve {
     Arena ar;
     Workspace w{};
     Plan plan;
-    int32_t *ctl_res = nullptr, *a_copy = nullptr;
-    unsigned long long* ctl_edges = nullptr;
-    uint8_t *ctl_estate = nullptr, *seen = nullptr;
+    int32_t* a_copy = nullptr;
+    CtlGlobal ctl{};
+    uint8_t* seen = nullptr;
     std::vector<int2> items;
     int64_t launches = 0;
     explicit Solve(cudaStream_t st) : s(st) {}
@@ -152,7 +174,7 @@ struct Solve {
         if (need_items) items = evaluation_items(n);
         Arena sizing;
         Workspace tmp{};
-        carve(sizing, tmp, plan, n, items.size(), &ctl_res, &ctl_edges, &ctl_estate, &seen, &a_copy);
+        carve(sizing, tmp, plan, n, items.size(), &ctl, &seen, &a_copy);
         plan.bytes = sizing.used;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
         if (e == cudaErrorMemoryAllocation) {
@@ -163,7 +185,7 @@ struct Solve {
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
         ar.size = plan.bytes;
-        carve(ar, w, plan, n, items.size(), &ctl_res, &ctl_edges, &ctl_estate, &seen, &a_copy);
+        carve(ar, w, plan, n, items.size(), &ctl, &seen, &a_copy);
         w.n = n;
         w.lda = plan.lda;
         w.ldt = plan.ldt;
@@ -186,6 +208,9 @@ struct Solve {
         const size_t nb = align_up((size_t)n, 128);
         e = cudaMemsetAsync(w.free_a, 1, nb, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.free_j, 1, nb, s);
+        // bitmaps: bits of agents/jobs >= n are never read
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_a, 0xFF, nb / 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_j, 0xFF, nb / 8, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         if (!items.empty()) {
             e = cudaMemcpyAsync(w.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
@@ -279,6 +304,13 @@ dgs_status map_device_status(const DeviceState& h) {
 dgs_status run_greedy(Solve& S) {
     DGS_CUDA(launch_greedy_pass1(S.w, S.s), "greedy pass 1");
     S.launches += 1;
+    const cudaError_t pe = launch_greedy_persistent(S.w, S.s);
+    if (pe == cudaSuccess) {
+        S.launches += 1;
+        return DGS_OK;
+    }
+    // the cooperative launch was refused: one launch per kernel per round
+    cudaGetLastError();
     const int32_t batch = 8;
     for (int32_t launched = 0; launched <= S.w.n + batch; launched += batch) {
         for (int32_t r = 0; r < batch; ++r) DGS_CUDA(launch_greedy_round(S.w, S.s), "greedy round");
@@ -326,8 +358,9 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.profile) DGS_TRY(ev.begin(stream));
     DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
     if (o.profile) DGS_TRY(ev.end(stream));
-    DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_estate, S.ctl_edges, stream), "controller");
-    S.launches += 4;
+    DGS_CUDA(launch_prepare_edges(S.w, stream), "prepare");
+    DGS_CUDA(launch_controller_impl(S.w, S.ctl, stream), "controller");
+    S.launches += 5;
     DeviceState h;
     const int32_t batch = 4;
     const int64_t max_iterations = 16 * (int64_t)n + 4096;
@@ -342,8 +375,9 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
             DGS_CUDA(launch_mark_rescan(S.w, stream), "mark");
             DGS_CUDA(launch_full_evaluation(S.w, 1, stream), "re-evaluation");
             DGS_CUDA(launch_row_tasks(S.w, stream), "row tasks");
-            DGS_CUDA(launch_controller_impl(S.w, S.ctl_res, S.ctl_estate, S.ctl_edges, stream), "controller");
-            S.launches += 4;
+            DGS_CUDA(launch_prepare_edges(S.w, stream), "prepare");
+            DGS_CUDA(launch_controller_impl(S.w, S.ctl, stream), "controller");
+            S.launches += 5;
         }
     }
     if (!ended) {
@@ -353,6 +387,14 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
     S.launches += 1;
     DGS_TRY(S.read_state(&h));
+    if (S.w.phase_ns) {  // test/diagnostic output only
+        unsigned long long ph[kPtCount];
+        if (cudaMemcpy(ph, S.w.phase_ns, sizeof(ph), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            fprintf(stderr, "[dgs phases] greedy ns: match %llu bar1 %llu check %llu scan %llu bar2 %llu scanmax %llu | "
+                            "controller cycles: entry %llu top %llu pass1 %llu pass2 %llu und %llu post %llu event %llu sweeps %llu\n",
+                    ph[0], ph[1], ph[2], ph[3], ph[4], ph[5], ph[8], ph[9], ph[10], ph[11], ph[12], ph[13], ph[14], ph[15]);
+        }
+    }
     const dgs_status status = map_device_status(h);
     *objective_out = h.f;
     if (stats) {

@@ -40,6 +40,8 @@ struct DeviceState {
     int32_t greedy_matched;  // the last match kernel matched >= 1 pair
     int32_t update_policy;   // 0: by cost, 1: always full evaluation, 2: always row tasks
     int32_t pad1;
+    uint32_t bar_count;      // grid barrier of cooperative launches: arrivals
+    uint32_t bar_gen;        //   and generation
     int64_t f;               // current objective
     int64_t f_initial;
     int64_t swaps;           // committed exchanges
@@ -66,19 +68,30 @@ struct Workspace {
     uint8_t* in_y; uint8_t* moved;        // jobs changed / agents moved in the last event
     int32_t* y_list;                      // jobs changed in the last event
     int32_t* rescan_list;                 // rows to re-evaluate fully
-    // controller: per edge position (priority order) the slot, and the
-    // re-evaluated candidate of that slot (key, exchange agents)
-    int32_t* ctl_slot;
-    unsigned long long* ctl_rkey;
-    int32_t* ctl_ru;
-    int32_t* ctl_rv;
+    // per slot (agent slots 0..n-1, job slots n..2n-1): its edge word (0 when
+    // it has no candidate) and its re-evaluated candidate (key, exchange agents)
+    unsigned long long* sl_edge;
+    unsigned long long* sl_rkey;
+    int32_t* sl_ru;
+    int32_t* sl_rv;
+    int32_t* ctl_slot;  // controller: slot of each edge position (priority order)
     // greedy start
     unsigned long long* g_row;  // best free job per agent   (biased value, ~j)
     unsigned long long* g_col;  // best free agent per job   (biased value, ~i)
     uint8_t* free_a; uint8_t* free_j;
+    uint32_t* g_free_a; uint32_t* g_free_j;  // free sets as bitmaps (persistent greedy)
+    uint32_t* g_dirty;                       // owners to rescan this round (persistent greedy)
     // evaluation work items (row-block, first column tile) of the tile-pair sweep
     int2* items; int32_t item_count; int32_t pad2;
     DeviceState* st;
+    unsigned long long* phase_ns;  // optional phase timers (DGS_PHASE_TIMERS=1), else null
+};
+
+// Phase timer slots.
+enum : int32_t {
+    kPtGreedyMatch = 0, kPtGreedyBar1, kPtGreedyCheck, kPtGreedyScan, kPtGreedyBar2, kPtGreedyScanMax,
+    kPtCtlEntry = 8, kPtCtlTop, kPtCtlPass1, kPtCtlPass2, kPtCtlUnd, kPtCtlPost, kPtCtlEvent, kPtCtlSweeps,
+    kPtCount = 16
 };
 
 // ------------------------------------------------------------- key packing
@@ -146,23 +159,67 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Grid-wide barrier for cooperative launches (every CTA co-resident).  The
+// wait is bounded in time; returns false (block-uniform) on timeout.
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;
+__device__ __forceinline__ bool grid_barrier(DeviceState* st) {
+    __shared__ int32_t s_bar_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&st->bar_gen) : "memory");
+        uint32_t prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&st->bar_count) : "memory");
+        int32_t ok = 1;
+        if (prev == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&st->bar_count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->bar_gen) : "memory");
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            for (;;) {
+                uint32_t cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&st->bar_gen) : "memory");
+                if (cur != g) break;
+                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) { ok = 0; break; }
+                __nanosleep(20);
+            }
+        }
+        s_bar_ok = ok;
+    }
+    __syncthreads();
+    return s_bar_ok != 0;
+}
+
 // ------------------------------------------------------ host-side launchers
 // Each returns the launch error (cudaSuccess on success).
 cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s);
 cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s);
+// All greedy rounds in one cooperative launch; returns cudaErrorNotSupported
+// (nothing launched) when the grid cannot be co-resident.
+cudaError_t launch_greedy_persistent(const Workspace& w, cudaStream_t s);
 cudaError_t launch_range_check(const Workspace& w, cudaStream_t s);
 cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, int32_t mode, uint8_t* seen,
                                   cudaStream_t s);
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s);
-cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_estate, unsigned long long* g_edges,
-                                   cudaStream_t s);
+// Controller scratch in global memory (the parts that do not live in shared
+// memory for this n; null otherwise) and its work lists.
+struct CtlGlobal {
+    uint32_t* res;
+    uint8_t* claimed;
+    uint8_t* estate;
+    void* edges;
+    int32_t* acc;
+    int32_t* und;
+};
+cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s);
 int32_t controller_smem_mode(int32_t n);
 size_t controller_smem_bytes(int32_t n);
 size_t full_evaluation_smem_bytes();
 int32_t evaluation_strip();
 cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s);
+cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
 
@@ -195,5 +252,9 @@ int32_t env_update_policy();
 // Store the text returned by dgs_last_cuda_error() for this thread.
 void set_last_error(const char* msg);
 int32_t env_controller_mode_cap();
+// DGS_SHORT_WRAPS=1 shortens the controller's key and stamp periods so that
+// tests reach their wrap-around paths.
+int32_t env_short_wraps();
+int32_t env_phase_timers();
 
 }  // namespace dgs

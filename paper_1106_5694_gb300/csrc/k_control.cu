@@ -32,17 +32,14 @@ namespace dgs {
 namespace {
 
 constexpr int kCtlThreads = 1024;
-constexpr int32_t kInf = 0x7fffffff;
-constexpr int32_t kClaimed = -1;  // reservation value of an agent claimed this sweep
-enum : uint8_t { kDead = 0, kLive = 1, kAcc = 2, kRej = 3 };
 
-// Edge word: agent u (bits 0..16), agent v (17..33), applies (34): its
-// exchange raises f under the current sigma, fresh (35): re-evaluated in this
-// launch.  Edge positions follow slot priority, so a position is a priority.
+// Slot edge word: agent u (bits 0..16), agent v (17..33), applies (34): its
+// exchange raises f under the current sigma, valid (36): set on every edge
+// (0 means "no candidate").  Edge positions follow slot priority, so a position is a priority.
 constexpr unsigned long long kApplies = 1ull << 34;
-constexpr unsigned long long kFresh = 1ull << 35;
+constexpr unsigned long long kValid = 1ull << 36;  // a slot's edge word is never 0
 __device__ __forceinline__ unsigned long long edge_word(int32_t u, int32_t v) {
-    return (unsigned long long)(uint32_t)u | ((unsigned long long)(uint32_t)v << 17);
+    return (unsigned long long)(uint32_t)u | ((unsigned long long)(uint32_t)v << 17) | kValid;
 }
 __device__ __forceinline__ int32_t edge_u(unsigned long long e) { return (int32_t)(e & 0x1FFFFu); }
 __device__ __forceinline__ int32_t edge_v(unsigned long long e) { return (int32_t)((e >> 17) & 0x1FFFFu); }
@@ -82,113 +79,166 @@ __device__ __forceinline__ int32_t block_scan(int32_t x, int32_t* warp_sums, int
     return r;
 }
 
+// Controller scratch.  res: per agent, the reservation key of the current DR
+// round; claimed: per agent, the stamp of the sweep that claimed it; estate:
+// per edge position (alive / applies / fresh bits); E: per edge position, the
+// two agents of its exchange.  The undecided and accepted lists are two-tier:
+// the first `cap` entries in shared memory (16-bit positions), the rest in
+// global memory.
 struct CtlScratch {
-    int32_t* res;               // per agent: reservation (lowest live priority) or kClaimed
-    uint8_t* estate;            // per edge position
-    unsigned long long* edges;  // per edge position
+    uint32_t* res;
+    uint8_t* claimed;
+    uint8_t* estate;
+    void* edges;
+    int32_t* acc_g;  // accepted positions beyond the shared-memory part
+    int32_t* und_g;  // undecided positions beyond it (two lists of 2n)
 };
 
-// Switching loop (see the file comment).  smem_mode 2: edges, reservations
-// and edge states in shared memory; 1: edges in global memory; 0: all global.
-__global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g) {
+enum : uint8_t { kAlive = 1, kAppl = 2, kFreshBit = 4, kAccBit = 8 };
+
+struct TwoTier {
+    uint16_t* s;
+    int32_t cap;
+    int32_t* g;
+    __device__ __forceinline__ void put(int32_t i, int32_t v) const {
+        if (i < cap) s[i] = (uint16_t)v;
+        else g[i - cap] = v;
+    }
+    __device__ __forceinline__ int32_t get(int32_t i) const { return i < cap ? (int32_t)s[i] : g[i - cap]; }
+};
+
+// Reservation key of edge position p in DR round r: each round's keys are
+// smaller than every earlier round's, so reservations never need clearing
+// (the array is reset once per key period).
+constexpr uint32_t kPosBits = 18, kPosMask = (1u << kPosBits) - 1u, kRoundSpanMax = 1u << 14;
+__device__ __forceinline__ uint32_t round_base(uint32_t r, uint32_t span) {
+    return (span - 1u - (r & (span - 1u))) << kPosBits;
+}
+
+template <typename EdgeT>
+struct Codec;
+template <>
+struct Codec<uint32_t> {  // n <= 65535
+    static __device__ __forceinline__ uint32_t make(int32_t u, int32_t v) { return (uint32_t)u | ((uint32_t)v << 16); }
+    static __device__ __forceinline__ int32_t u(uint32_t e) { return (int32_t)(e & 0xFFFFu); }
+    static __device__ __forceinline__ int32_t v(uint32_t e) { return (int32_t)(e >> 16); }
+};
+template <>
+struct Codec<unsigned long long> {
+    static __device__ __forceinline__ unsigned long long make(int32_t u, int32_t v) {
+        return (unsigned long long)(uint32_t)u | ((unsigned long long)(uint32_t)v << 32);
+    }
+    static __device__ __forceinline__ int32_t u(unsigned long long e) { return (int32_t)(uint32_t)e; }
+    static __device__ __forceinline__ int32_t v(unsigned long long e) { return (int32_t)(e >> 32); }
+};
+
+constexpr int kUnroll = 4;
+
+// Switching loop (see the file comment).
+// span: reservation-key period (power of two <= kRoundSpanMax); stamp_wrap:
+// claim-stamp period (<= 255).  Both are shortened only by a test knob.
+// list_cap: entries of each two-tier list held in shared memory.
+template <typename EdgeT>
+__global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
+                                                                   uint32_t span, uint32_t stamp_wrap,
+                                                                   int32_t list_cap) {
+    using C = Codec<EdgeT>;
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int32_t warp_sums[33];
-    __shared__ int32_t s_L, s_live, s_stop, s_acc, s_app, s_y, s_sweeps, s_event;
-    __shared__ unsigned long long s_gain;
+    __shared__ int32_t s_L, s_live, s_stop, s_acc, s_und, s_und2, s_app, s_y, s_sweeps, s_event;
+    __shared__ int32_t s_max_sweeps, s_trace_cap;
+    __shared__ uint32_t s_round;
+    __shared__ uint32_t s_stamp;
+    __shared__ unsigned long long s_gain, s_deadline;
+    __shared__ long long s_f;
 
     const int32_t n = w.n;
     const int tid = threadIdx.x;
-    CtlScratch c = g;
+    uint32_t* res = g.res;
+    uint8_t* claimed = g.claimed;
+    uint8_t* estate = g.estate;
+    EdgeT* E = static_cast<EdgeT*>(g.edges);
+    uint16_t* lists_s = nullptr;
+    uint16_t* slot_s = nullptr;  // slot of each edge position (shared-memory modes)
     if (smem_mode >= 1) {
-        c.res = reinterpret_cast<int32_t*>(smem_raw);
-        c.estate = smem_raw + 4 * (size_t)n;
-        if (smem_mode == 2)
-            c.edges = reinterpret_cast<unsigned long long*>(smem_raw + ((4 * (size_t)n + 2 * (size_t)n + 15) & ~(size_t)15));
+        size_t off = 0;
+        res = reinterpret_cast<uint32_t*>(smem_raw);
+        off += 4 * (size_t)n;
+        if (smem_mode == 2) {
+            E = reinterpret_cast<EdgeT*>(smem_raw + off);
+            off += sizeof(EdgeT) * 2 * (size_t)n;
+        }
+        lists_s = reinterpret_cast<uint16_t*>(smem_raw + off);
+        off += 2 * 3 * (size_t)list_cap;
+        slot_s = reinterpret_cast<uint16_t*>(smem_raw + off);
+        off += 2 * 2 * (size_t)n;
+        claimed = smem_raw + off;
+        off += (size_t)n;
+        estate = smem_raw + off;
     }
-    int32_t* res = c.res;
-    uint8_t* estate = c.estate;
-    unsigned long long* E = c.edges;
+    const int32_t cap = lists_s ? list_cap : 0;
+    TwoTier accl{lists_s, cap, g.acc_g};
+    TwoTier und_a{lists_s ? lists_s + list_cap : nullptr, cap, g.und_g};
+    TwoTier und_b{lists_s ? lists_s + 2 * list_cap : nullptr, cap, g.und_g + 2 * n};
+    unsigned long long* pt = (tid == 0) ? w.phase_ns : nullptr;
+    long long tp = clock64();
+#define DGS_CT(slot)                                            \
+    if (pt) {                                                   \
+        const long long now = clock64();                        \
+        atomicAdd(pt + (slot), (unsigned long long)(now - tp)); \
+        tp = now;                                               \
+    }
 
     // ---------------------------------------------------------------- entry
+    // The slot refresh and the per-slot edge data were prepared by the grid
+    // (prepare_edges_kernel); here the edges are listed in priority order.
     {
-        const int32_t yc = st->y_count;
-        for (int32_t t = tid; t < yc; t += kCtlThreads) {
-            const int32_t j = w.y_list[t];
-            w.in_y[j] = 0;
-            w.moved[w.sigma[j]] = 0;
-        }
-        // re-evaluation of the slots not in C: read the current row keys
         for (int32_t i = tid; i < n; i += kCtlThreads) {
-            if (!w.in_ca[i]) {
-                const unsigned long long ka = w.key_a[w.tau[i]];
-                w.ag_gain[i] = ka ? key_gain(ka) : 0;
-                w.ag_job[i] = ka ? key_index(ka) : -1;
-            }
-            if (!w.in_cj[i]) {
-                const unsigned long long kj = w.key_j[i];
-                w.jb_gain[i] = kj ? key_gain(kj) : 0;
-                w.jb_agent[i] = kj ? key_index(kj) : -1;
-            }
-            res[i] = kInf;
+            res[i] = 0xFFFFFFFFu;
+            claimed[i] = 0;
         }
         if (tid == 0) {
             st->need_update = 0;
             st->y_count = 0;
             s_sweeps = st->sweeps;
+            s_max_sweeps = st->max_sweeps;
+            s_deadline = st->deadline_ns;
+            s_trace_cap = st->trace_capacity;
+            s_f = st->f;
+            s_round = 0;
+            s_stamp = 0;
         }
-        __syncthreads();
-        // edge list in priority order: each thread owns a contiguous slot range
-        const int32_t per = (2 * n + kCtlThreads - 1) / kCtlThreads;
-        const int32_t t0 = min(2 * n, tid * per), t1 = min(2 * n, t0 + per);
-        int32_t cnt = 0;
-        for (int32_t t = t0; t < t1; ++t) cnt += (t < n) ? (w.ag_gain[t] > 0) : (w.jb_gain[t - n] > 0);
-        int32_t total;
-        int32_t pos = block_scan(cnt, warp_sums, &total);
-        for (int32_t t = t0; t < t1; ++t) {
-            int32_t u, v;
-            if (t < n) {
-                if (w.ag_gain[t] <= 0) continue;
-                u = t;
-                v = w.sigma[w.ag_job[t]];
-            } else {
-                if (w.jb_gain[t - n] <= 0) continue;
-                u = w.sigma[t - n];
-                v = w.jb_agent[t - n];
+        // slots t = c * 1024 + tid, chunk by chunk in priority order; the
+        // slot words of several chunks are loaded before they are scanned
+        int32_t base = 0;
+        for (int32_t c0 = 0; c0 < 2 * n; c0 += 4 * kCtlThreads) {
+            unsigned long long ew[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t t = c0 + k * kCtlThreads + tid;
+                ew[k] = t < 2 * n ? w.sl_edge[t] : 0ull;
             }
-            w.ctl_slot[pos] = t;
-            E[pos] = edge_word(u, v);
-            ++pos;
-        }
-        if (tid == 0) { s_L = total; s_live = total; }
-        __syncthreads();
-        const int32_t L = s_L;
-        // current gains and the re-evaluation outcome of every edge's slot
-        // (keys do not change while no exchange is committed)
-#pragma unroll 4
-        for (int32_t p = tid; p < L; p += kCtlThreads) {
-            const unsigned long long e = E[p];
-            const int32_t t = w.ctl_slot[p];
-            unsigned long long key;
-            int32_t ru, rv;
-            if (t < n) {
-                key = w.key_a[w.tau[t]];
-                ru = t;
-                rv = key ? w.sigma[key_index(key)] : t;
-            } else {
-                key = w.key_j[t - n];
-                ru = w.sigma[t - n];
-                rv = key ? key_index(key) : ru;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t t = c0 + k * kCtlThreads + tid;
+                const int32_t has = ew[k] != 0ull;
+                int32_t total;
+                const int32_t pos = base + block_scan(has, warp_sums, &total);
+                if (has) {
+                    w.ctl_slot[pos] = t;
+                    if (slot_s) slot_s[pos] = (uint16_t)t;
+                    E[pos] = C::make(edge_u(ew[k]), edge_v(ew[k]));
+                    estate[pos] = kAlive | ((ew[k] & kApplies) ? kAppl : 0);
+                }
+                base += total;
             }
-            w.ctl_rkey[p] = key;
-            w.ctl_ru[p] = ru;
-            w.ctl_rv[p] = rv;
-            E[p] = e | (exchange_gain(w, edge_u(e), edge_v(e)) > 0 ? kApplies : 0ull);
-            estate[p] = kLive;
         }
+        if (tid == 0) { s_L = base; s_live = base; }
         __syncthreads();
     }
+    DGS_CT(kPtCtlEntry)
 
     // ------------------------------------------------------------- sweeps
     // Quiet sweeps turn at least one stale slot into a fresh one each, so one
@@ -202,8 +252,8 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
             if (s_live == 0) {
                 st->status = kDone;
                 stop = 1;
-            } else if ((st->max_sweeps > 0 && s_sweeps >= st->max_sweeps) ||
-                       (st->deadline_ns != 0 && globaltimer_ns() > st->deadline_ns)) {
+            } else if ((s_max_sweeps > 0 && s_sweeps >= s_max_sweeps) ||
+                       (s_deadline != 0 && globaltimer_ns() > s_deadline)) {
                 st->status = kTimeout;
                 stop = 1;
             } else if (quiet > 2 * n + 1) {
@@ -212,66 +262,169 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
                 stop = 1;
             }
             s_stop = stop;
-            s_acc = 0; s_app = 0; s_y = 0; s_gain = 0ull; s_event = 0;
+            s_acc = 0; s_und = 0; s_app = 0; s_y = 0; s_gain = 0ull; s_event = 0;
+            s_stamp = s_stamp + 1u;
         }
         __syncthreads();
+        DGS_CT(kPtCtlTop)
         if (s_stop) break;
-        // CC (Algorithm 4) by deterministic reservations
-        for (uint32_t round = 0;; ++round) {
-            for (int32_t p = tid; p < L; p += kCtlThreads) {
-                if (estate[p] != kLive) continue;
-                const unsigned long long e = E[p];
-                const int32_t u = edge_u(e), v = edge_v(e);
-                if (p < res[u]) atomicMin(&res[u], p);
-                if (p < res[v]) atomicMin(&res[v], p);
-            }
+        if (pt) atomicAdd(pt + kPtCtlSweeps, 1ull);
+        if (s_stamp >= stamp_wrap) {  // claim stamps wrap: clear them once
+            for (int32_t i = tid; i < n; i += kCtlThreads) claimed[i] = 0;
             __syncthreads();
-            int32_t acc = 0, ev = 0;
-            for (int32_t p = tid; p < L; p += kCtlThreads) {
-                if (estate[p] != kLive) continue;
-                const unsigned long long e = E[p];
-                const int32_t u = edge_u(e), v = edge_v(e);
-                if (res[u] == p && res[v] == p) {
-                    estate[p] = kAcc;
-                    res[u] = kClaimed;
-                    res[v] = kClaimed;
-                    ++acc;
-                    ev |= (e & kApplies) ? 1 : 0;
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(w.ctl_rkey + p));
-                }
-            }
-            if (acc) atomicAdd(&s_acc, acc);
-            if (ev) s_event = 1;
+            if (tid == 0) s_stamp = 1;
             __syncthreads();
-            int32_t any = 0;
-            for (int32_t p = tid; p < L; p += kCtlThreads) {
-                if (estate[p] != kLive) continue;
-                const unsigned long long e = E[p];
-                const int32_t u = edge_u(e), v = edge_v(e);
-                if (res[u] == kClaimed || res[v] == kClaimed) {
-                    estate[p] = kRej;
-                } else {
-                    res[u] = kInf;
-                    res[v] = kInf;
-                    any = 1;
-                }
+        }
+        if ((s_round & (span - 1u)) == 0u && s_round != 0u) {  // reservation keys wrap
+            for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
+            __syncthreads();
+        }
+        const uint8_t stamp = (uint8_t)s_stamp;
+        // CC (Algorithm 4) by deterministic reservations.  Round 1 over all
+        // edges: reserve both agents; then each edge is accepted (holds both),
+        // rejected (lost an agent to an edge that holds both of its own) or
+        // undecided (later rounds, on the undecided list only).
+        const uint32_t kb = round_base(s_round, span);
+        for (int32_t p0 = tid; p0 < L; p0 += kUnroll * kCtlThreads) {
+            uint8_t es[kUnroll];
+            EdgeT e[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int32_t p = p0 + k * kCtlThreads;
+                es[k] = p < L ? estate[p] : (uint8_t)0;
+                e[k] = (es[k] & kAlive) ? E[p] : (EdgeT)0;
             }
-            if (!__syncthreads_or(any)) break;
-            if (round > (uint32_t)(L + 2)) {  // each round accepts the first live edge
-                if (tid == 0) { st->error = kErrInternal; st->status = kError; }
-                return;
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                if (!(es[k] & kAlive)) continue;
+                const uint32_t key = kb | (uint32_t)(p0 + k * kCtlThreads);
+                const int32_t u = C::u(e[k]), v = C::v(e[k]);
+                if (key < res[u]) atomicMin(&res[u], key);
+                if (key < res[v]) atomicMin(&res[v], key);
             }
         }
+        __syncthreads();
+        DGS_CT(kPtCtlPass1)
+        {
+            int32_t ev = 0;
+            for (int32_t p0 = tid; p0 < L; p0 += kUnroll * kCtlThreads) {
+                uint8_t es[kUnroll];
+                EdgeT e[kUnroll];
+                uint32_t ru[kUnroll], rv[kUnroll];
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int32_t p = p0 + k * kCtlThreads;
+                    es[k] = p < L ? estate[p] : (uint8_t)0;
+                    e[k] = (es[k] & kAlive) ? E[p] : (EdgeT)0;
+                }
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    ru[k] = (es[k] & kAlive) ? res[C::u(e[k])] : 0u;
+                    rv[k] = (es[k] & kAlive) ? res[C::v(e[k])] : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    if (!(es[k] & kAlive)) continue;
+                    const int32_t p = p0 + k * kCtlThreads;
+                    const uint32_t key = kb | (uint32_t)p;
+                    if (ru[k] == key && rv[k] == key) {
+                        claimed[C::u(e[k])] = stamp;
+                        claimed[C::v(e[k])] = stamp;
+                        accl.put(atomicAdd(&s_acc, 1), p);
+                        if (slot_s) {  // the re-evaluation record of its slot
+                            const int32_t t = slot_s[p];
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rkey + t));
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
+                        }
+                        ev |= (es[k] & kAppl) ? 1 : 0;
+                    } else {
+                        bool rej = false;
+                        if (ru[k] != key) {
+                            const EdgeT f = E[ru[k] & kPosMask];
+                            rej = res[C::u(f)] == ru[k] && res[C::v(f)] == ru[k];
+                        }
+                        if (!rej && rv[k] != key) {
+                            const EdgeT f = E[rv[k] & kPosMask];
+                            rej = res[C::u(f)] == rv[k] && res[C::v(f)] == rv[k];
+                        }
+                        if (!rej) und_a.put(atomicAdd(&s_und, 1), p);
+                    }
+                }
+            }
+            if (ev) s_event = 1;
+            if (tid == 0) s_round = s_round + 1u;
+        }
+        __syncthreads();
+        DGS_CT(kPtCtlPass2)
+        // later rounds on the undecided edges only
+        {
+            TwoTier cur = und_a, nxt = und_b;
+            for (uint32_t guard = 0; s_und > 0; ++guard) {
+                if ((s_round & (span - 1u)) == 0u) {  // reservation keys wrap
+                    for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
+                    __syncthreads();
+                }
+                const int32_t m = s_und;
+                const uint32_t kb2 = round_base(s_round, span);
+                for (int32_t q = tid; q < m; q += kCtlThreads) {
+                    const int32_t p = cur.get(q);
+                    const EdgeT e = E[p];
+                    const int32_t u = C::u(e), v = C::v(e);
+                    if (claimed[u] == stamp || claimed[v] == stamp) continue;
+                    const uint32_t key = kb2 | (uint32_t)p;
+                    atomicMin(&res[u], key);
+                    atomicMin(&res[v], key);
+                }
+                if (tid == 0) s_und2 = 0;
+                __syncthreads();
+                int32_t ev = 0;
+                for (int32_t q = tid; q < m; q += kCtlThreads) {
+                    const int32_t p = cur.get(q);
+                    const EdgeT e = E[p];
+                    const int32_t u = C::u(e), v = C::v(e);
+                    if (claimed[u] == stamp || claimed[v] == stamp) continue;  // rejected
+                    const uint32_t key = kb2 | (uint32_t)p;
+                    if (res[u] == key && res[v] == key) {
+                        claimed[u] = stamp;
+                        claimed[v] = stamp;
+                        accl.put(atomicAdd(&s_acc, 1), p);
+                        ev |= (estate[p] & kAppl) ? 1 : 0;
+                    } else {
+                        nxt.put(atomicAdd(&s_und2, 1), p);
+                    }
+                }
+                if (ev) s_event = 1;
+                __syncthreads();
+                if (tid == 0) {
+                    s_und = s_und2;
+                    s_round = s_round + 1u;
+                    if (guard > (uint32_t)(L + 2)) {  // each round accepts the first live edge
+                        st->error = kErrInternal;
+                        st->status = kError;
+                        s_und = 0;
+                    }
+                }
+                const TwoTier tmp = cur;
+                cur = nxt;
+                nxt = tmp;
+                __syncthreads();
+            }
+        }
+        DGS_CT(kPtCtlUnd)
+        if (st->status != kRunning) break;
+        const int32_t nacc = s_acc;
         if (s_event) {
             // parallel switch: accepted exchanges are agent-disjoint; those
             // that raise f under the current sigma commit
             int32_t my_app = 0;
             long long my_gain = 0;
-            for (int32_t p = tid; p < L; p += kCtlThreads) {
-                if (estate[p] != kAcc) continue;
-                const unsigned long long e = E[p];
-                if (!(e & kApplies)) continue;
-                const int32_t u = edge_u(e), v = edge_v(e);
+            for (int32_t q = tid; q < nacc; q += kCtlThreads) {
+                const int32_t p = accl.get(q);
+                estate[p] |= kAccBit;
+                if (!(estate[p] & kAppl)) continue;
+                const EdgeT e = E[p];
+                const int32_t u = C::u(e), v = C::v(e);
                 const int32_t ju = w.tau[u], jv = w.tau[v];
                 const int32_t x1 = w.a[(size_t)u * w.lda + jv];
                 const int32_t x2 = w.a[(size_t)v * w.lda + ju];
@@ -283,9 +436,9 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
                 w.diag[jv] = x1;
                 w.diag[ju] = x2;
                 ++my_app;
-                const int32_t q = atomicAdd(&s_y, 2);
-                w.y_list[q] = ju;
-                w.y_list[q + 1] = jv;
+                const int32_t qy = atomicAdd(&s_y, 2);
+                w.y_list[qy] = ju;
+                w.y_list[qy + 1] = jv;
                 w.in_y[ju] = 1;
                 w.in_y[jv] = 1;
                 w.moved[u] = 1;
@@ -300,21 +453,23 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
                 w.in_cj[i] = 0;
             }
             __syncthreads();
-            // record C (the rejected slots keep their candidates, reading R4)
+            // record C: every live slot that was not accepted keeps its
+            // candidate (reading R4)
             for (int32_t p = tid; p < L; p += kCtlThreads) {
-                if (estate[p] != kRej) continue;
+                const uint8_t es = estate[p];
+                if (!(es & kAlive) || (es & kAccBit)) continue;
                 const int32_t t = w.ctl_slot[p];
                 if (t < n) w.in_ca[t] = 1;
                 else w.in_cj[t - n] = 1;
             }
             if (tid == 0) {
                 const int32_t sw = s_sweeps;
-                st->f += (long long)s_gain;
+                s_f += (long long)s_gain;
                 st->swaps += s_app;
-                if (sw < st->trace_capacity) {
-                    if (st->trace_accepted) st->trace_accepted[sw] = s_acc;
+                if (sw < s_trace_cap) {
+                    if (st->trace_accepted) st->trace_accepted[sw] = nacc;
                     if (st->trace_applied) st->trace_applied[sw] = s_app;
-                    if (st->trace_objective) st->trace_objective[sw] = st->f;
+                    if (st->trace_objective) st->trace_objective[sw] = s_f;
                 }
                 s_sweeps = sw + 1;
                 st->events += 1;
@@ -323,51 +478,103 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
                 st->need_update = 1;
                 st->phase = kPhaseRefreshAll;
             }
+            DGS_CT(kPtCtlEvent)
             break;
         }
         // quiet sweep: sigma unchanged, so the keys are current.  Accepted
-        // slots are re-evaluated (their precomputed outcome); rejected slots
-        // stay in C with their candidates for the next sweep.
+        // slots are re-evaluated (their precomputed outcome); the others stay
+        // in C with their candidates for the next sweep.
         int32_t died = 0;
-        for (int32_t p = tid; p < L; p += kCtlThreads) {
-            const uint8_t es = estate[p];
-            if (es == kDead) continue;
-            const unsigned long long e = E[p];
-            res[edge_u(e)] = kInf;
-            res[edge_v(e)] = kInf;
-            if (es == kRej) {
-                estate[p] = kLive;
-            } else if (es == kAcc) {
-                const int32_t t = w.ctl_slot[p];
-                const unsigned long long key = w.ctl_rkey[p];
-                const int32_t gain = key ? key_gain(key) : 0;
-                const int32_t target = key ? key_index(key) : -1;
-                if (t < n) { w.ag_gain[t] = gain; w.ag_job[t] = target; }
-                else { w.jb_gain[t - n] = gain; w.jb_agent[t - n] = target; }
-                if (key) {
-                    E[p] = edge_word(w.ctl_ru[p], w.ctl_rv[p]) | kApplies | kFresh;
-                    estate[p] = kLive;
-                } else {
-                    estate[p] = kDead;
-                    ++died;
-                }
+        for (int32_t q = tid; q < nacc; q += kCtlThreads) {
+            const int32_t p = accl.get(q);
+            const int32_t t = slot_s ? (int32_t)slot_s[p] : w.ctl_slot[p];
+            const unsigned long long key = w.sl_rkey[t];
+            const int32_t gain = key ? key_gain(key) : 0;
+            const int32_t target = key ? key_index(key) : -1;
+            if (t < n) { w.ag_gain[t] = gain; w.ag_job[t] = target; }
+            else { w.jb_gain[t - n] = gain; w.jb_agent[t - n] = target; }
+            if (gain > 0) {
+                E[p] = C::make(w.sl_ru[t], w.sl_rv[t]);
+                estate[p] = kAlive | kAppl | kFreshBit;
+            } else {
+                estate[p] = 0;
+                ++died;
             }
         }
         if (died) atomicSub(&s_live, died);
-        if (tid == 0) {
+        if (tid == 0 && s_sweeps < s_trace_cap) {
             const int32_t sw = s_sweeps;
-            if (sw < st->trace_capacity) {
-                if (st->trace_accepted) st->trace_accepted[sw] = s_acc;
-                if (st->trace_applied) st->trace_applied[sw] = 0;
-                if (st->trace_objective) st->trace_objective[sw] = st->f;
-            }
-            s_sweeps = sw + 1;
+            if (st->trace_accepted) st->trace_accepted[sw] = nacc;
+            if (st->trace_applied) st->trace_applied[sw] = 0;
+            if (st->trace_objective) st->trace_objective[sw] = s_f;
         }
+        if (tid == 0) s_sweeps = s_sweeps + 1;
         __syncthreads();
+        DGS_CT(kPtCtlPost)
     }
+#undef DGS_CT
     if (tid == 0) {
         st->sweeps = s_sweeps;
         st->edge_count = s_live;
+        st->f = s_f;
+    }
+}
+
+// Before each controller launch: clear the marks of the last event, re-
+// evaluate every slot not in C from the current row keys (reading R4), and
+// for every slot with a candidate (delta > 0) record its edge (the agents of
+// its exchange under the current sigma, and whether that exchange raises f
+// now).  Also record each slot's re-evaluated candidate, which stays valid
+// for as long as no exchange is committed.  One thread per slot.
+__global__ void prepare_edges_kernel(Workspace w) {
+    DeviceState* st = w.st;
+    if (st->status != kRunning) return;
+    const int32_t n = w.n;
+    const int32_t stride = gridDim.x * blockDim.x;
+    const int32_t yc = st->y_count;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < yc; t += stride) {
+        const int32_t j = w.y_list[t];
+        w.in_y[j] = 0;
+        w.moved[w.sigma[j]] = 0;
+    }
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * n; t += stride) {
+        unsigned long long key;
+        int32_t ru, rv, gain, target;
+        bool in_c;
+        if (t < n) {
+            key = w.key_a[w.tau[t]];
+            ru = t;
+            rv = key ? w.sigma[key_index(key)] : t;
+            in_c = w.in_ca[t];
+            if (!in_c) {
+                w.ag_gain[t] = key ? key_gain(key) : 0;
+                w.ag_job[t] = key ? key_index(key) : -1;
+            }
+            gain = in_c ? w.ag_gain[t] : (key ? key_gain(key) : 0);
+            target = in_c ? w.ag_job[t] : (key ? key_index(key) : -1);
+        } else {
+            const int32_t j = t - n;
+            key = w.key_j[j];
+            ru = w.sigma[j];
+            rv = key ? key_index(key) : ru;
+            in_c = w.in_cj[j];
+            if (!in_c) {
+                w.jb_gain[j] = key ? key_gain(key) : 0;
+                w.jb_agent[j] = key ? key_index(key) : -1;
+            }
+            gain = in_c ? w.jb_gain[j] : (key ? key_gain(key) : 0);
+            target = in_c ? w.jb_agent[j] : (key ? key_index(key) : -1);
+        }
+        w.sl_rkey[t] = key;
+        w.sl_ru[t] = ru;
+        w.sl_rv[t] = rv;
+        unsigned long long e = 0ull;
+        if (gain > 0) {
+            const int32_t u = (t < n) ? t : w.sigma[t - n];
+            const int32_t v = (t < n) ? w.sigma[target] : target;
+            e = edge_word(u, v) | (exchange_gain(w, u, v) > 0 ? kApplies : 0ull);
+        }
+        w.sl_edge[t] = e;
     }
 }
 
@@ -520,34 +727,60 @@ __global__ void finish_kernel(Workspace w, int32_t* sigma_out) {
 
 }  // namespace
 
-// Controller scratch placement (bytes of dynamic shared memory per mode).
+// Controller scratch placement.  Mode 2: reservations, 32-bit edges, list
+// heads, claims and edge states in shared memory; mode 1: edges in global
+// memory; mode 0: everything in global memory.
 constexpr size_t kCtlSmemLimit = 227 * 1024 - 1024;
 
+static size_t ctl_fixed_bytes(int32_t n, int32_t mode) {
+    // res (4n) + slot of each position (4n) + claimed (n) + estate (2n) [+ 32-bit edges (8n)]
+    return 11 * (size_t)n + (mode == 2 ? 8 * (size_t)n : 0);
+}
+
 int32_t controller_smem_mode(int32_t n) {
-    const size_t all = ((6 * (size_t)n + 15) & ~(size_t)15) + 16 * (size_t)n;
     int32_t mode = 0;
-    if (all <= kCtlSmemLimit) mode = 2;
-    else if (6 * (size_t)n <= kCtlSmemLimit) mode = 1;
+    if (n <= 32767 && ctl_fixed_bytes(n, 2) + 6 * 256 + 16 <= kCtlSmemLimit) mode = 2;
+    else if (n <= 32767 && ctl_fixed_bytes(n, 1) + 6 * 256 + 16 <= kCtlSmemLimit) mode = 1;
     return min(mode, env_controller_mode_cap());
+}
+
+static int32_t ctl_list_cap(int32_t n, int32_t mode) {
+    if (mode == 0) return 0;
+    const size_t room = kCtlSmemLimit - ctl_fixed_bytes(n, mode) - 16;
+    const size_t cap = room / 6;  // three 16-bit lists
+    return (int32_t)(cap < 2 * (size_t)n ? cap : 2 * (size_t)n);
 }
 
 size_t controller_smem_bytes(int32_t n) {
     const int32_t mode = controller_smem_mode(n);
-    if (mode == 2) return ((6 * (size_t)n + 15) & ~(size_t)15) + 16 * (size_t)n;
-    if (mode == 1) return 6 * (size_t)n;
-    return 0;
+    if (mode == 0) return 0;
+    return ctl_fixed_bytes(n, mode) + 6 * (size_t)ctl_list_cap(n, mode) + 16;
 }
 
-cudaError_t launch_controller_impl(const Workspace& w, int32_t* g_res, uint8_t* g_estate, unsigned long long* g_edges,
-                                   cudaStream_t s) {
+cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s) {
     const int32_t mode = controller_smem_mode(w.n);
     const size_t smem = controller_smem_bytes(w.n);
+    const int32_t cap = ctl_list_cap(w.n, mode);
+    CtlScratch c{gs.res, gs.claimed, gs.estate, gs.edges, gs.acc, gs.und};
+    const bool narrow = w.n <= 65535;
+    const void* fn = narrow ? reinterpret_cast<const void*>(controller_kernel<uint32_t>)
+                            : reinterpret_cast<const void*>(controller_kernel<unsigned long long>);
     if (smem > 48 * 1024) {
-        cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(controller_kernel), 1, smem);
+        cudaError_t e = ensure_smem_limit(fn, narrow ? 1 : 3, smem);
         if (e != cudaSuccess) return e;
     }
-    CtlScratch c{g_res, g_estate, g_edges};
-    controller_kernel<<<1, kCtlThreads, smem, s>>>(w, mode, c);
+    const bool short_wrap = env_short_wraps() != 0;
+    const uint32_t span = short_wrap ? 4u : kRoundSpanMax;
+    const uint32_t stamp_wrap = short_wrap ? 5u : 250u;
+    if (narrow) controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap);
+    else controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s) {
+    int grid = (2 * w.n + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    prepare_edges_kernel<<<grid, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 

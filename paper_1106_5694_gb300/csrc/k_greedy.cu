@@ -161,6 +161,230 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
     }
 }
 
+// All rounds in one cooperative launch, one grid barrier per round.  Every
+// CTA keeps its own copy of the free-agent and free-job sets as bitmaps in
+// shared memory and computes the round's matches redundantly from the keys
+// (all CTAs reach the same result), then the full list of owners to rescan;
+// CTA b rescans the entries of rank b, b + G, ... of that list, so the work
+// is balanced without further synchronisation.  Round r equals round r of
+// the launch-per-round path.
+constexpr int kPThreads = 1024;
+constexpr int kPGroups = 8;          // rescans run in groups of 128 threads
+constexpr int kPMaxBitWords = 2048;  // n <= 65536 (larger n: one launch per round)
+constexpr int kPMaxMine = 512;       // rescans per CTA per round held in shared memory
+
+__device__ __forceinline__ bool bit_get(const uint32_t* bm, int32_t i) { return (bm[i >> 5] >> (i & 31)) & 1u; }
+
+// Flags and keys written by other CTAs during the launch are read with
+// __ldcg (from L2): L1 is not coherent across SMs.
+__global__ void __launch_bounds__(kPThreads, 1) greedy_persistent_kernel(Workspace w) {
+    DeviceState* st = w.st;
+    if (st->status != kRunning) return;
+    __shared__ uint32_t s_free_a[kPMaxBitWords], s_free_j[kPMaxBitWords], s_dirty[2 * kPMaxBitWords];
+    __shared__ int32_t s_mine[kPMaxMine];
+    __shared__ int32_t s_nmine, s_rem, s_warp[33];
+    __shared__ unsigned long long s_red[kPThreads / 32];
+    const int32_t n = w.n, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int32_t words = (n + 31) >> 5;
+    for (int32_t q = tid; q < words; q += kPThreads) {
+        const int32_t hi = min(32, n - 32 * q);
+        const uint32_t m = hi == 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+        s_free_a[q] = m;
+        s_free_j[q] = m;
+    }
+    // the global copies start full (set by the host); every CTA reads them
+    // only after the first barrier
+    __syncthreads();
+    unsigned long long* pt = w.phase_ns;
+    const bool timing = pt != nullptr && tid == 0;
+    uint64_t tp = timing ? globaltimer_ns() : 0, scan_total = 0;
+#define DGS_PT(slot)                                   \
+    if (timing && b == 0) {                            \
+        const uint64_t now = globaltimer_ns();         \
+        atomicAdd(pt + (slot), now - tp);              \
+        tp = now;                                      \
+    } else if (timing) {                               \
+        tp = globaltimer_ns();                         \
+    }
+    int32_t rounds = 0;
+    for (int32_t round = 0; round <= n; ++round) {
+        // ---- every CTA copied last round's dirty bitmap before the round's
+        // final barrier: clear it (the new flags are set after the next one)
+        for (int32_t q = b * kPThreads + tid; q < (2 * n + 31) >> 5; q += G * kPThreads) w.g_dirty[q] = 0u;
+        // ---- match every mutually-best pair: each CTA its slice of agents,
+        // recorded in the global free bitmaps; then every CTA copies them
+        for (int32_t i0 = b * kPThreads + tid; i0 < n; i0 += 4 * G * kPThreads) {
+            int32_t jj[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t i = i0 + k * G * kPThreads;
+                jj[k] = (i < n && bit_get(s_free_a, i)) ? key_index(__ldcg(w.g_row + i)) : -1;
+            }
+            int32_t back[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) back[k] = (jj[k] >= 0 && jj[k] < n) ? key_index(__ldcg(w.g_col + jj[k])) : -2;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t i = i0 + k * G * kPThreads, j = jj[k];
+                if (back[k] != i) continue;
+                atomicAnd(w.g_free_a + (i >> 5), ~(1u << (i & 31)));
+                atomicAnd(w.g_free_j + (j >> 5), ~(1u << (j & 31)));
+                w.tau[i] = j;
+                w.sigma[j] = i;
+            }
+        }
+        if (!grid_barrier(st)) {
+            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
+            return;
+        }
+        for (int32_t q = tid; q < words; q += kPThreads) {
+            s_free_a[q] = __ldcg(w.g_free_a + q);
+            s_free_j[q] = __ldcg(w.g_free_j + q);
+        }
+        __syncthreads();
+        ++rounds;
+        // ---- remaining free agents, and the owners to rescan (rows: free
+        // agents whose best job was taken; columns: the converse)
+        if (tid == 0) { s_rem = 0; s_nmine = 0; }
+        __syncthreads();
+        {
+            int32_t rem = 0;
+            for (int32_t q = tid; q < words; q += kPThreads) {
+                const int32_t hi = min(32, n - 32 * q);  // bits of agents >= n are not counted
+                rem += __popc(s_free_a[q] & (hi == 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) rem += __shfl_xor_sync(0xffffffffu, rem, off);
+            if ((tid & 31) == 0 && rem) atomicAdd(&s_rem, rem);
+        }
+        __syncthreads();
+        if (b == 0 && tid == 0) st->greedy_remaining = s_rem;
+        DGS_PT(kPtGreedyMatch)
+        if (s_rem == 0 || *(volatile int32_t*)&st->status != kRunning) break;
+        // owners are numbered 0..2n-1 (rows, then columns): each CTA flags
+        // the dirty owners of its slice in the global bitmap (cleared by the
+        // previous round), then every CTA copies the bitmap and ranks it
+        const int32_t owner_words = (2 * n + 31) >> 5;
+        for (int32_t o0 = b * kPThreads + tid; o0 < 2 * n; o0 += 4 * G * kPThreads) {
+            int32_t best[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t o = o0 + k * G * kPThreads;
+                best[k] = -3;
+                if (o < 2 * n) {
+                    const bool is_row = o < n;
+                    const int32_t x = is_row ? o : o - n;
+                    if (bit_get(is_row ? s_free_a : s_free_j, x))
+                        best[k] = key_index(__ldcg(is_row ? w.g_row + x : w.g_col + x));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (best[k] == -3) continue;
+                const int32_t o = o0 + k * G * kPThreads;
+                const bool is_row = o < n;
+                const bool taken = best[k] < 0 || best[k] >= n || !bit_get(is_row ? s_free_j : s_free_a, best[k]);
+                if (taken) atomicOr(w.g_dirty + (o >> 5), 1u << (o & 31));
+            }
+        }
+        if (!grid_barrier(st)) {
+            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
+            return;
+        }
+        for (int32_t q = tid; q < owner_words; q += kPThreads) s_dirty[q] = __ldcg(w.g_dirty + q);
+        __syncthreads();
+        int32_t base_rank = 0;
+        for (int32_t w0 = 0; w0 < owner_words; w0 += kPThreads) {
+            const int32_t q = w0 + tid;
+            uint32_t dirty = q < owner_words ? s_dirty[q] : 0u;
+            const int32_t c = __popc(dirty);
+            int32_t total;
+            // exclusive block scan of c
+            int32_t incl = c;
+            const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += o;
+            }
+            if (lane == 31) s_warp[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const int32_t v = s_warp[lane];
+                int32_t wi = v;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int32_t o = __shfl_up_sync(0xffffffffu, wi, off);
+                    if (lane >= off) wi += o;
+                }
+                s_warp[lane] = wi - v;
+                if (lane == 31) s_warp[32] = wi;
+            }
+            __syncthreads();
+            int32_t rank = base_rank + s_warp[warp] + incl - c;
+            total = s_warp[32];
+            while (dirty) {
+                const int k = __ffs(dirty) - 1;
+                dirty &= dirty - 1u;
+                if (rank % G == b) {
+                    const int32_t slot = atomicAdd(&s_nmine, 1);
+                    if (slot < kPMaxMine) s_mine[slot] = 32 * q + k;
+                }
+                ++rank;
+            }
+            base_rank += total;
+            __syncthreads();
+        }
+        if (s_nmine > kPMaxMine) {  // cannot happen for n <= 131072 with G >= 152
+            if (tid == 0) { st->error = kErrInternal; st->status = kError; }
+            break;
+        }
+        DGS_PT(kPtGreedyCheck)
+        // ---- rescan this CTA's owners: eight 128-thread groups
+        const int32_t cnt = s_nmine;
+        const int grp = tid >> 7, gt = tid & 127, glane = tid & 31, gwarp = (tid >> 5) & 3;
+        for (int32_t t = grp; t < cnt; t += kPGroups) {
+            const int32_t o2 = s_mine[t];
+            const bool is_row = o2 < n;
+            const int32_t o = is_row ? o2 : o2 - n;
+            const int32_t* row = is_row ? w.a + (size_t)o * w.lda : w.at + (size_t)o * w.ldt;
+            const uint32_t* pfree = is_row ? s_free_j : s_free_a;
+            unsigned long long best = 0;
+#pragma unroll 8
+            for (int32_t c = gt * 4; c < n; c += 4 * 128) {
+                const int4 v = *reinterpret_cast<const int4*>(row + c);
+                const uint32_t fr = (pfree[c >> 5] >> (c & 31)) & 0xFu;
+                const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (c + e < n && ((fr >> e) & 1u)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
+            if (glane == 0) s_red[grp * 4 + gwarp] = best;
+            asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
+            if (gt == 0) {
+                const unsigned long long m = umax64(umax64(s_red[grp * 4], s_red[grp * 4 + 1]),
+                                                    umax64(s_red[grp * 4 + 2], s_red[grp * 4 + 3]));
+                (is_row ? w.g_row : w.g_col)[o] = m;
+            }
+            asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
+        }
+        __syncthreads();
+        if (timing) scan_total += globaltimer_ns() - tp;
+        DGS_PT(kPtGreedyScan)
+        if (!grid_barrier(st)) {
+            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
+            return;
+        }
+        DGS_PT(kPtGreedyBar2)
+    }
+    if (timing) atomicMax(pt + kPtGreedyScanMax, (unsigned long long)scan_total);
+#undef DGS_PT
+    if (b == 0 && tid == 0) st->greedy_rounds = rounds;
+    // the free flags of the round-based path are not used after this kernel
+}
+
 // |a| < 2^29 check alone (for entry points that do not run pass 1).
 __global__ void range_check_kernel(Workspace w) {
     bool bad = false;
@@ -202,6 +426,23 @@ cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1);
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0);
     return cudaGetLastError();
+}
+
+cudaError_t launch_greedy_persistent(const Workspace& w, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, greedy_persistent_kernel, kPThreads, 0);
+    if (e != cudaSuccess) return e;
+    int grid = sms * (per_sm < 1 ? per_sm : 1);
+    if (w.g_free_a == nullptr || w.g_free_j == nullptr || w.g_dirty == nullptr) return cudaErrorNotSupported;
+    if (grid < 1) return cudaErrorNotSupported;
+    if (w.n > 32 * kPMaxBitWords || (int64_t)2 * w.n > (int64_t)kPMaxMine * grid) return cudaErrorNotSupported;
+    Workspace arg = w;
+    void* args[] = {&arg};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(greedy_persistent_kernel), dim3(grid),
+                                       dim3(kPThreads), args, 0, s);
 }
 
 }  // namespace dgs
