@@ -29,6 +29,13 @@ int32_t env_update_policy() {
     }();
     return v;
 }
+int32_t env_exact_keys() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_EXACT_KEYS");
+        return (e && std::atoi(e) == 1) ? 1 : 0;
+    }();
+    return v;
+}
 int32_t env_phase_timers() {
     static const int32_t v = [] {
         const char* e = std::getenv("DGS_PHASE_TIMERS");
@@ -190,6 +197,7 @@ struct Solve {
         w.lda = plan.lda;
         w.ldt = plan.ldt;
         w.item_count = (int32_t)items.size();
+        w.exact_keys = env_exact_keys();
         if (plan.need_copy) {
             e = cudaMemsetAsync(a_copy, 0, (size_t)n * plan.lda * sizeof(int32_t), s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");

@@ -39,7 +39,7 @@ struct DeviceState {
     int32_t trace_capacity;
     int32_t greedy_matched;  // the last match kernel matched >= 1 pair
     int32_t update_policy;   // 0: by cost, 1: always full evaluation, 2: always row tasks
-    int32_t pad1;
+    int32_t max_abs;         // max |a| (set by the passes that check the range)
     uint32_t bar_count;      // grid barrier of cooperative launches: arrivals
     uint32_t bar_gen;        //   and generation
     int64_t f;               // current objective
@@ -82,7 +82,8 @@ struct Workspace {
     uint32_t* g_free_a; uint32_t* g_free_j;  // free sets as bitmaps (persistent greedy)
     uint32_t* g_dirty;                       // owners to rescan this round (persistent greedy)
     // evaluation work items (row-block, first column tile) of the tile-pair sweep
-    int2* items; int32_t item_count; int32_t pad2;
+    int2* items; int32_t item_count;
+    int32_t exact_keys;  // 1: never use the packed 32-bit keys (test knob)
     DeviceState* st;
     unsigned long long* phase_ns;  // optional phase timers (DGS_PHASE_TIMERS=1), else null
 };
@@ -256,5 +257,7 @@ int32_t env_controller_mode_cap();
 // tests reach their wrap-around paths.
 int32_t env_short_wraps();
 int32_t env_phase_timers();
+// DGS_EXACT_KEYS=1 disables the packed 32-bit keys of the evaluation kernel.
+int32_t env_exact_keys();
 
 }  // namespace dgs

@@ -125,6 +125,7 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
     uint8_t* seen = base + kOffSeen;
     w.items = reinterpret_cast<int2*>(base + kOffItems);
     w.item_count = item_count_for(n);
+    w.exact_keys = env_exact_keys();
     w.st = reinterpret_cast<DeviceState*>(base + kOffState);
 
     const int32_t nb = (n + 63) / 64;

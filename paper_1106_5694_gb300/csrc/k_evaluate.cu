@@ -39,6 +39,8 @@ constexpr int kGroups = kThreads / kT;
 struct Stage {
     int32_t x[kT * kT];
     int32_t y[kT * kYP];
+    int32_t sk[kT];  // sigma of the tile's columns
+    int32_t dk[kT];  // D of the tile's columns
 };
 
 struct TileCursor {
@@ -100,62 +102,115 @@ __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int
     if (in_x && c.x1 >= 0) cp_async16(stage->x + (rq + 32) * kT + chunk, w.a + (size_t)c.x1 * w.lda + K0 + chunk);
     if (in_y && c.y0 >= 0) cp_async16(stage->y + rq * kYP + chunk, w.a + (size_t)c.y0 * w.lda + J0 + chunk);
     if (in_y && c.y1 >= 0) cp_async16(stage->y + (rq + 32) * kYP + chunk, w.a + (size_t)c.y1 * w.lda + J0 + chunk);
+    // sigma and D of the columns (arrays hold at least round_up(n, 64) entries)
+    if (threadIdx.x < 16) cp_async16(stage->sk + chunk, w.sigma + K0 + chunk);
+    else if (threadIdx.x < 32) cp_async16(stage->dk + chunk, w.diag + K0 + chunk);
 }
 
+// Row-side state of a thread's 8 rows across a strip.  Exact path: best gain,
+// its lowest column, lowest partner agent among columns reaching it.  Packed
+// path (when |gain| * 2^s fits in int32, s = index bits): two int32 keys per
+// row, (gain << s) + (mask - column) and (gain << s) + (mask - partner agent),
+// where max picks the larger gain, then the lower index.
 struct RowState {
-    int32_t g[kRows];  // best gain (starts at 0: only strictly positive gains count)
-    int32_t c[kRows];  // its lowest partner column
-    int32_t s[kRows];  // lowest partner agent among the columns reaching g
+    int32_t g[kRows];
+    int32_t c[kRows];
+    int32_t s[kRows];
 };
+
+// Packed-key geometry for this n and value range; pw = 0 means "exact path".
+struct Packing {
+    int32_t pw;    // 2^s
+    int32_t mask;  // 2^s - 1
+};
+
+__device__ __forceinline__ Packing packing_for(int32_t n, int32_t max_abs) {
+    const int32_t s = 32 - __clz(max(n - 1, 1));
+    const int64_t gmax = 4ll * (int64_t)max_abs + 1;
+    Packing p{0, 0};
+    if (s <= 24 && gmax < ((int64_t)1 << (30 - s))) {
+        p.pw = 1 << s;
+        p.mask = p.pw - 1;
+    }
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long unpack_key(int32_t key, const Packing& pk) {
+    if (key <= pk.mask) return 0ull;  // gain <= 0
+    return pack_gain(key >> __popc(pk.mask), (uint32_t)(pk.mask - (key & pk.mask)));
+}
 
 // One tile: thread (ty, tx) covers column k = K0 + tx and rows J0 + ty*8 .. +7.
 // Column-side partial keys go to colbuf (combined at the next barrier).
-template <bool kRagged>
+template <bool kRagged, bool kPacked>
 __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, const int32_t (&dj)[kRows],
                                              const int32_t (&sj)[kRows], int32_t J0, int32_t K0, int32_t n,
-                                             const Workspace& w, unsigned long long* col_a,
+                                             const Packing& pk, unsigned long long* col_a,
                                              unsigned long long* col_j) {
     const int tx = threadIdx.x & 63;
     const int ty = threadIdx.x >> 6;
     const int32_t k = K0 + tx;
     unsigned long long ka = 0ull, kj = 0ull;
     if (!kRagged || k < n) {
-        const int32_t sk = w.sigma[k];
-        const int32_t dk = w.diag[k];
-        int32_t cg = 0, cc = -1, cs = 0x7fffffff;
+        const int32_t sk = stage->sk[tx];
+        const int32_t dk = stage->dk[tx];
         const int32_t* xrow = stage->x + (ty * kRows) * kT + tx;
         const int4* yrow = reinterpret_cast<const int4*>(stage->y + tx * kYP + ty * kRows);
+        if (kPacked) {
+            const int32_t cka = pk.mask - k, ckj = pk.mask - sk;
+            int32_t ca = pk.mask, cj = pk.mask;
 #pragma unroll
-        for (int q = 0; q < kRows / 4; ++q) {
-            const int4 y4 = yrow[q];
-            const int32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            for (int q = 0; q < kRows / 4; ++q) {
+                const int4 y4 = yrow[q];
+                const int32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = q * 4 + e;
-                const int32_t jr = J0 + ty * kRows + r;
-                if (kRagged && jr >= n) continue;
-                const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
-                // row side: row jr, partner column k (ascending in this thread)
-                {
-                    const bool gt = g > rs.g[r];
-                    const bool eq = g == rs.g[r];
-                    rs.s[r] = gt ? sk : (eq ? min(rs.s[r], sk) : rs.s[r]);
-                    rs.c[r] = gt ? k : rs.c[r];
-                    rs.g[r] = max(rs.g[r], g);
-                }
-                // column side: row k, partner column jr (ascending in this loop)
-                {
-                    const bool gt = g > cg;
-                    const bool eq = g == cg;
-                    cs = gt ? sj[r] : (eq ? min(cs, sj[r]) : cs);
-                    cc = gt ? jr : cc;
-                    cg = max(cg, g);
+                for (int e = 0; e < 4; ++e) {
+                    const int r = q * 4 + e;
+                    const int32_t jr = J0 + ty * kRows + r;
+                    if (kRagged && jr >= n) continue;
+                    const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
+                    rs.g[r] = max(rs.g[r], g * pk.pw + cka);          // row jr, lowest column
+                    rs.s[r] = max(rs.s[r], g * pk.pw + ckj);          // row jr, lowest partner agent
+                    ca = max(ca, g * pk.pw + (pk.mask - jr));          // row k, lowest column
+                    cj = max(cj, g * pk.pw + (pk.mask - sj[r]));       // row k, lowest partner agent
                 }
             }
-        }
-        if (cg > 0) {
-            ka = pack_gain(cg, (uint32_t)cc);
-            kj = pack_gain(cg, (uint32_t)cs);
+            ka = unpack_key(ca, pk);
+            kj = unpack_key(cj, pk);
+        } else {
+            int32_t cg = 0, cc = -1, cs = 0x7fffffff;
+#pragma unroll
+            for (int q = 0; q < kRows / 4; ++q) {
+                const int4 y4 = yrow[q];
+                const int32_t yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = q * 4 + e;
+                    const int32_t jr = J0 + ty * kRows + r;
+                    if (kRagged && jr >= n) continue;
+                    const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
+                    // row side: row jr, partner column k (ascending in this thread)
+                    {
+                        const bool gt = g > rs.g[r];
+                        const bool eq = g == rs.g[r];
+                        rs.s[r] = gt ? sk : (eq ? min(rs.s[r], sk) : rs.s[r]);
+                        rs.c[r] = gt ? k : rs.c[r];
+                        rs.g[r] = max(rs.g[r], g);
+                    }
+                    // column side: row k, partner column jr (ascending in this loop)
+                    {
+                        const bool gt = g > cg;
+                        const bool eq = g == cg;
+                        cs = gt ? sj[r] : (eq ? min(cs, sj[r]) : cs);
+                        cc = gt ? jr : cc;
+                        cg = max(cg, g);
+                    }
+                }
+            }
+            if (cg > 0) {
+                ka = pack_gain(cg, (uint32_t)cc);
+                kj = pack_gain(cg, (uint32_t)cs);
+            }
         }
     }
     col_a[ty * kT + tx] = ka;
@@ -176,17 +231,31 @@ __device__ __forceinline__ void commit_columns(const unsigned long long* col_a, 
     if (m != 0ull && k < n) atomicMax((t < kT) ? &w.key_a[k] : &w.key_j[k], m);
 }
 
-__device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int32_t n, const Workspace& w) {
+template <bool kPacked>
+__device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int32_t n, const Workspace& w,
+                                            const Packing& pk) {
     const int lane = threadIdx.x & 31;
     const int ty = threadIdx.x >> 6;
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        unsigned long long ka = rs.g[r] > 0 ? pack_gain(rs.g[r], (uint32_t)rs.c[r]) : 0ull;
-        unsigned long long kj = rs.g[r] > 0 ? pack_gain(rs.g[r], (uint32_t)rs.s[r]) : 0ull;
+        unsigned long long ka, kj;
+        if (kPacked) {
+            int32_t a = rs.g[r], j = rs.s[r];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            ka = umax64(ka, __shfl_xor_sync(0xffffffffu, ka, off));
-            kj = umax64(kj, __shfl_xor_sync(0xffffffffu, kj, off));
+            for (int off = 16; off > 0; off >>= 1) {
+                a = max(a, __shfl_xor_sync(0xffffffffu, a, off));
+                j = max(j, __shfl_xor_sync(0xffffffffu, j, off));
+            }
+            ka = unpack_key(a, pk);
+            kj = unpack_key(j, pk);
+        } else {
+            ka = rs.g[r] > 0 ? pack_gain(rs.g[r], (uint32_t)rs.c[r]) : 0ull;
+            kj = rs.g[r] > 0 ? pack_gain(rs.g[r], (uint32_t)rs.s[r]) : 0ull;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                ka = umax64(ka, __shfl_xor_sync(0xffffffffu, ka, off));
+                kj = umax64(kj, __shfl_xor_sync(0xffffffffu, kj, off));
+            }
         }
         const int32_t jr = J0 + ty * kRows + r;
         if (lane == 0 && jr < n && ka != 0) {
@@ -210,6 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
 
     const int32_t n = w.n;
     const int32_t nb = (n + kT - 1) / kT;
+    const Packing pk = packing_for(n, st->max_abs);
+    const bool packed = pk.pw != 0 && !w.exact_keys;
 
     // producer cursor: kStages - 1 tiles ahead of the consumer
     TileCursor prod;
@@ -238,9 +309,9 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
                 const int32_t jr = J0 + ty * kRows + r;
                 dj[r] = jr < n ? w.diag[jr] : 0;
                 sj[r] = jr < n ? w.sigma[jr] : 0;
-                rs.g[r] = 0;
+                rs.g[r] = packed ? pk.mask : 0;
                 rs.c[r] = -1;
-                rs.s[r] = 0x7fffffff;
+                rs.s[r] = packed ? pk.mask : 0x7fffffff;
             }
             item_start = false;
         }
@@ -259,9 +330,18 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
         const int32_t K0 = cons.k * kT;
         unsigned long long* cb = colbuf + (t & 1) * 2 * kGroups * kT;
         const Stage* stage = &stages[t % kStages];
-        if ((J0 + kT > n) || (K0 + kT > n)) compute_tile<true>(stage, rs, dj, sj, J0, K0, n, w, cb, cb + kGroups * kT);
-        else compute_tile<false>(stage, rs, dj, sj, J0, K0, n, w, cb, cb + kGroups * kT);
-        if (cons.k + 1 >= cons.kend) commit_rows(rs, J0, n, w);
+        const bool ragged = (J0 + kT > n) || (K0 + kT > n);
+        if (packed) {
+            if (ragged) compute_tile<true, true>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
+            else compute_tile<false, true>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
+        } else {
+            if (ragged) compute_tile<true, false>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
+            else compute_tile<false, false>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
+        }
+        if (cons.k + 1 >= cons.kend) {
+            if (packed) commit_rows<true>(rs, J0, n, w, pk);
+            else commit_rows<false>(rs, J0, n, w, pk);
+        }
         prev_k0 = K0;
         ++t;
         if (++cons.k >= cons.kend) {

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t 
     const int t = threadIdx.x;
     const int lane16 = t & 15;
     bool bad = false;
+    int32_t amax = 0;
     for (int32_t tile = blockIdx.x; tile < tiles_total; tile += gridDim.x) {
         const int32_t I0 = (tile / tiles_x) * kT;
         const int32_t J0 = (tile % tiles_x) * kT;
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t 
                 if (i < n && j + e < n) {
                     const int32_t x = vals[e];
                     bad |= (x >= kBenefitLimit) || (x <= -kBenefitLimit);
+                    amax = max(amax, x == INT32_MIN ? INT32_MAX : abs(x));
                     best = umax64(best, pack_benefit(x, (uint32_t)(j + e)));
                 }
             }
@@ -89,6 +91,9 @@ __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t 
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((t & 31) == 0 && amax) atomicMax(&w.st->max_abs, amax);
     if (bad) {
         atomicExch(&w.st->error, kErrRange);
         atomicExch(&w.st->status, kError);
@@ -388,6 +393,7 @@ __global__ void __launch_bounds__(kPThreads, 1) greedy_persistent_kernel(Workspa
 // |a| < 2^29 check alone (for entry points that do not run pass 1).
 __global__ void range_check_kernel(Workspace w) {
     bool bad = false;
+    int32_t amax = 0;
     const size_t total4 = (size_t)w.n * (size_t)(w.lda / 4);
     const int32_t row4 = w.lda / 4;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total4; q += (size_t)gridDim.x * blockDim.x) {
@@ -396,8 +402,14 @@ __global__ void range_check_kernel(Workspace w) {
         const int32_t vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            if (c + e < w.n) bad |= (vals[e] >= kBenefitLimit) || (vals[e] <= -kBenefitLimit);
+            if (c + e < w.n) {
+                bad |= (vals[e] >= kBenefitLimit) || (vals[e] <= -kBenefitLimit);
+                amax = max(amax, vals[e] == INT32_MIN ? INT32_MAX : abs(vals[e]));
+            }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(&w.st->max_abs, amax);
     if (bad) {
         atomicExch(&w.st->error, kErrRange);
         atomicExch(&w.st->status, kError);

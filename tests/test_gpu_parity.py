@@ -238,11 +238,13 @@ print(json.dumps(out))
 @pytest.mark.parametrize("env", [{"DGS_UPDATE_POLICY": "1"}, {"DGS_UPDATE_POLICY": "2"},
                                  {"DGS_CTL_MODE": "1"}, {"DGS_CTL_MODE": "0"},
                                  {"DGS_CTL_MODE": "0", "DGS_UPDATE_POLICY": "2"},
-                                 {"DGS_SHORT_WRAPS": "1"}, {"DGS_SHORT_WRAPS": "1", "DGS_CTL_MODE": "1"}])
+                                 {"DGS_SHORT_WRAPS": "1"}, {"DGS_SHORT_WRAPS": "1", "DGS_CTL_MODE": "1"},
+                                 {"DGS_EXACT_KEYS": "1"}])
 def test_internal_paths_agree_with_oracle(env):
     """Forcing the full-evaluation or row-task update path, placing the
-    controller's scratch in global memory, or making its reservation keys and
-    claim stamps wrap every few rounds, must not change any result."""
+    controller's scratch in global memory, making its reservation keys and
+    claim stamps wrap every few rounds, or disabling the evaluation kernel's
+    packed 32-bit keys, must not change any result."""
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
