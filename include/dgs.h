@@ -77,8 +77,9 @@ typedef struct {
     int32_t* trace_accepted;
     int32_t* trace_applied;
     int64_t* trace_objective;
-    /* 1: time the first full difference evaluation with CUDA events on the
-     * call's stream (dgs_stats.evaluation_ms); 0: no timing. */
+    /* 1: time the first full difference evaluation and the greedy start with
+     * CUDA events on the call's stream (dgs_stats.evaluation_ms, greedy_ms);
+     * 0: no timing. */
     int32_t profile;
 } dgs_options;
 
@@ -93,6 +94,8 @@ typedef struct {
     int64_t initial_objective;/* objective of the starting assignment */
     int64_t kernel_launches;  /* kernels this call launched */
     double evaluation_ms;     /* first full evaluation, when options.profile */
+    double greedy_ms;         /* greedy start after pass 1, when options.profile */
+    int64_t greedy_rescans;   /* rows of a (or its transpose) the greedy start rescanned */
 } dgs_stats;
 
 /* Fill *opt with the defaults (GREEDY start, no cap, no deadline, no trace). */

@@ -60,6 +60,8 @@ class dgs_stats(ctypes.Structure):
         ("initial_objective", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
         ("evaluation_ms", ctypes.c_double),
+        ("greedy_ms", ctypes.c_double),
+        ("greedy_rescans", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -14,7 +14,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <vector>
 
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
@@ -100,18 +99,8 @@ struct Plan {
 
 int32_t round_up32(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 
-std::vector<int2> evaluation_items(int32_t n) {
-    const int32_t nb = (n + 63) / 64;
-    const int32_t strip = evaluation_strip();
-    std::vector<int2> items;
-    items.reserve((size_t)nb * nb / (2 * strip) + nb + 1);
-    for (int32_t j = 0; j < nb; ++j)
-        for (int32_t k = j; k < nb; k += strip) items.push_back(make_int2(j, k));
-    return items;
-}
-
 // Carve the workspace; sizes first (base == nullptr), then pointers.
-size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, CtlGlobal* ctl, uint8_t** seen,
+size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, uint8_t** seen,
              int32_t** a_copy) {
     const size_t nb = align_up((size_t)n, 128);
     *a_copy = p.need_copy ? ar.take<int32_t>((size_t)n * p.lda) : nullptr;
@@ -143,7 +132,6 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, size_t items, Ct
     w.g_free_a = ar.take<uint32_t>(nb / 32);
     w.g_free_j = ar.take<uint32_t>(nb / 32);
     w.g_dirty = ar.take<uint32_t>(2 * nb / 32);
-    w.items = ar.take<int2>(items ? items : 1);
     w.phase_ns = env_phase_timers() ? ar.take<unsigned long long>(kPtCount) : nullptr;
     w.st = ar.take<DeviceState>(1);
     *seen = ar.take<uint8_t>(4 * nb);
@@ -166,22 +154,20 @@ struct Solve {
     int32_t* a_copy = nullptr;
     CtlGlobal ctl{};
     uint8_t* seen = nullptr;
-    std::vector<int2> items;
     int64_t launches = 0;
     explicit Solve(cudaStream_t st) : s(st) {}
     ~Solve() {
         if (ar.base) cudaFreeAsync(ar.base, s);
     }
 
-    dgs_status setup(const int32_t* a, int32_t n, bool need_at, bool need_items) {
+    dgs_status setup(const int32_t* a, int32_t n, bool need_at) {
         plan.need_at = need_at;
         plan.need_copy = (n % 4) != 0 || (reinterpret_cast<uintptr_t>(a) % 16) != 0;
         plan.lda = plan.need_copy ? round_up32(n, 4) : n;
         plan.ldt = round_up32(n, 64);
-        if (need_items) items = evaluation_items(n);
         Arena sizing;
         Workspace tmp{};
-        carve(sizing, tmp, plan, n, items.size(), &ctl, &seen, &a_copy);
+        carve(sizing, tmp, plan, n, &ctl, &seen, &a_copy);
         plan.bytes = sizing.used;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
         if (e == cudaErrorMemoryAllocation) {
@@ -192,11 +178,10 @@ struct Solve {
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
         ar.size = plan.bytes;
-        carve(ar, w, plan, n, items.size(), &ctl, &seen, &a_copy);
+        carve(ar, w, plan, n, &ctl, &seen, &a_copy);
         w.n = n;
         w.lda = plan.lda;
         w.ldt = plan.ldt;
-        w.item_count = (int32_t)items.size();
         w.exact_keys = env_exact_keys();
         if (plan.need_copy) {
             e = cudaMemsetAsync(a_copy, 0, (size_t)n * plan.lda * sizeof(int32_t), s);
@@ -220,10 +205,6 @@ struct Solve {
         if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_a, 0xFF, nb / 8, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_j, 0xFF, nb / 8, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-        if (!items.empty()) {
-            e = cudaMemcpyAsync(w.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(items)");
-        }
         return DGS_OK;
     }
 
@@ -309,12 +290,14 @@ dgs_status map_device_status(const DeviceState& h) {
     } while (0)
 
 // Greedy rounds until every agent is matched (or an error).
-dgs_status run_greedy(Solve& S) {
+dgs_status run_greedy(Solve& S, EventPair* timer) {
     DGS_CUDA(launch_greedy_pass1(S.w, S.s), "greedy pass 1");
     S.launches += 1;
+    if (timer) DGS_TRY(timer->begin(S.s));
     const cudaError_t pe = launch_greedy_persistent(S.w, S.s);
     if (pe == cudaSuccess) {
         S.launches += 1;
+        if (timer) DGS_TRY(timer->end(S.s));
         return DGS_OK;
     }
     // the cooperative launch was refused: one launch per kernel per round
@@ -325,7 +308,10 @@ dgs_status run_greedy(Solve& S) {
         S.launches += 3 * batch;
         DeviceState h;
         DGS_TRY(S.read_state(&h));
-        if (h.status != kRunning || h.greedy_remaining == 0) return DGS_OK;
+        if (h.status != kRunning || h.greedy_remaining == 0) {
+            if (timer) DGS_TRY(timer->end(S.s));
+            return DGS_OK;
+        }
     }
     snprintf(g_last_error, sizeof(g_last_error), "greedy start did not finish");
     return DGS_ERR_INTERNAL;
@@ -347,15 +333,16 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
 
     Solve S(stream);
-    DGS_TRY(S.setup(benefit, n, true, true));
+    DGS_TRY(S.setup(benefit, n, true));
     DGS_TRY(S.init_state(o.max_sweeps, &o));
     if (o.deadline_us > 0) {
         arm_deadline_kernel<<<1, 1, 0, stream>>>(S.w.st, o.deadline_us);
         DGS_CUDA(cudaGetLastError(), "arm deadline");
         S.launches += 1;
     }
+    EventPair gev;
     if (o.init == DGS_INIT_GREEDY) {
-        DGS_TRY(run_greedy(S));
+        DGS_TRY(run_greedy(S, o.profile ? &gev : nullptr));
     } else {
         DGS_CUDA(launch_greedy_pass1(S.w, stream), "pass 1");  // transpose + range check
         S.launches += 1;
@@ -416,6 +403,8 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         stats->initial_objective = h.f_initial;
         stats->kernel_launches = S.launches;
         stats->evaluation_ms = o.profile ? ev.elapsed_ms() : 0.0;
+        stats->greedy_ms = (o.profile && o.init == DGS_INIT_GREEDY) ? gev.elapsed_ms() : 0.0;
+        stats->greedy_rescans = h.greedy_rescans;
     }
     return status;
 }
@@ -476,7 +465,7 @@ dgs_status dgs_evaluate(const int32_t* benefit, int32_t n, const int32_t* sigma_
     if (!sigma_in || !agent_gain || !agent_job || !job_gain || !job_agent) return DGS_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Solve S(s);
-    DGS_TRY(S.setup(benefit, n, false, true));
+    DGS_TRY(S.setup(benefit, n, false));
     DGS_TRY(S.init_state(0, nullptr));
     DGS_CUDA(launch_range_check(S.w, s), "range check");
     DGS_CUDA(launch_start_from_tau(S.w, sigma_in, DGS_INIT_USER, S.seen, s), "start");
@@ -492,9 +481,9 @@ dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* sigma_out
     if (!sigma_out) return DGS_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Solve S(s);
-    DGS_TRY(S.setup(benefit, n, true, false));
+    DGS_TRY(S.setup(benefit, n, true));
     DGS_TRY(S.init_state(0, nullptr));
-    DGS_TRY(run_greedy(S));
+    DGS_TRY(run_greedy(S, nullptr));
     DGS_CUDA(launch_finish(S.w, sigma_out, s), "finish");
     DeviceState h;
     DGS_TRY(S.read_state(&h));

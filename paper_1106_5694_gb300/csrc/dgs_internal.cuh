@@ -40,6 +40,7 @@ struct DeviceState {
     int32_t greedy_matched;  // the last match kernel matched >= 1 pair
     int32_t update_policy;   // 0: by cost, 1: always full evaluation, 2: always row tasks
     int32_t max_abs;         // max |a| (set by the passes that check the range)
+    long long greedy_rescans;  // rows of a / at rescanned by the greedy start
     uint32_t bar_count;      // grid barrier of cooperative launches: arrivals
     uint32_t bar_gen;        //   and generation
     int64_t f;               // current objective
@@ -81,9 +82,8 @@ struct Workspace {
     uint8_t* free_a; uint8_t* free_j;
     uint32_t* g_free_a; uint32_t* g_free_j;  // free sets as bitmaps (persistent greedy)
     uint32_t* g_dirty;                       // owners to rescan this round (persistent greedy)
-    // evaluation work items (row-block, first column tile) of the tile-pair sweep
-    int2* items; int32_t item_count;
     int32_t exact_keys;  // 1: never use the packed 32-bit keys (test knob)
+    int32_t pad2;
     DeviceState* st;
     unsigned long long* phase_ns;  // optional phase timers (DGS_PHASE_TIMERS=1), else null
 };

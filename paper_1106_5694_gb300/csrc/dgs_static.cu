@@ -25,9 +25,6 @@ namespace {
 using namespace dgs;
 
 constexpr int32_t kStaticMaxN = DGS_STATIC_MAX_N;
-constexpr int32_t kTiles = (kStaticMaxN + 63) / 64;
-constexpr int32_t kStripTiles = 8;  // same strip length as the solver's evaluation
-constexpr size_t kMaxItems = (size_t)kTiles * (kTiles + 1) / 2 / kStripTiles + kTiles + 1;
 
 // Byte offsets of each array inside the static block (each 256-B aligned).
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -37,8 +34,7 @@ constexpr size_t kOffDiag = kOffTau + align256(4 * (size_t)kStaticMaxN);
 constexpr size_t kOffKeyA = kOffDiag + align256(4 * (size_t)kStaticMaxN);
 constexpr size_t kOffKeyJ = kOffKeyA + align256(8 * (size_t)kStaticMaxN);
 constexpr size_t kOffSeen = kOffKeyJ + align256(8 * (size_t)kStaticMaxN);
-constexpr size_t kOffItems = kOffSeen + align256(4 * (size_t)kStaticMaxN);
-constexpr size_t kOffState = kOffItems + align256(8 * kMaxItems);
+constexpr size_t kOffState = kOffSeen + align256(4 * (size_t)kStaticMaxN);
 constexpr size_t kStaticBytes = kOffState + align256(sizeof(DeviceState));
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
@@ -61,22 +57,6 @@ cudaError_t scratch_address(unsigned char** out) {
     }
     *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
     return cudaSuccess;
-}
-
-int32_t item_count_for(int32_t n) {
-    const int32_t nb = (n + 63) / 64;
-    int32_t c = 0;
-    for (int32_t j = 0; j < nb; ++j) c += (nb - j + kStripTiles - 1) / kStripTiles;
-    return c;
-}
-
-// Work items (row block J, first column tile K) of the tile-pair evaluation.
-__global__ void static_items_kernel(int2* items, int32_t nb) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
-    int32_t off = 0;
-    for (int32_t q = 0; q < j; ++q) off += (nb - q + kStripTiles - 1) / kStripTiles;
-    for (int32_t k = j; k < nb; k += kStripTiles) items[off++] = make_int2(j, k);
 }
 
 __global__ void static_state_kernel(DeviceState* st) {
@@ -104,7 +84,6 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
         set_last_error(why);
         return DGS_ERR_INVALID;
     }
-    if (evaluation_strip() != kStripTiles) return DGS_ERR_INTERNAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* base = nullptr;
     cudaError_t e = scratch_address(&base);
@@ -123,12 +102,9 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
     w.key_a = reinterpret_cast<unsigned long long*>(base + kOffKeyA);
     w.key_j = reinterpret_cast<unsigned long long*>(base + kOffKeyJ);
     uint8_t* seen = base + kOffSeen;
-    w.items = reinterpret_cast<int2*>(base + kOffItems);
-    w.item_count = item_count_for(n);
     w.exact_keys = env_exact_keys();
     w.st = reinterpret_cast<DeviceState*>(base + kOffState);
 
-    const int32_t nb = (n + 63) / 64;
     // what must start at zero: row keys, the permutation check, the loop state
     e = cudaMemsetAsync(w.key_a, 0, kOffSeen - kOffKeyA, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(seen, 0, 4 * (size_t)n, s);
@@ -137,7 +113,6 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
         return DGS_ERR_CUDA;
     }
     static_state_kernel<<<1, 1, 0, s>>>(w.st);
-    static_items_kernel<<<(nb + 127) / 128, 128, 0, s>>>(w.items, nb);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_range_check(w, s);
     if (e == cudaSuccess) e = launch_start_from_tau(w, sigma_in, DGS_INIT_USER, seen, s);

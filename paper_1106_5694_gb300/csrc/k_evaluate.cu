@@ -41,6 +41,8 @@ struct Stage {
     int32_t y[kT * kYP];
     int32_t sk[kT];  // sigma of the tile's columns
     int32_t dk[kT];  // D of the tile's columns
+    int32_t sj[kT];  // sigma of the tile's rows (the row block J)
+    int32_t dj[kT];  // D of the tile's rows
 };
 
 struct TileCursor {
@@ -50,20 +52,30 @@ struct TileCursor {
     int32_t j;      // row block
 };
 
-__device__ __forceinline__ bool cursor_load(TileCursor& c, const Workspace& w, int32_t item, int32_t nb,
-                                            int32_t strip) {
+// Work items (row block J, first column tile J + strip * c) are numbered
+// J * chunks + c; items whose first tile lies past the last block are empty
+// and skipped.  CTA b walks items b, b + G, b + 2G, ...
+__device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t nb, int32_t strip) {
+    const int32_t chunks = (nb + strip - 1) / strip;
+    const int32_t total = nb * chunks;
+    for (; item < total; item += gridDim.x) {
+        const int32_t j = item / chunks;
+        const int32_t k0 = j + strip * (item - j * chunks);
+        if (k0 < nb) {
+            c.item = item;
+            c.j = j;
+            c.k = k0;
+            c.kend = min(k0 + strip, nb);
+            return true;
+        }
+    }
     c.item = item;
-    if (item >= w.item_count) return false;
-    const int2 it = w.items[item];
-    c.j = it.x;
-    c.k = it.y;
-    c.kend = min(it.y + strip, nb);
-    return true;
+    return false;
 }
 
-__device__ __forceinline__ bool cursor_next(TileCursor& c, const Workspace& w, int32_t nb, int32_t strip) {
+__device__ __forceinline__ bool cursor_next(TileCursor& c, int32_t nb, int32_t strip) {
     if (++c.k < c.kend) return true;
-    return cursor_load(c, w, c.item + gridDim.x, nb, strip);
+    return cursor_load(c, c.item + gridDim.x, nb, strip);
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -105,6 +117,8 @@ __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int
     // sigma and D of the columns (arrays hold at least round_up(n, 64) entries)
     if (threadIdx.x < 16) cp_async16(stage->sk + chunk, w.sigma + K0 + chunk);
     else if (threadIdx.x < 32) cp_async16(stage->dk + chunk, w.diag + K0 + chunk);
+    else if (threadIdx.x < 48) cp_async16(stage->sj + chunk, w.sigma + J0 + chunk);
+    else if (threadIdx.x < 64) cp_async16(stage->dj + chunk, w.diag + J0 + chunk);
 }
 
 // Row-side state of a thread's 8 rows across a strip.  Exact path: best gain,
@@ -282,54 +296,62 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
     const Packing pk = packing_for(n, st->max_abs);
     const bool packed = pk.pw != 0 && !w.exact_keys;
 
-    // producer cursor: kStages - 1 tiles ahead of the consumer
+    // producer cursor: kStages - 1 tiles ahead of the consumer; the rows
+    // (sigma) it will copy are loaded two tiles before they are needed
     TileCursor prod;
-    bool prod_ok = cursor_load(prod, w, blockIdx.x, nb, strip);
+    bool prod_ok = cursor_load(prod, blockIdx.x, nb, strip);
     for (int s = 0; s < kStages - 1; ++s) {
         if (prod_ok) {
             issue_tile(w, &stages[s], prod.j, prod.k, copy_rows(w, prod.j, prod.k));
-            prod_ok = cursor_next(prod, w, nb, strip);
+            prod_ok = cursor_next(prod, nb, strip);
         }
         cp_async_commit();
     }
-    CopyRows next_rows = prod_ok ? copy_rows(w, prod.j, prod.k) : CopyRows{-1, -1, -1, -1};
+    TileCursor ahead = prod;  // one tile after prod
+    bool ahead_ok = prod_ok && cursor_next(ahead, nb, strip);
+    CopyRows rows_now = prod_ok ? copy_rows(w, prod.j, prod.k) : CopyRows{-1, -1, -1, -1};
+    CopyRows rows_next = ahead_ok ? copy_rows(w, ahead.j, ahead.k) : CopyRows{-1, -1, -1, -1};
 
     TileCursor cons;
-    bool cons_ok = cursor_load(cons, w, blockIdx.x, nb, strip);
+    bool cons_ok = cursor_load(cons, blockIdx.x, nb, strip);
     RowState rs;
     int32_t dj[kRows], sj[kRows];
     bool item_start = true;
     int32_t t = 0, prev_k0 = -1;
     while (cons_ok) {
         const int32_t J0 = cons.j * kT;
+        cp_async_wait<kStages - 2>();
+        __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
+        const Stage* stage = &stages[t % kStages];
         if (item_start) {
             const int ty = threadIdx.x >> 6;
 #pragma unroll
             for (int r = 0; r < kRows; ++r) {
-                const int32_t jr = J0 + ty * kRows + r;
-                dj[r] = jr < n ? w.diag[jr] : 0;
-                sj[r] = jr < n ? w.sigma[jr] : 0;
+                dj[r] = stage->dj[ty * kRows + r];
+                sj[r] = stage->sj[ty * kRows + r];
                 rs.g[r] = packed ? pk.mask : 0;
                 rs.c[r] = -1;
                 rs.s[r] = packed ? pk.mask : 0x7fffffff;
             }
             item_start = false;
         }
-        cp_async_wait<kStages - 2>();
-        __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
         if (prev_k0 >= 0) {
             const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
             commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
         }
         if (prod_ok) {
-            issue_tile(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, next_rows);
-            prod_ok = cursor_next(prod, w, nb, strip);
-            if (prod_ok) next_rows = copy_rows(w, prod.j, prod.k);
+            issue_tile(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, rows_now);
+            prod = ahead;
+            prod_ok = ahead_ok;
+            rows_now = rows_next;
+            if (ahead_ok) {
+                ahead_ok = cursor_next(ahead, nb, strip);
+                if (ahead_ok) rows_next = copy_rows(w, ahead.j, ahead.k);
+            }
         }
         cp_async_commit();
         const int32_t K0 = cons.k * kT;
         unsigned long long* cb = colbuf + (t & 1) * 2 * kGroups * kT;
-        const Stage* stage = &stages[t % kStages];
         const bool ragged = (J0 + kT > n) || (K0 + kT > n);
         if (packed) {
             if (ragged) compute_tile<true, true>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
@@ -345,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
         prev_k0 = K0;
         ++t;
         if (++cons.k >= cons.kend) {
-            cons_ok = cursor_load(cons, w, cons.item + gridDim.x, nb, strip);
+            cons_ok = cursor_load(cons, cons.item + gridDim.x, nb, strip);
             item_start = true;
         }
     }
@@ -379,7 +401,7 @@ cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cuda
     const size_t smem = full_evaluation_smem_bytes();
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel), 0, smem);
     if (e != cudaSuccess) return e;
-    int grid = w.item_count < 152 ? w.item_count : 152;
+    int grid = 152;
     if (grid < 1) grid = 1;
     full_evaluation_kernel<<<grid, kThreads, smem, s>>>(w, conditional, kStrip);
     return cudaGetLastError();

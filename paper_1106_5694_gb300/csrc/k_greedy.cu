@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
         const int32_t b = key_index(keys[o]);
         if (b >= 0 && b < n && partner_free[b]) continue;  // best partner still free
         const int32_t* row = mat + (size_t)o * ld;
+        if (tid == 0) atomicAdd((unsigned long long*)&st->greedy_rescans, 1ull);
         unsigned long long best = 0;
 #pragma unroll 4
         for (int32_t c = tid * 4; c < n; c += 1024) {
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(kPThreads, 1) greedy_persistent_kernel(Workspa
             break;
         }
         DGS_PT(kPtGreedyCheck)
+        if (tid == 0 && s_nmine) atomicAdd((unsigned long long*)&st->greedy_rescans, (unsigned long long)s_nmine);
         // ---- rescan this CTA's owners: eight 128-thread groups
         const int32_t cnt = s_nmine;
         const int grp = tid >> 7, gt = tid & 127, glane = tid & 31, gwarp = (tid >> 5) & 3;
