@@ -154,11 +154,11 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(kernel: str, n: int):
+def kernel_traffic(kernel: str, n: int, workload: str):
     """dram bytes per launch of `kernel` from its committed ncu summary
-    (profiles/<kernel>.md), if that summary was taken on the current kernel
-    source and this n; else None."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    (profiles/<kernel>_n<n>_<workload>.md), if that summary was taken on the
+    current kernel source and this n; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_n{n}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -172,11 +172,11 @@ def kernel_traffic(kernel: str, n: int):
     return int(m_b.group(1))
 
 
-def roofline_entry(kernel, what, alg_bytes, ms, n, peak, peak_src):
+def roofline_entry(kernel, what, alg_bytes, ms, n, workload, peak, peak_src):
     achieved = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     return {"kernel": kernel, "work": what, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
-            "traffic": kernel_traffic(kernel, n), "algorithmic_bytes_per_launch": int(alg_bytes),
+            "traffic": kernel_traffic(kernel, n, workload), "algorithmic_bytes_per_launch": int(alg_bytes),
             "launch_ms": round(ms, 4), "note": "frac of measured copy bandwidth"}
 
 
@@ -300,10 +300,10 @@ def run_ours(args):
     # plus the per-round key traffic (two 8-byte keys per agent and job)
     greedy_bytes = 4 * n * stats["greedy_rescans"] + 32 * n * stats["greedy_rounds"]
     roofline = roofline_entry("greedy_persistent_kernel", "greedy start (Section 3.1): locally-dominant rounds",
-                              greedy_bytes, statistics.mean(greedy_ms), n, peak, peak_src)
+                              greedy_bytes, statistics.mean(greedy_ms), n, args.workload, peak, peak_src)
     roofline_eval = roofline_entry("full_evaluation_kernel",
                                    "full difference evaluation (Algorithm 2 for all slots), every benefit once",
-                                   4 * n * n + 24 * n, statistics.mean(eval_ms), n, peak, peak_src)
+                                   4 * n * n + 24 * n, statistics.mean(eval_ms), n, args.workload, peak, peak_src)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
