@@ -43,6 +43,7 @@ def parse_args():
     p.add_argument("--workload", choices=["peer", "uniform"], default="peer")
     p.add_argument("--n", type=int, default=10000)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched and served measurements")
     return p.parse_args()
 
 
@@ -93,27 +94,55 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.out = None
+        self.lines = []  # (perf_counter at arrival, line)
+        self.reader = None
+        self.window = (0.0, float("inf"))
 
     def start(self):
+        """Start sampling every 50 ms; the first samples arrive after
+        nvidia-smi has initialised (its start-up stalls the GPU briefly, so
+        the caller waits for them before the timed region)."""
+        import threading
+
         try:
-            self.out = open(os.devnull, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 10:
+            time.sleep(0.05)
+        time.sleep(0.2)
+
+    def mark(self, begin: float, end: float):
+        self.window = (begin, end)
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
-            text, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            text = ""
+        if self.reader is not None:
+            self.reader.join(timeout=5)
+        b, e = self.window
+        # samples from the timed region (plus the one just after it, which
+        # covers its end when the region is shorter than the interval)
+        inside = [ln for t, ln in self.lines if b <= t <= e]
+        after = [ln for t, ln in self.lines if t > e][:1]
+        text = "".join(inside + after)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in text.splitlines():
@@ -252,9 +281,10 @@ def run_ours(args):
     step_ms, eval_ms, greedy_ms, launches = [], [], [], 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    sampler.start()
     barrier()
     torch.cuda.synchronize(dev)
-    sampler.start()
+    t_begin = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k)  # evict the matrix and state from L2, outside the timed events
         e0.record(stream)
@@ -269,6 +299,7 @@ def run_ours(args):
         launches += stats["kernel_launches"]
     torch.cuda.synchronize(dev)
     barrier()
+    sampler.mark(t_begin, time.perf_counter())
     clocks = sampler.stop()
     ms_per_step = statistics.mean(step_ms)
     if world > 1:
@@ -313,6 +344,14 @@ def run_ours(args):
                "sample": (f"oracle greedy start ({tg:.1f} s) + one full difference evaluation ({te:.2f} s) on the "
                           f"same instance; ms/solve = t_greedy + (1 + {stats['sweeps']} sweeps) x t_eval")}
 
+    extra = {}
+    if not args.no_batched:
+        for key, fn in (("batched", run_batched), ("serving", run_serving)):
+            try:
+                extra[key] = fn(dev)
+            except Exception as exc:  # reported, never hides the main measurement
+                extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
+
     value = ms_per_step / world  # job-wide ms per solve (world independent solves per step)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -327,11 +366,158 @@ def run_ours(args):
                   "greedy_rounds": stats["greedy_rounds"], "greedy_rescans": stats["greedy_rescans"],
                   "objective": f, "parity": parity,
                   "step_ms": [round(x, 3) for x in step_ms]},
+        **extra,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- batched and served solves
+def _pool(n_max: int, count: int, seed0: int):
+    """Peer-shaped pool matrices; an instance of size n is the leading n x n
+    block of one of them (the first n agents and jobs of a larger scenario,
+    itself a peer-shaped instance)."""
+    from paper_1106_5694_gb300 import inputs
+
+    return [inputs.peer_shaped(n_max, seed0 + k) for k in range(count)]
+
+
+def run_batched(dev, count=1024, lo=64, hi=4096):
+    """1024 peer-shaped instances, n log-uniform in [64, 4096]: one
+    dgs_solve_batched call vs the same instances solved one dgs_solve call at
+    a time; inputs resident on the device; every result checked equal."""
+    import numpy as np
+    import torch
+
+    from paper_1106_5694_gb300 import binding as B
+    from paper_1106_5694_gb300 import inputs
+
+    ns = inputs.batched_sizes(count, lo, hi, seed=7)
+    pool = _pool(hi, 4, 500)
+    mats = [torch.from_numpy(np.ascontiguousarray(pool[k % 4][:n, :n])).to(dev) for k, n in enumerate(ns)]
+    outs = [torch.empty(int(n), dtype=torch.int32, device=dev) for n in ns]
+    stream = torch.cuda.current_stream(dev)
+    B.dgs_solve_batched(mats[:8], sigma_outs=outs[:8])  # warm-up (graph capture, module load)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, outs, objs, sts, stats = B.dgs_solve_batched(mats, sigma_outs=outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if st != B.DGS_OK:
+        raise RuntimeError(f"batched solve: {B.dgs_status_string(st)} {B.dgs_last_cuda_error()}")
+    t_batched = e0.elapsed_time(e1) / 1e3
+    plain_out = torch.empty(hi, dtype=torch.int32, device=dev)
+    for m in mats[:4]:
+        B.dgs_solve(m, sigma_out=plain_out[: m.shape[0]])
+    torch.cuda.synchronize(dev)
+    same = True
+    e0.record(stream)
+    plain_objs = []
+    for m in mats:
+        st1, _, f1 = B.dgs_solve(m, sigma_out=plain_out[: m.shape[0]])
+        plain_objs.append(f1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = e0.elapsed_time(e1) / 1e3
+    same = plain_objs == objs
+    # assignments of a sample compared element by element
+    for k in range(0, count, 97):
+        st1, sig1, _ = B.dgs_solve(mats[k])
+        same = same and bool(torch.equal(sig1, outs[k]))
+    launches = stats[0]["kernel_launches"]
+    return {
+        "workload": f"{count} peer-shaped instances, n log-uniform in [{lo},{hi}] (seeded), one dgs_solve_batched call, "
+                    "matrices resident in HBM",
+        "instances": count, "sum_n2": int(sum(int(n) * int(n) for n in ns)),
+        "ms": round(t_batched * 1e3, 2), "solves_per_s": round(count / t_batched, 1),
+        "plain_ms": round(t_plain * 1e3, 2), "plain_solves_per_s": round(count / t_plain, 1),
+        "speedup_vs_plain": round(t_plain / t_batched, 2),
+        "gpu_launches": int(launches),
+        "parity": "objectives of all instances and assignments of every 97th equal to one-at-a-time dgs_solve"
+                  if same else "MISMATCH",
+    }
+
+
+def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
+    """Poisson stream of peer-shaped requests, n log-uniform in [256, 16384],
+    host-memory inputs, 40 GB admission budget.  The plain comparison is a
+    FIFO single-server queue over the same arrivals whose service time is a
+    dgs_solve_host call per request (measured), latency = completion -
+    arrival."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1106_5694_gb300 import binding as B
+    from paper_1106_5694_gb300 import inputs
+
+    ns = inputs.batched_sizes(count, lo, hi, seed=11)
+    pool = _pool(hi, 2, 900)
+    reqs = [np.ascontiguousarray(pool[k % 2][:n, :n]) for k, n in enumerate(ns)]
+    # plain: each request alone through the host entry point
+    B.dgs_solve_host(reqs[0], device=dev)
+    service, plain_f = [], []
+    for a in reqs:
+        t0 = time.perf_counter()
+        st, _, f, _ = B.dgs_solve_host(a, device=dev)
+        service.append(time.perf_counter() - t0)
+        plain_f.append(f)
+    capacity = count / sum(service)
+    rate = 0.7 * capacity
+    arrivals = inputs.poisson_arrivals(count, rate, seed=13)
+    done, lat_plain = 0.0, []
+    for t_a, s_i in zip(arrivals, service):
+        done = max(done, t_a) + s_i
+        lat_plain.append(done - t_a)
+    plain_span = done - arrivals[0]
+    # served
+    torch.cuda.set_device(dev)
+    srv = B.Server(budget_bytes=budget)
+    w = srv.dgs_submit(reqs[0][:256, :256].copy())[1]  # warm-up (graph capture)
+    srv.dgs_server_wait(w)
+    tickets = [None] * count
+    t_start = time.perf_counter()
+
+    def submitter():
+        for k, (t_a, a) in enumerate(zip(arrivals, reqs)):
+            delay = t_start + t_a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.dgs_submit(a)[1]
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat, ok, first_submit, last_done = [], True, None, 0
+    for k, t in enumerate(tickets):
+        st, _, f, _, tm = srv.dgs_server_wait(t, timeout_us=600_000_000)
+        ok = ok and st == B.DGS_OK and f == plain_f[k]
+        lat.append((tm["done_ns"] - tm["submit_ns"]) / 1e9)
+        first_submit = tm["submit_ns"] if first_submit is None else min(first_submit, tm["submit_ns"])
+        last_done = max(last_done, tm["done_ns"])
+    info = srv.dgs_server_get_info()[1]
+    srv.dgs_server_destroy()
+    span = (last_done - first_submit) / 1e9
+
+    def pct(x, q):
+        return round(float(np.percentile(np.array(x) * 1e3, q)), 2)
+
+    return {
+        "workload": f"{count} peer-shaped requests, n log-uniform in [{lo},{hi}] (seeded), Poisson arrivals at "
+                    f"{rate:.1f}/s (70% of the plain solver's measured capacity), host-memory inputs, "
+                    f"{budget >> 30} GB admission budget",
+        "rate_per_s": round(rate, 2), "solves_per_s": round(count / span, 2),
+        "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+        "plain": {"solves_per_s": round(count / plain_span, 2), "p50_ms": pct(lat_plain, 50),
+                  "p99_ms": pct(lat_plain, 99), "capacity_solves_per_s": round(capacity, 2),
+                  "how": "FIFO queue over the same arrivals, service = measured dgs_solve_host per request"},
+        "steps": info["steps"], "gpu_launches": info["kernel_launches"],
+        "parity": "every objective equal to the plain solve of the same request" if ok else "MISMATCH",
+    }
 
 
 # ---------------------------------------------------------- reference (oracle)

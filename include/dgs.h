@@ -140,6 +140,93 @@ DGS_API dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* s
                            dgs_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Batched solves.  The paper solves one instance at a time; its motivating
+ * setting (Section 1: a central node that repeatedly assigns peers) solves
+ * many.  dgs_solve_batched runs Algorithm 3 (from the start of Section 3.1)
+ * on `count` independent instances of different sizes together: every
+ * instance keeps its own loop state on the device, and one persistent launch
+ * per kernel works on all instances that are in that kernel's phase
+ * (greedy rounds, first evaluation, switching sweeps).  The host replays a
+ * captured CUDA graph of one step (a fixed number of greedy rounds and
+ * switching iterations) until every instance has finished.  Each result is
+ * bit-identical to dgs_solve_ex on that instance alone with the same options.
+ *
+ *   benefits[k]    DEVICE pointer to instance k's ns[k] x ns[k] int32 matrix
+ *                  (row-major, caller-owned, not written); the array of
+ *                  pointers itself is HOST memory, as are ns[].
+ *   ns[k]          1 <= ns[k] <= DGS_BATCH_MAX_N.
+ *   sigma_outs[k]  DEVICE pointer to ns[k] int32 (agent -> job); host array.
+ *   objectives_out HOST array of count int64.
+ *   options        NULL or shared by all instances: init GREEDY or IDENTITY
+ *                  (USER and traces are not supported: DGS_ERR_INVALID),
+ *                  max_sweeps and deadline_us apply to each instance.
+ *   statuses_out   NULL or HOST array of count statuses (per instance).
+ *   stats_out      NULL or HOST array of count dgs_stats.
+ * Returns DGS_OK when every instance returned DGS_OK, else the status of the
+ * first instance that did not.  Workspace: about 4*n*n + O(n) bytes per
+ * instance, allocated stream-ordered for the call.  Blocks until done; the
+ * work runs on a private stream ordered after `stream`. */
+#define DGS_BATCH_MAX_N 32767
+DGS_API dgs_status dgs_solve_batched(const int32_t* const* benefits, const int32_t* ns, int32_t count,
+                                     int32_t* const* sigma_outs, int64_t* objectives_out,
+                                     const dgs_options* options, dgs_status* statuses_out,
+                                     dgs_stats* stats_out, dgs_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Served solves: a request loop in the spirit of the paper's central
+ * peer-assignment node (Section 1).  A server owns one worker thread and a
+ * device-memory budget on the device that is current when it is created.
+ * Requests are admitted in arrival order as soon as their workspace fits in
+ * the budget (continuous batching): admitted instances join the running
+ * batch at the next step, keep their matrix and loop state resident on the
+ * device until they finish, and overlap on the GPU with every other resident
+ * instance.  Results are bit-identical to dgs_solve of the instance alone.
+ *
+ * dgs_server_create: budget_bytes > 0; max_resident = cap on instances
+ *   resident at once (<= 0: 256).  *out receives the server.
+ * dgs_submit: benefit is n x n int32 row-major, in HOST memory when flags
+ *   has DGS_SUBMIT_HOST, else DEVICE memory of the server's device.  The
+ *   buffer must hold the final values when dgs_submit is called and stay
+ *   valid until the ticket has finished (it is copied into the server's own
+ *   device memory at admission).  1 <= n <= DGS_BATCH_MAX_N.  A request whose
+ *   workspace (dgs_server_request_bytes) exceeds the whole budget returns
+ *   DGS_ERR_BUSY; otherwise it is queued and *ticket identifies it.
+ * dgs_poll: DGS_PENDING while the request is queued or running; otherwise
+ *   the request's final status, with sigma_out_host (n int32, agent -> job,
+ *   HOST), *objective_out, and (if not NULL) *stats and *times filled; a
+ *   finished ticket is forgotten after the poll that returns it.  Unknown
+ *   ticket: DGS_ERR_INVALID.
+ * dgs_server_wait: as dgs_poll, waiting up to timeout_us (< 0: no limit).
+ * dgs_server_destroy: finishes the resident instances, drops queued ones,
+ *   stops the worker and frees the server's device memory. */
+typedef struct dgs_server dgs_server;
+#define DGS_SUBMIT_HOST 1
+typedef struct {
+    int64_t submit_ns;  /* steady-clock times of submission, admission and */
+    int64_t admit_ns;   /* completion (the step that finished the instance) */
+    int64_t done_ns;
+} dgs_request_times;
+typedef struct {
+    int32_t resident;        /* instances on the device now */
+    int32_t queued;          /* requests waiting for admission */
+    int64_t steps;           /* steps run so far */
+    int64_t completed;       /* requests finished so far */
+    size_t bytes_in_use;     /* budget taken by resident instances */
+    int64_t kernel_launches; /* kernels launched by all steps so far */
+} dgs_server_info;
+DGS_API dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_server** out);
+DGS_API size_t dgs_server_request_bytes(int32_t n);
+DGS_API dgs_status dgs_submit(dgs_server* server, const int32_t* benefit, int32_t n, int32_t flags,
+                              uint64_t* ticket);
+DGS_API dgs_status dgs_poll(dgs_server* server, uint64_t ticket, int32_t* sigma_out_host,
+                            int64_t* objective_out, dgs_stats* stats, dgs_request_times* times);
+DGS_API dgs_status dgs_server_wait(dgs_server* server, uint64_t ticket, int64_t timeout_us,
+                                   int32_t* sigma_out_host, int64_t* objective_out, dgs_stats* stats,
+                                   dgs_request_times* times);
+DGS_API dgs_status dgs_server_get_info(dgs_server* server, dgs_server_info* info);
+DGS_API void dgs_server_destroy(dgs_server* server);
+
+/* ------------------------------------------------------------------------
  * Difference evaluation without any allocation.  The paper has no
  * counterpart to this entry point; it exists for callers that must not
  * allocate device memory while they run -- for example a latency-bound

@@ -30,8 +30,12 @@ DGS_INIT_IDENTITY = 2
 DGS_INIT_USER = 3
 
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
-            "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error"]
+            "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
+            "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
+            "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy"]
 DGS_STATIC_MAX_N = 8192
+DGS_BATCH_MAX_N = 32767
+DGS_SUBMIT_HOST = 1
 
 
 class dgs_options(ctypes.Structure):
@@ -66,6 +70,21 @@ class dgs_stats(ctypes.Structure):
 
     def as_dict(self):
         return {name: (float if name.endswith("_ms") else int)(getattr(self, name)) for name, _ in self._fields_}
+
+
+class dgs_request_times(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class dgs_server_info(ctypes.Structure):
+    _fields_ = [
+        ("resident", ctypes.c_int32),
+        ("queued", ctypes.c_int32),
+        ("steps", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("bytes_in_use", ctypes.c_size_t),
+        ("kernel_launches", ctypes.c_int64),
+    ]
 
 
 _lib = None
@@ -105,6 +124,24 @@ def load():
     lib.dgs_status_string.restype = ctypes.c_char_p
     lib.dgs_last_cuda_error.argtypes = []
     lib.dgs_last_cuda_error.restype = ctypes.c_char_p
+    lib.dgs_solve_batched.argtypes = [P, P, i32, P, P, ctypes.POINTER(dgs_options), P, P, P]
+    lib.dgs_solve_batched.restype = ctypes.c_int
+    lib.dgs_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.dgs_server_create.restype = ctypes.c_int
+    lib.dgs_server_request_bytes.argtypes = [i32]
+    lib.dgs_server_request_bytes.restype = ctypes.c_size_t
+    lib.dgs_submit.argtypes = [P, P, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.dgs_submit.restype = ctypes.c_int
+    lib.dgs_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_stats),
+                             ctypes.POINTER(dgs_request_times)]
+    lib.dgs_poll.restype = ctypes.c_int
+    lib.dgs_server_wait.argtypes = [P, ctypes.c_uint64, i64, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_stats),
+                                    ctypes.POINTER(dgs_request_times)]
+    lib.dgs_server_wait.restype = ctypes.c_int
+    lib.dgs_server_get_info.argtypes = [P, ctypes.POINTER(dgs_server_info)]
+    lib.dgs_server_get_info.restype = ctypes.c_int
+    lib.dgs_server_destroy.argtypes = [P]
+    lib.dgs_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -230,3 +267,100 @@ def dgs_greedy_init(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None
     st = load().dgs_greedy_init(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"),
                                 _stream(benefit, stream))
     return st, sigma_out
+
+
+def dgs_solve_batched(benefits, sigma_outs=None, stream=None, **opts):
+    """dgs_solve_batched: ``benefits`` is a list of square int32 CUDA tensors
+    (one device).  Returns (status, sigma_outs, objectives list, statuses
+    list, stats dicts).  Keyword options as dgs_solve_ex (init, max_sweeps,
+    deadline_us)."""
+    count = len(benefits)
+    if count == 0:
+        raise ValueError("empty batch")
+    ns = (ctypes.c_int32 * count)(*[_n(b) for b in benefits])
+    if sigma_outs is None:
+        sigma_outs = [torch.empty(_n(b), dtype=torch.int32, device=b.device) for b in benefits]
+    a_ptrs = (ctypes.c_void_p * count)(*[_dev(b, "benefit").value for b in benefits])
+    o_ptrs = (ctypes.c_void_p * count)(*[_dev(o, "sigma_out").value for o in sigma_outs])
+    objs = (ctypes.c_int64 * count)()
+    stats = (dgs_stats * count)()
+    statuses = (ctypes.c_int * count)()
+    o = _options(**opts)
+    st = load().dgs_solve_batched(a_ptrs, ns, count, o_ptrs, objs, ctypes.byref(o), statuses, stats,
+                                  _stream(benefits[0], stream))
+    return st, sigma_outs, [int(x) for x in objs], [int(x) for x in statuses], [s.as_dict() for s in stats]
+
+
+def dgs_server_request_bytes(n: int) -> int:
+    return int(load().dgs_server_request_bytes(int(n)))
+
+
+class Server:
+    """dgs_server_* handle: create on the current CUDA device, submit host
+    (numpy) or device (torch) matrices, poll or wait for tickets, destroy."""
+
+    def __init__(self, budget_bytes: int, max_resident: int = 0):
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        st = load().dgs_server_create(int(budget_bytes), int(max_resident), ctypes.byref(self._h))
+        if st != DGS_OK:
+            raise RuntimeError(f"dgs_server_create: {dgs_status_string(st)} {dgs_last_cuda_error()}")
+
+    def dgs_submit(self, benefit):
+        """Returns (status, ticket).  The matrix is kept referenced until its ticket is taken."""
+        if isinstance(benefit, torch.Tensor):
+            n, ptr, flags = _n(benefit), _dev(benefit, "benefit"), 0
+        else:
+            benefit = np.ascontiguousarray(benefit, dtype=np.int32)
+            n, ptr, flags = _n(benefit), ctypes.c_void_p(benefit.ctypes.data), DGS_SUBMIT_HOST
+        t = ctypes.c_uint64(0)
+        st = load().dgs_submit(self._h, ptr, n, flags, ctypes.byref(t))
+        if st == DGS_OK:
+            self._keep[int(t.value)] = (benefit, n)
+        return st, int(t.value)
+
+    def _take(self, fn, ticket, *extra):
+        n = self._keep[ticket][1] if ticket in self._keep else 0  # unknown: the library says so
+        out = np.empty(max(n, 1), dtype=np.int32)
+        f = ctypes.c_int64(0)
+        s = dgs_stats()
+        tm = dgs_request_times()
+        st = fn(self._h, ctypes.c_uint64(ticket), *extra, ctypes.c_void_p(out.ctypes.data), ctypes.byref(f),
+                ctypes.byref(s), ctypes.byref(tm))
+        if st != DGS_PENDING:
+            self._keep.pop(ticket, None)
+        times = {"submit_ns": tm.submit_ns, "admit_ns": tm.admit_ns, "done_ns": tm.done_ns}
+        return st, out, int(f.value), s.as_dict(), times
+
+    def dgs_poll(self, ticket: int):
+        """Returns (status, sigma numpy, objective, stats, times); DGS_PENDING while running."""
+        return self._take(load().dgs_poll, ticket)
+
+    def dgs_server_wait(self, ticket: int, timeout_us: int = -1):
+        return self._take(load().dgs_server_wait, ticket, ctypes.c_int64(int(timeout_us)))
+
+    def dgs_server_get_info(self):
+        info = dgs_server_info()
+        st = load().dgs_server_get_info(self._h, ctypes.byref(info))
+        return st, {name: int(getattr(info, name)) for name, _ in info._fields_}
+
+    def dgs_server_destroy(self):
+        if self._h:
+            load().dgs_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.dgs_server_destroy()
+
+    def __del__(self):
+        try:
+            self.dgs_server_destroy()
+        except Exception:
+            pass
+
+
+def dgs_server_create(budget_bytes: int, max_resident: int = 0) -> Server:
+    return Server(budget_bytes, max_resident)

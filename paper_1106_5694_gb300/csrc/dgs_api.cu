@@ -145,6 +145,46 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
     return ar.used;
 }
 
+}  // namespace
+
+namespace dgs {
+// Workspace of one batched or served instance inside a caller-provided block
+// (base == nullptr: only the size).  need_copy: w.a is a re-pitched copy in
+// the block (pitch round_up(n, 4)); otherwise the caller sets w.a.
+size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in) {
+    Plan p;
+    p.need_copy = need_copy;
+    p.need_at = true;
+    p.lda = need_copy ? round_up32(n, 4) : n;
+    p.ldt = round_up32(n, 64);
+    Arena ar;
+    ar.base = base;
+    Workspace w{};
+    CtlGlobal ctl{};
+    uint8_t* seen = nullptr;
+    int32_t* a_copy = nullptr;
+    const size_t bytes = carve(ar, w, p, n, &ctl, &seen, &a_copy);
+    if (base == nullptr) return bytes;
+    w.n = n;
+    w.lda = p.lda;
+    w.ldt = p.ldt;
+    w.exact_keys = env_exact_keys();
+    w.a = a_copy;
+    const int32_t mode = controller_smem_mode(n);
+    in->w = w;
+    in->ctl = ctl;
+    in->seen = seen;
+    in->ctl_mode = mode;
+    in->ctl_cap = controller_list_cap(n, mode);
+    in->zero_begin = reinterpret_cast<char*>(w.sigma);
+    in->zero_bytes = (size_t)(base + bytes - in->zero_begin);
+    return bytes;
+}
+}  // namespace dgs
+
+namespace {
+using namespace dgs;
+
 // Everything one call needs, released in the destructor (stream-ordered).
 struct Solve {
     cudaStream_t s;

@@ -1,0 +1,744 @@
+// dgs_batch.cu -- batched and served solves (include/dgs.h: dgs_solve_batched,
+// dgs_server_*).
+//
+// Many instances of different sizes advance together.  Each instance owns a
+// slot: its workspace (the same layout as a single solve) and its loop state
+// in one device array of DeviceState, indexed by slot.  An instance moves
+// through stages (new -> greedy -> start -> switch -> done) on the device;
+// every batched kernel is a persistent grid that walks a table of (instance,
+// block) entries and acts only on the instances in the stage it serves, with
+// the instance's own n, sigma and loop state.  One step is a fixed sequence
+// of launches:
+//
+//   init (fresh slots) -> pass 1 -> advance(new)
+//   -> greedy rounds x kGreedyPerStep -> advance(greedy)
+//   -> start, first full evaluation -> advance(start)
+//   -> switching iterations x kSwitchPerStep -> finish -> advance(switch)
+//   -> copy of every slot's loop state to pinned host memory
+//
+// captured once as a CUDA graph and replayed; the tables have a fixed
+// capacity per slot, so admitting or retiring instances only rewrites the
+// tables' contents, never the graph.  Within a stage an instance executes
+// exactly the launches of a single solve, in the same order, so its result
+// is bit-identical to dgs_solve_ex on that instance alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dgs.h"
+#include "dgs_internal.cuh"
+
+namespace dgs {
+namespace {
+
+constexpr int32_t kGreedyPerStep = 16;  // greedy rounds per step
+constexpr int32_t kSwitchPerStep = 8;   // switching iterations per step
+
+// Table partitions and the most entries one instance can take in each.
+enum : int32_t { kTabRows = 0, kTabTiles, kTabOwners, kTabEval, kTabRowTasks, kTabOne, kTabCount };
+constexpr int32_t kMaxPerInstance[kTabCount] = {
+    64,       // rows: ceil(n / 512), n <= 32767
+    152 * 8,  // tiles of pass 1
+    512,      // owners: ceil(n / 64)
+    152,      // evaluation blocks
+    152,      // row-task blocks
+    1         // one
+};
+
+int32_t ceil_div(int64_t a, int64_t b) { return (int32_t)((a + b - 1) / b); }
+int32_t clampi(int32_t x, int32_t lo, int32_t hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// Blocks that instance of size n gets in each partition.
+int32_t blocks_for(int32_t tab, int32_t n) {
+    switch (tab) {
+        case kTabRows: return clampi(ceil_div(n, 512), 1, kMaxPerInstance[kTabRows]);
+        case kTabTiles: {
+            const int64_t t = (int64_t)ceil_div(n, 64) * ceil_div(n, 64);
+            return clampi(ceil_div(t, 4), 1, kMaxPerInstance[kTabTiles]);
+        }
+        case kTabOwners: return clampi(ceil_div(n, 64), 1, kMaxPerInstance[kTabOwners]);
+        case kTabEval: {
+            const int32_t nb = ceil_div(n, 64), chunks = ceil_div(nb, evaluation_strip());
+            return clampi(ceil_div((int64_t)nb * chunks, 2), 1, kMaxPerInstance[kTabEval]);
+        }
+        case kTabRowTasks: return clampi(n / 16, 1, kMaxPerInstance[kTabRowTasks]);
+        default: return 1;
+    }
+}
+
+thread_local char g_err[512];
+
+dgs_status fail(cudaError_t e, const char* what) {
+    snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+    set_last_error(g_err);
+    return DGS_ERR_CUDA;
+}
+
+#define B_CUDA(expr, what)                              \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return fail(_e, what);   \
+    } while (0)
+
+dgs_status status_of(const DeviceState& h) {
+    if (h.status == kDone) return DGS_OK;
+    if (h.status == kTimeout) return DGS_TIMEOUT;
+    if (h.status == kError) {
+        if (h.error == kErrRange) return DGS_ERR_RANGE;
+        if (h.error == kErrUserInit) return DGS_ERR_INVALID;
+        return DGS_ERR_INTERNAL;
+    }
+    return DGS_ERR_INTERNAL;  // finished without a final status
+}
+
+void stats_of(const DeviceState& h, int64_t launches, dgs_stats* out) {
+    memset(out, 0, sizeof(*out));
+    out->sweeps = h.sweeps;
+    out->events = h.events;
+    out->swaps_applied = h.swaps;
+    out->greedy_rounds = h.greedy_rounds;
+    out->full_evaluations = h.full_evals + 1;
+    out->row_updates = h.row_updates;
+    out->rows_recomputed = h.rows_recomputed;
+    out->initial_objective = h.f_initial;
+    out->kernel_launches = launches;
+    out->greedy_rescans = h.greedy_rescans;
+}
+
+// Slots, tables and the step graph of one batch of resident instances.
+class Engine {
+  public:
+    explicit Engine(int32_t capacity) : cap_(capacity) {}
+    Engine(const Engine&) = delete;
+    Engine& operator=(const Engine&) = delete;
+
+    ~Engine() {
+        if (exec_) cudaGraphExecDestroy(exec_);
+        if (stream_) cudaStreamSynchronize(stream_);
+        if (d_inst_) cudaFree(d_inst_);
+        if (d_st_) cudaFree(d_st_);
+        if (d_ent_) cudaFree(d_ent_);
+        if (d_cnt_) cudaFree(d_cnt_);
+        if (h_inst_) cudaFreeHost(h_inst_);
+        if (h_st_) cudaFreeHost(h_st_);
+        if (h_ent_) cudaFreeHost(h_ent_);
+        if (h_cnt_) cudaFreeHost(h_cnt_);
+        if (stream_) cudaStreamDestroy(stream_);
+    }
+
+    dgs_status init() {
+        B_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking), "stream");
+        B_CUDA(cudaMalloc(&d_inst_, sizeof(Instance) * cap_), "instance table");
+        B_CUDA(cudaMalloc(&d_st_, sizeof(DeviceState) * cap_), "loop states");
+        B_CUDA(cudaMemset(d_st_, 0, sizeof(DeviceState) * cap_), "loop states");
+        size_t total = 0;
+        for (int32_t t = 0; t < kTabCount; ++t) {
+            off_[t] = total;
+            total += (size_t)kMaxPerInstance[t] * cap_;
+        }
+        B_CUDA(cudaMalloc(&d_ent_, sizeof(BatchEntry) * total), "work tables");
+        B_CUDA(cudaMalloc(&d_cnt_, sizeof(int32_t) * kTabCount), "work table counts");
+        B_CUDA(cudaMallocHost(&h_inst_, sizeof(Instance) * cap_), "instance table (host)");
+        B_CUDA(cudaMallocHost(&h_st_, sizeof(DeviceState) * cap_), "loop states (host)");
+        B_CUDA(cudaMallocHost(&h_ent_, sizeof(BatchEntry) * total), "work tables (host)");
+        B_CUDA(cudaMallocHost(&h_cnt_, sizeof(int32_t) * kTabCount), "counts (host)");
+        memset(h_inst_, 0, sizeof(Instance) * cap_);
+        memset(h_st_, 0, sizeof(DeviceState) * cap_);
+        used_.assign(cap_, 0);
+        return DGS_OK;
+    }
+
+    cudaStream_t stream() const { return stream_; }
+    int32_t capacity() const { return cap_; }
+    bool used(int32_t k) const { return used_[k] != 0; }
+    const DeviceState& state(int32_t k) const { return h_st_[k]; }
+    int64_t launches_per_step() const { return launches_per_step_; }
+    int32_t free_slot() const {
+        for (int32_t k = 0; k < cap_; ++k)
+            if (!used_[k]) return k;
+        return -1;
+    }
+
+    // Place an instance in slot k.  mem: carve_instance(nullptr, n, with_copy)
+    // bytes of device memory.  Without a copy region the matrix a is used in
+    // place; with one, a (if not null) is the caller's unpitched matrix that
+    // the init kernel re-pitches into the region, and a == null means the
+    // region already holds the pitched matrix.
+    void place(int32_t k, char* mem, int32_t n, bool with_copy, const int32_t* a, int32_t* sigma_out,
+               int32_t init_mode, int32_t max_sweeps, int64_t deadline_us) {
+        Instance in{};
+        carve_instance(mem, n, with_copy, &in);
+        if (!with_copy) in.w.a = a;
+        else in.a_src = a;
+        in.w.st = d_st_ + k;
+        in.fresh = 1;
+        in.max_sweeps = max_sweeps;
+        in.init_mode = init_mode;
+        in.deadline_us = deadline_us;
+        in.sigma_out = sigma_out;
+        h_inst_[k] = in;
+        h_st_[k] = DeviceState{};
+        used_[k] = 1;
+        tables_dirty_ = true;
+        inst_dirty_ = true;
+    }
+
+    void vacate(int32_t k) {
+        used_[k] = 0;
+        memset(&h_inst_[k], 0, sizeof(Instance));
+        tables_dirty_ = true;
+        inst_dirty_ = true;
+    }
+
+    // One step: upload what changed, replay the step graph, wait for it and
+    // read every slot's loop state.
+    dgs_status step() {
+        if (tables_dirty_) build_tables();
+        if (inst_dirty_)
+            B_CUDA(cudaMemcpyAsync(d_inst_, h_inst_, sizeof(Instance) * cap_, cudaMemcpyHostToDevice, stream_),
+                   "upload instances");
+        if (tables_dirty_) {
+            size_t total = 0;
+            for (int32_t t = 0; t < kTabCount; ++t) total = std::max(total, off_[t] + (size_t)h_cnt_[t]);
+            B_CUDA(cudaMemcpyAsync(d_ent_, h_ent_, sizeof(BatchEntry) * total, cudaMemcpyHostToDevice, stream_),
+                   "upload tables");
+            B_CUDA(cudaMemcpyAsync(d_cnt_, h_cnt_, sizeof(int32_t) * kTabCount, cudaMemcpyHostToDevice, stream_),
+                   "upload counts");
+        }
+        if (!exec_) {
+            dgs_status st = capture();
+            if (st != DGS_OK) return st;
+        }
+        B_CUDA(cudaGraphLaunch(exec_, stream_), "step graph");
+        B_CUDA(cudaStreamSynchronize(stream_), "step");
+        // fresh instances were initialised by this step
+        bool cleared = false;
+        for (int32_t k = 0; k < cap_; ++k)
+            if (used_[k] && h_inst_[k].fresh) {
+                h_inst_[k].fresh = 0;
+                cleared = true;
+            }
+        inst_dirty_ = cleared;
+        tables_dirty_ = false;
+        ++steps_;
+        return DGS_OK;
+    }
+
+    int64_t steps() const { return steps_; }
+
+  private:
+    BatchTable table(int32_t t) const {
+        return BatchTable{d_inst_, d_ent_ + off_[t], d_cnt_ + t};
+    }
+
+    void build_tables() {
+        for (int32_t t = 0; t < kTabCount; ++t) {
+            int32_t c = 0;
+            BatchEntry* e = h_ent_ + off_[t];
+            for (int32_t k = 0; k < cap_; ++k) {
+                if (!used_[k]) continue;
+                const int32_t nb = blocks_for(t, h_inst_[k].w.n);
+                for (int32_t b = 0; b < nb; ++b) e[c++] = BatchEntry{k, b, nb, 0};
+            }
+            h_cnt_[t] = c;
+        }
+    }
+
+    dgs_status enqueue_step(cudaStream_t s, int64_t* launches) {
+        int64_t L = 0;
+#define B_LAUNCH(expr, n_kernels, what)           \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return fail(_e, what); \
+        L += (n_kernels);                         \
+    } while (0)
+        const BatchTable rows = table(kTabRows), tiles = table(kTabTiles), owners = table(kTabOwners),
+                         eval = table(kTabEval), rowt = table(kTabRowTasks), one = table(kTabOne);
+        B_LAUNCH(launch_b_init(rows, s), 1, "init");
+        B_LAUNCH(launch_b_pass1(tiles, s), 1, "pass 1");
+        B_LAUNCH(launch_b_advance(one, kStageNew, s), 1, "advance");
+        for (int32_t r = 0; r < kGreedyPerStep; ++r) B_LAUNCH(launch_b_greedy_round(rows, owners, s), 3, "greedy round");
+        B_LAUNCH(launch_b_advance(one, kStageGreedy, s), 1, "advance");
+        B_LAUNCH(launch_b_start(rows, s), 1, "start");
+        B_LAUNCH(launch_b_evaluation(eval, kStageStart, 0, evaluation_strip(), s), 1, "evaluation");
+        B_LAUNCH(launch_b_advance(one, kStageStart, s), 1, "advance");
+        for (int32_t i = 0; i < kSwitchPerStep; ++i) {
+            B_LAUNCH(launch_b_mark_rescan(rows, s), 1, "mark");
+            B_LAUNCH(launch_b_evaluation(eval, kStageSwitch, 1, evaluation_strip(), s), 1, "re-evaluation");
+            B_LAUNCH(launch_b_row_tasks(rowt, s), 1, "row tasks");
+            B_LAUNCH(launch_b_prepare_edges(rows, s), 1, "prepare");
+            B_LAUNCH(launch_b_controller(one, s), 1, "controller");
+        }
+        B_LAUNCH(launch_b_finish(rows, s), 1, "finish");
+        B_LAUNCH(launch_b_advance(one, kStageSwitch, s), 1, "advance");
+#undef B_LAUNCH
+        B_CUDA(cudaMemcpyAsync(h_st_, d_st_, sizeof(DeviceState) * cap_, cudaMemcpyDeviceToHost, s), "read states");
+        *launches = L;
+        return DGS_OK;
+    }
+
+    dgs_status capture() {
+        // kernel attributes are set outside the capture (first launch of each
+        // kernel on this device), by one uncaptured pass over empty tables
+        {
+            const int32_t zero[kTabCount] = {0, 0, 0, 0, 0, 0};
+            int32_t* saved = d_cnt_;
+            int32_t* d_zero = nullptr;
+            B_CUDA(cudaMallocAsync(&d_zero, sizeof(zero), stream_), "counts");
+            B_CUDA(cudaMemcpyAsync(d_zero, zero, sizeof(zero), cudaMemcpyHostToDevice, stream_), "counts");
+            B_CUDA(cudaStreamSynchronize(stream_), "counts");
+            d_cnt_ = d_zero;
+            int64_t l = 0;
+            const dgs_status st = enqueue_step(stream_, &l);
+            d_cnt_ = saved;
+            cudaFreeAsync(d_zero, stream_);
+            if (st != DGS_OK) return st;
+            B_CUDA(cudaStreamSynchronize(stream_), "warm-up step");
+        }
+        cudaGraph_t g = nullptr;
+        B_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int64_t launches = 0;
+        const dgs_status st = enqueue_step(stream_, &launches);
+        const cudaError_t e = cudaStreamEndCapture(stream_, &g);
+        if (st != DGS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(e, "end capture");
+        const cudaError_t ei = cudaGraphInstantiate(&exec_, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return fail(ei, "instantiate step graph");
+        launches_per_step_ = launches;
+        return DGS_OK;
+    }
+
+    int32_t cap_;
+    cudaStream_t stream_ = nullptr;
+    Instance* d_inst_ = nullptr;
+    Instance* h_inst_ = nullptr;
+    DeviceState* d_st_ = nullptr;
+    DeviceState* h_st_ = nullptr;
+    BatchEntry* d_ent_ = nullptr;
+    BatchEntry* h_ent_ = nullptr;
+    int32_t* d_cnt_ = nullptr;
+    int32_t* h_cnt_ = nullptr;
+    size_t off_[kTabCount] = {};
+    std::vector<char> used_;
+    bool tables_dirty_ = true, inst_dirty_ = true;
+    cudaGraphExec_t exec_ = nullptr;
+    int64_t launches_per_step_ = 0;
+    int64_t steps_ = 0;
+};
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Upper bound on the steps of one instance: every step runs kGreedyPerStep
+// greedy rounds (at most n in all) and kSwitchPerStep switching iterations
+// (at most 16 n + 4096 in all, the bound of the single solve).
+int64_t max_steps_for(int32_t n) {
+    return 4 + ceil_div(n + 1, kGreedyPerStep) + ceil_div(16ll * n + 4096, kSwitchPerStep);
+}
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+}  // namespace dgs
+
+using namespace dgs;
+
+// ------------------------------------------------------------- batched solve
+extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const int32_t* ns, int32_t count,
+                                        int32_t* const* sigma_outs, int64_t* objectives_out,
+                                        const dgs_options* options, dgs_status* statuses_out,
+                                        dgs_stats* stats_out, dgs_stream_t stream) {
+    if (count <= 0 || !benefits || !ns || !sigma_outs || !objectives_out) return DGS_ERR_INVALID;
+    dgs_options o;
+    dgs_default_options(&o);
+    if (options) o = *options;
+    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY) return DGS_ERR_INVALID;
+    if (o.trace_capacity > 0) return DGS_ERR_INVALID;
+    int32_t max_n = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        if (!benefits[k] || !sigma_outs[k] || ns[k] <= 0 || ns[k] > DGS_BATCH_MAX_N) return DGS_ERR_INVALID;
+        max_n = std::max(max_n, ns[k]);
+    }
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    Engine eng(count);
+    dgs_status st = eng.init();
+    if (st != DGS_OK) return st;
+    cudaStream_t s = eng.stream();
+    // the private stream starts after the caller's stream
+    cudaEvent_t ev = nullptr;
+    B_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(s, ev, 0);
+    // one allocation for every instance's workspace
+    std::vector<size_t> off(count);
+    std::vector<char> copy(count);
+    size_t total = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        copy[k] = (ns[k] % 4) != 0 || !aligned16(benefits[k]);
+        off[k] = total;
+        total += carve_instance(nullptr, ns[k], copy[k] != 0, nullptr);
+    }
+    char* mem = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), total, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        cudaEventDestroy(ev);
+        snprintf(g_err, sizeof(g_err), "batched workspace of %zu bytes", total);
+        set_last_error(g_err);
+        return DGS_ERR_OOM;
+    }
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return fail(e, "cudaMallocAsync");
+    }
+    for (int32_t k = 0; k < count; ++k)
+        eng.place(k, mem + off[k], ns[k], copy[k] != 0, benefits[k], sigma_outs[k], o.init, o.max_sweeps,
+                  o.deadline_us);
+    const int64_t max_steps = max_steps_for(max_n);
+    bool all_done = false;
+    for (int64_t it = 0; it < max_steps && st == DGS_OK; ++it) {
+        st = eng.step();
+        if (st != DGS_OK) break;
+        all_done = true;
+        for (int32_t k = 0; k < count; ++k)
+            if (eng.state(k).stage != kStageDone) {
+                all_done = false;
+                break;
+            }
+        if (all_done) break;
+    }
+    cudaFreeAsync(mem, s);
+    cudaEventRecord(ev, s);
+    cudaStreamWaitEvent(user, ev, 0);
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(ev);
+    if (st != DGS_OK) return st;
+    if (!all_done) {
+        set_last_error("batched solve did not finish");
+        return DGS_ERR_INTERNAL;
+    }
+    dgs_status first = DGS_OK;
+    const int64_t launches = eng.launches_per_step() * eng.steps();
+    for (int32_t k = 0; k < count; ++k) {
+        const DeviceState& h = eng.state(k);
+        const dgs_status sk = status_of(h);
+        objectives_out[k] = h.f;
+        if (statuses_out) statuses_out[k] = sk;
+        if (stats_out) stats_of(h, launches, &stats_out[k]);
+        if (first == DGS_OK && sk != DGS_OK) first = sk;
+    }
+    return first;
+}
+
+// ------------------------------------------------------------------- server
+struct dgs_server {
+    struct Request {
+        uint64_t ticket;
+        const int32_t* a;
+        int32_t n;
+        int32_t flags;
+        size_t bytes;
+        int64_t submit_ns;
+    };
+    struct Resident {
+        uint64_t ticket = 0;
+        char* mem = nullptr;
+        size_t bytes = 0;
+        int32_t n = 0;
+        int32_t* out = nullptr;
+        int64_t submit_ns = 0, admit_ns = 0;
+    };
+    struct Result {
+        dgs_status status;
+        int64_t objective;
+        std::vector<int32_t> sigma;
+        dgs_stats stats;
+        dgs_request_times times;
+    };
+
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;  // guarded by mu
+    Engine eng;
+    std::vector<Resident> slots;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> queue;
+    std::unordered_map<uint64_t, Result> results;
+    std::unordered_map<uint64_t, int32_t> pending;  // ticket -> 0 queued / 1 resident
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    dgs_status fatal = DGS_OK;
+    int64_t completed = 0;
+    int32_t resident_count = 0;  // guarded by mu (the worker alone changes it)
+    int64_t steps = 0, launches = 0;  // guarded by mu
+
+    int32_t eng_resident() {
+        std::lock_guard<std::mutex> lk(mu);
+        return resident_count;
+    }
+    int32_t* h_sigma = nullptr;  // pinned staging for results
+    size_t h_sigma_cap = 0;
+
+    explicit dgs_server(int32_t cap) : eng(cap), slots(cap) {}
+
+    void finish_all_pending(dgs_status why) {
+        for (auto& kv : pending) {
+            Result r{};
+            r.status = why;
+            results[kv.first] = std::move(r);
+        }
+        pending.clear();
+        queue.clear();
+    }
+
+    void run() {
+        cudaSetDevice(device);
+        for (;;) {
+            std::vector<Request> admit;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (resident_count == 0) {
+                    cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+                    if (stop && resident_count == 0) break;
+                }
+                if (!stop) {
+                    int32_t free_slots = eng.capacity() - resident_count;
+                    while (!queue.empty() && free_slots > 0 && used + queue.front().bytes <= budget) {
+                        admit.push_back(queue.front());
+                        used += queue.front().bytes;
+                        pending[queue.front().ticket] = 1;
+                        queue.pop_front();
+                        --free_slots;
+                    }
+                }
+            }
+            dgs_status st = DGS_OK;
+            for (const Request& r : admit) {
+                st = admit_one(r);
+                if (st != DGS_OK) break;
+            }
+            if (st == DGS_OK && eng_resident() > 0) {
+                st = eng.step();
+                std::lock_guard<std::mutex> lk(mu);
+                steps = eng.steps();
+                launches = eng.launches_per_step() * steps;
+            }
+            if (st == DGS_OK) st = retire_done();
+            if (st != DGS_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                fatal = st;
+                finish_all_pending(st);
+                stop = true;
+                cv_done.notify_all();
+                break;
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            if (stop && resident_count == 0) break;
+        }
+    }
+
+    dgs_status admit_one(const Request& r) {
+        cudaStream_t s = eng.stream();
+        const int32_t k = eng.free_slot();
+        if (k < 0) return DGS_ERR_INTERNAL;
+        Resident& R = slots[k];
+        R = Resident{};
+        R.ticket = r.ticket;
+        R.n = r.n;
+        R.bytes = r.bytes;
+        R.submit_ns = r.submit_ns;
+        R.admit_ns = now_ns();
+        const cudaError_t ea = cudaMallocAsync(reinterpret_cast<void**>(&R.mem), r.bytes, s);
+        if (ea == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
+            cudaGetLastError();
+            Result res{};
+            res.status = DGS_ERR_OOM;
+            res.times.submit_ns = r.submit_ns;
+            res.times.admit_ns = res.times.done_ns = now_ns();
+            std::lock_guard<std::mutex> lk(mu);
+            used -= r.bytes;
+            pending.erase(r.ticket);
+            results[r.ticket] = std::move(res);
+            ++completed;
+            cv_done.notify_all();
+            R = Resident{};
+            return DGS_OK;
+        }
+        if (ea != cudaSuccess) return fail(ea, "request workspace");
+        // the instance's matrix, pitched (round_up(n, 4)) inside its workspace
+        Instance probe{};
+        const size_t ws = carve_instance(R.mem, r.n, true, &probe);
+        R.out = reinterpret_cast<int32_t*>(R.mem + ws);
+        const size_t lda = (size_t)probe.w.lda;
+        int32_t* a_dev = const_cast<int32_t*>(probe.w.a);
+        if (lda != (size_t)r.n) B_CUDA(cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, s), "pad");
+        const cudaMemcpyKind kind = (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        B_CUDA(cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, s), "upload");
+        eng.place(k, R.mem, r.n, true, nullptr, R.out, DGS_INIT_GREEDY, 0, 0);
+        std::lock_guard<std::mutex> lk(mu);
+        ++resident_count;
+        return DGS_OK;
+    }
+
+    dgs_status retire_done() {
+        cudaStream_t s = eng.stream();
+        for (int32_t k = 0; k < eng.capacity(); ++k) {
+            if (!eng.used(k) || eng.state(k).stage != kStageDone) continue;
+            Resident& R = slots[k];
+            const DeviceState& h = eng.state(k);
+            Result res{};
+            res.status = status_of(h);
+            res.objective = h.f;
+            stats_of(h, eng.launches_per_step() * eng.steps(), &res.stats);
+            if (res.status == DGS_OK || res.status == DGS_TIMEOUT) {
+                if (h_sigma_cap < (size_t)R.n) {
+                    if (h_sigma) cudaFreeHost(h_sigma);
+                    h_sigma = nullptr;
+                    B_CUDA(cudaMallocHost(&h_sigma, sizeof(int32_t) * R.n), "result staging");
+                    h_sigma_cap = R.n;
+                }
+                B_CUDA(cudaMemcpyAsync(h_sigma, R.out, sizeof(int32_t) * R.n, cudaMemcpyDeviceToHost, s),
+                       "read result");
+                B_CUDA(cudaStreamSynchronize(s), "read result");
+                res.sigma.assign(h_sigma, h_sigma + R.n);
+            }
+            res.times.submit_ns = R.submit_ns;
+            res.times.admit_ns = R.admit_ns;
+            res.times.done_ns = now_ns();
+            cudaFreeAsync(R.mem, s);
+            eng.vacate(k);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                --resident_count;
+                used -= R.bytes;
+                pending.erase(R.ticket);
+                results[R.ticket] = std::move(res);
+                ++completed;
+            }
+            cv_done.notify_all();
+            R = Resident{};
+        }
+        return DGS_OK;
+    }
+};
+
+namespace {
+size_t request_bytes(int32_t n) {
+    // workspace with the pitched matrix, then the result
+    return carve_instance(nullptr, n, true, nullptr) + ((size_t)n * 4 + 255) / 256 * 256;
+}
+
+dgs_status take_result(dgs_server* sv, uint64_t ticket, int32_t* sigma_out_host, int64_t* objective_out,
+                       dgs_stats* stats, dgs_request_times* times) {
+    auto it = sv->results.find(ticket);
+    dgs_server::Result& r = it->second;
+    const dgs_status st = r.status;
+    if (st == DGS_OK || st == DGS_TIMEOUT) {
+        if (sigma_out_host) memcpy(sigma_out_host, r.sigma.data(), sizeof(int32_t) * r.sigma.size());
+        if (objective_out) *objective_out = r.objective;
+    }
+    if (stats) *stats = r.stats;
+    if (times) *times = r.times;
+    sv->results.erase(it);
+    return st;
+}
+}  // namespace
+
+extern "C" {
+
+size_t dgs_server_request_bytes(int32_t n) {
+    if (n <= 0 || n > DGS_BATCH_MAX_N) return 0;
+    return request_bytes(n);
+}
+
+dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_server** out) {
+    if (!out || budget_bytes == 0) return DGS_ERR_INVALID;
+    *out = nullptr;
+    const int32_t cap = max_resident > 0 ? max_resident : 256;
+    dgs_server* sv = new dgs_server(cap);
+    B_CUDA(cudaGetDevice(&sv->device), "cudaGetDevice");
+    sv->budget = budget_bytes;
+    dgs_status st = sv->eng.init();
+    if (st != DGS_OK) {
+        delete sv;
+        return st;
+    }
+    sv->worker = std::thread([sv] { sv->run(); });
+    *out = sv;
+    return DGS_OK;
+}
+
+dgs_status dgs_submit(dgs_server* sv, const int32_t* benefit, int32_t n, int32_t flags, uint64_t* ticket) {
+    if (!sv || !benefit || !ticket || n <= 0 || n > DGS_BATCH_MAX_N) return DGS_ERR_INVALID;
+    const size_t bytes = request_bytes(n);
+    if (bytes > sv->budget) return DGS_ERR_BUSY;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return sv->fatal != DGS_OK ? sv->fatal : DGS_ERR_INVALID;
+    const uint64_t t = sv->next_ticket++;
+    sv->queue.push_back(dgs_server::Request{t, benefit, n, flags, bytes, now_ns()});
+    sv->pending[t] = 0;
+    *ticket = t;
+    sv->cv_work.notify_one();
+    return DGS_OK;
+}
+
+dgs_status dgs_poll(dgs_server* sv, uint64_t ticket, int32_t* sigma_out_host, int64_t* objective_out,
+                    dgs_stats* stats, dgs_request_times* times) {
+    if (!sv) return DGS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->results.count(ticket)) return take_result(sv, ticket, sigma_out_host, objective_out, stats, times);
+    return sv->pending.count(ticket) ? DGS_PENDING : DGS_ERR_INVALID;
+}
+
+dgs_status dgs_server_wait(dgs_server* sv, uint64_t ticket, int64_t timeout_us, int32_t* sigma_out_host,
+                           int64_t* objective_out, dgs_stats* stats, dgs_request_times* times) {
+    if (!sv) return DGS_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto ready = [&] { return sv->results.count(ticket) || !sv->pending.count(ticket); };
+    if (timeout_us < 0) sv->cv_done.wait(lk, ready);
+    else sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (sv->results.count(ticket)) return take_result(sv, ticket, sigma_out_host, objective_out, stats, times);
+    return sv->pending.count(ticket) ? DGS_PENDING : DGS_ERR_INVALID;
+}
+
+dgs_status dgs_server_get_info(dgs_server* sv, dgs_server_info* info) {
+    if (!sv || !info) return DGS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    info->resident = sv->resident_count;
+    info->queued = (int32_t)sv->queue.size();
+    info->steps = sv->steps;
+    info->completed = sv->completed;
+    info->bytes_in_use = sv->used;
+    info->kernel_launches = sv->launches;
+    return sv->fatal;
+}
+
+void dgs_server_destroy(dgs_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->queue.clear();
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    if (sv->h_sigma) cudaFreeHost(sv->h_sigma);
+    delete sv;
+}
+
+}  // extern "C"

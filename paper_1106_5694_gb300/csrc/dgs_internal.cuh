@@ -13,6 +13,17 @@ constexpr int32_t kMaxN = 1 << 17;           // index fields are 17 bits in plac
 constexpr int32_t kBenefitLimit = 1 << 29;   // |a| < 2^29 keeps gains exact in int32
 constexpr uint32_t kSpinLimit = 1u << 26;    // bound on every device-side wait loop
 
+// Stage of an instance in a batched or served solve (DeviceState::stage);
+// every batched kernel acts only on the instances in the stage it serves.
+enum : int32_t {
+    kStageFree = 0,    // slot unused
+    kStageNew = 1,     // workspace initialised, pass 1 (transpose, range check) next
+    kStageGreedy = 2,  // locally-dominant greedy rounds
+    kStageStart = 3,   // sigma, D, f from the start; first full evaluation
+    kStageSwitch = 4,  // switching loop (Algorithm 3)
+    kStageDone = 5     // finished; assignment written to the instance's output
+};
+
 // Loop status (DeviceState::status).
 enum : int32_t { kRunning = 0, kDone = 1, kTimeout = 2, kError = 3 };
 // Device-side error codes (DeviceState::error).
@@ -43,6 +54,8 @@ struct DeviceState {
     long long greedy_rescans;  // rows of a / at rescanned by the greedy start
     uint32_t bar_count;      // grid barrier of cooperative launches: arrivals
     uint32_t bar_gen;        //   and generation
+    int32_t stage;           // kStage* (batched and served solves only)
+    int32_t init_mode;       // batched: DGS_INIT_* of the instance (from Instance::init_mode)
     int64_t f;               // current objective
     int64_t f_initial;
     int64_t swaps;           // committed exchanges
@@ -87,6 +100,64 @@ struct Workspace {
     DeviceState* st;
     unsigned long long* phase_ns;  // optional phase timers (DGS_PHASE_TIMERS=1), else null
 };
+
+// Controller scratch in global memory (the parts that do not live in shared
+// memory for this n; null otherwise) and its work lists.
+struct CtlGlobal {
+    uint32_t* res;
+    uint8_t* claimed;
+    uint8_t* estate;
+    void* edges;
+    int32_t* acc;
+    int32_t* und;
+};
+
+// One instance of a batched or served solve, as the batched kernels see it.
+struct Instance {
+    Workspace w;
+    CtlGlobal ctl;
+    int32_t ctl_mode;          // controller scratch placement for this n
+    int32_t ctl_cap;           // entries of each controller list in shared memory
+    int32_t fresh;             // 1: the next step initialises this instance
+    int32_t max_sweeps;        // options of the instance
+    int32_t init_mode;         // DGS_INIT_GREEDY / _IDENTITY / _USER
+    int32_t pad_;
+    int64_t deadline_us;
+    const int32_t* a_src;      // caller's matrix when w.a is a re-pitched copy, else null
+    const int32_t* user_tau;   // DGS_INIT_USER start
+    int32_t* sigma_out;        // where the finished assignment goes (device)
+    char* zero_begin;          // small arrays to clear at initialisation
+    size_t zero_bytes;
+    uint8_t* seen;             // start validation flags
+};
+
+// One entry of a batched work table: block bid of the nblk blocks that one
+// launch gives to instance inst.  Each CTA of a persistent batched launch
+// walks the entries blockIdx.x, blockIdx.x + gridDim.x, ...
+struct BatchEntry {
+    int32_t inst, bid, nblk, pad;
+};
+struct BatchTable {
+    const Instance* inst;
+    const BatchEntry* e;
+    const int32_t* count;  // device: number of entries
+};
+
+// Walk this CTA's entries of a batched table, calling f(instance, bid, nblk)
+// for the entries whose instance is in `stage` (stage < 0: every instance
+// not free).  The stage is written only by the advance kernel, never during
+// another batched launch, so the test is uniform across the CTA.
+template <typename F>
+__device__ __forceinline__ void for_each_entry(const BatchTable& t, int32_t stage, F&& f) {
+    const int32_t count = *t.count;
+    for (int32_t g = blockIdx.x; g < count; g += gridDim.x) {
+        const BatchEntry e = t.e[g];
+        const Instance& in = t.inst[e.inst];
+        const int32_t sg = in.w.st->stage;
+        if (stage >= 0 ? sg != stage : sg == 0) continue;
+        f(in, e.bid, e.nblk);
+    }
+}
 
 // Phase timer slots.
 enum : int32_t {
@@ -204,17 +275,8 @@ cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, i
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s);
-// Controller scratch in global memory (the parts that do not live in shared
-// memory for this n; null otherwise) and its work lists.
-struct CtlGlobal {
-    uint32_t* res;
-    uint8_t* claimed;
-    uint8_t* estate;
-    void* edges;
-    int32_t* acc;
-    int32_t* und;
-};
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s);
+int32_t controller_list_cap(int32_t n, int32_t mode);
 int32_t controller_smem_mode(int32_t n);
 size_t controller_smem_bytes(int32_t n);
 size_t full_evaluation_smem_bytes();
@@ -223,6 +285,24 @@ cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s);
 cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
+
+size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in);
+
+// Batched launches (one persistent grid each; every kernel acts only on the
+// table's instances that are in `stage`).  The tables are described at each
+// launcher's definition.
+cudaError_t launch_b_init(const BatchTable& rows, cudaStream_t s);
+cudaError_t launch_b_pass1(const BatchTable& tiles, cudaStream_t s);
+cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchTable& owners, cudaStream_t s);
+cudaError_t launch_b_start(const BatchTable& rows, cudaStream_t s);
+cudaError_t launch_b_evaluation(const BatchTable& eval, int32_t stage, int32_t conditional, int32_t strip,
+                                cudaStream_t s);
+cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s);
+cudaError_t launch_b_row_tasks(const BatchTable& rowt, cudaStream_t s);
+cudaError_t launch_b_prepare_edges(const BatchTable& rows, cudaStream_t s);
+cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s);
+cudaError_t launch_b_finish(const BatchTable& rows, cudaStream_t s);
+cudaError_t launch_b_advance(const BatchTable& one, int32_t from_stage, cudaStream_t s);
 
 // Raise a kernel's dynamic shared memory limit once per device (slot = one
 // small integer per kernel).

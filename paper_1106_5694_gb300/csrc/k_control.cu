@@ -139,9 +139,8 @@ constexpr int kUnroll = 4;
 // claim-stamp period (<= 255).  Both are shortened only by a test knob.
 // list_cap: entries of each two-tier list held in shared memory.
 template <typename EdgeT>
-__global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
-                                                                   uint32_t span, uint32_t stamp_wrap,
-                                                                   int32_t list_cap) {
+__device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem_mode, const CtlScratch& g,
+                                                uint32_t span, uint32_t stamp_wrap, int32_t list_cap) {
     using C = Codec<EdgeT>;
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
@@ -518,6 +517,14 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
         st->edge_count = s_live;
         st->f = s_f;
     }
+    __syncthreads();  // shared memory is reused by the caller's next call
+}
+
+template <typename EdgeT>
+__global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
+                                                                   uint32_t span, uint32_t stamp_wrap,
+                                                                   int32_t list_cap) {
+    controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap);
 }
 
 // Before each controller launch: clear the marks of the last event, re-
@@ -526,18 +533,18 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w,
 // its exchange under the current sigma, and whether that exchange raises f
 // now).  Also record each slot's re-evaluated candidate, which stays valid
 // for as long as no exchange is committed.  One thread per slot.
-__global__ void prepare_edges_kernel(Workspace w) {
+__device__ __forceinline__ void prepare_edges_body(const Workspace& w, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
     const int32_t n = w.n;
-    const int32_t stride = gridDim.x * blockDim.x;
+    const int32_t stride = nblk * blockDim.x;
     const int32_t yc = st->y_count;
-    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < yc; t += stride) {
+    for (int32_t t = bid * blockDim.x + threadIdx.x; t < yc; t += stride) {
         const int32_t j = w.y_list[t];
         w.in_y[j] = 0;
         w.moved[w.sigma[j]] = 0;
     }
-    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * n; t += stride) {
+    for (int32_t t = bid * blockDim.x + threadIdx.x; t < 2 * n; t += stride) {
         unsigned long long key;
         int32_t ru, rv, gain, target;
         bool in_c;
@@ -578,12 +585,14 @@ __global__ void prepare_edges_kernel(Workspace w) {
     }
 }
 
+__global__ void prepare_edges_kernel(Workspace w) { prepare_edges_body(w, blockIdx.x, gridDim.x); }
+
 // Rows whose best is no longer known: rows of changed jobs, and rows whose
 // best partner column changed holder.  Their keys are cleared and listed.
-__global__ void mark_rescan_kernel(Workspace w) {
+__device__ __forceinline__ void mark_rescan_body(const Workspace& w, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning || !st->need_update) return;
-    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < w.n; j += gridDim.x * blockDim.x) {
+    for (int32_t j = bid * blockDim.x + threadIdx.x; j < w.n; j += nblk * blockDim.x) {
         bool need = w.in_y[j];
         const unsigned long long ka = w.key_a[j];
         const unsigned long long kj = w.key_j[j];
@@ -597,19 +606,21 @@ __global__ void mark_rescan_kernel(Workspace w) {
     }
 }
 
+__global__ void mark_rescan_kernel(Workspace w) { mark_rescan_body(w, blockIdx.x, gridDim.x); }
+
 // Full re-evaluation of the listed rows: row j of G from row sigma(j) of a
 // and row j of at (gathered through sigma; staged in shared memory by one TMA
 // bulk copy).  Rows of changed jobs also push G[k][j] = G[j][k] into every
 // other row k (the only entries of row k that changed), through the same
 // atomic keys.
 template <bool kStage>
-__global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
+__device__ __forceinline__ void row_tasks_body(const Workspace& w, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning || !st->need_update) return;
     const int32_t count = st->rescan_count;
     const int32_t n = w.n;
     if (use_full_update(count, n, st->update_policy)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         st->row_updates += 1;
         st->rows_recomputed += count;
     }
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
     __syncthreads();
     uint32_t phase = 0;
     const int32_t n4 = (n + 3) / 4;
-    for (int32_t t = blockIdx.x; t < count; t += gridDim.x) {
+    for (int32_t t = bid; t < count; t += nblk) {
         const int32_t j = w.rescan_list[t];
         const int32_t* atrow = w.at + (size_t)j * w.ldt;
         if (kStage) {
@@ -697,12 +708,18 @@ __global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
     }
 }
 
+template <bool kStage>
+__global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
+    row_tasks_body<kStage>(w, blockIdx.x, gridDim.x);
+}
+
 // tau given (greedy result, identity or the caller's permutation): build
 // sigma, D and f; validate a caller's permutation.
-__global__ void start_from_tau_kernel(Workspace w, const int32_t* user_tau, int32_t mode, uint8_t* seen) {
+__device__ __forceinline__ void start_from_tau_body(const Workspace& w, const int32_t* user_tau, int32_t mode,
+                                                    uint8_t* seen, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x) {
+    for (int32_t i = bid * blockDim.x + threadIdx.x; i < w.n; i += nblk * blockDim.x) {
         int32_t j;
         if (mode == 2) j = i;                 // identity
         else if (mode == 3) j = user_tau[i];  // caller's permutation
@@ -720,9 +737,123 @@ __global__ void start_from_tau_kernel(Workspace w, const int32_t* user_tau, int3
     }
 }
 
+__global__ void start_from_tau_kernel(Workspace w, const int32_t* user_tau, int32_t mode, uint8_t* seen) {
+    start_from_tau_body(w, user_tau, mode, seen, blockIdx.x, gridDim.x);
+}
+
 __global__ void finish_kernel(Workspace w, int32_t* sigma_out) {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x)
         sigma_out[i] = w.tau[i];
+}
+
+// ------------------------------------------------------- batched launches
+// Initialise the fresh instances of the table: clear their small arrays, mark
+// every agent and job free, re-pitch the caller's matrix where needed, and
+// write the loop state (stage kStageNew).  Entries walk 16-byte chunks.
+__global__ void init_batched_kernel(BatchTable t, int32_t update_policy) {
+    const int32_t count = *t.count;
+    for (int32_t g = blockIdx.x; g < count; g += gridDim.x) {
+        const BatchEntry e = t.e[g];
+        const Instance& in = t.inst[e.inst];
+        if (!in.fresh) continue;
+        const Workspace& w = in.w;
+        const size_t nb = ((size_t)w.n + 127) / 128 * 128;
+        const char* fa = reinterpret_cast<const char*>(w.free_a);
+        const char* fj = reinterpret_cast<const char*>(w.free_j);
+        const size_t chunks = in.zero_bytes / 16;
+        const size_t stride = (size_t)e.nblk * blockDim.x;
+        for (size_t q = (size_t)e.bid * blockDim.x + threadIdx.x; q < chunks; q += stride) {
+            char* p = in.zero_begin + 16 * q;
+            const bool ones = (p >= fa && p < fa + nb) || (p >= fj && p < fj + nb);
+            const uint32_t v = ones ? 0x01010101u : 0u;
+            *reinterpret_cast<uint4*>(p) = make_uint4(v, v, v, v);
+        }
+        if (in.a_src) {  // re-pitched copy of the caller's matrix (n % 4 != 0 or misaligned)
+            int32_t* dst = const_cast<int32_t*>(w.a);
+            const size_t total = (size_t)w.n * w.lda;
+            for (size_t q = (size_t)e.bid * blockDim.x + threadIdx.x; q < total; q += stride) {
+                const size_t i = q / w.lda, j = q - i * w.lda;
+                dst[q] = j < (size_t)w.n ? in.a_src[i * w.n + j] : 0;
+            }
+        }
+        if (e.bid == 0 && threadIdx.x == 0) {
+            DeviceState h{};
+            h.status = kRunning;
+            h.phase = kPhaseRefreshAll;
+            h.max_sweeps = in.max_sweeps;
+            h.greedy_remaining = w.n;
+            h.update_policy = update_policy;
+            h.stage = kStageNew;
+            h.init_mode = in.init_mode;
+            if (in.deadline_us > 0) h.deadline_ns = globaltimer_ns() + (uint64_t)in.deadline_us * 1000ull;
+            *w.st = h;
+        }
+    }
+}
+
+__global__ void start_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageStart, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        start_from_tau_body(in.w, in.user_tau, in.w.st->init_mode, in.seen, bid, nblk);
+    });
+}
+
+__global__ void mark_rescan_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        mark_rescan_body(in.w, bid, nblk);
+    });
+}
+
+__global__ void __launch_bounds__(512) row_tasks_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        row_tasks_body<false>(in.w, bid, nblk);
+    });
+}
+
+__global__ void prepare_edges_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        prepare_edges_body(in.w, bid, nblk);
+    });
+}
+
+__global__ void __launch_bounds__(kCtlThreads, 1) controller_batched_kernel(BatchTable t, uint32_t span,
+                                                                           uint32_t stamp_wrap) {
+    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t, int32_t) {
+        const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc, in.ctl.und};
+        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap);
+    });
+}
+
+// The switching loop of an instance has ended: write its assignment.
+__global__ void finish_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        const DeviceState* st = in.w.st;
+        if (st->status != kDone && st->status != kTimeout) return;
+        for (int32_t i = bid * blockDim.x + threadIdx.x; i < in.w.n; i += nblk * blockDim.x)
+            in.sigma_out[i] = in.w.tau[i];
+    });
+}
+
+// Stage transitions of the instances in from_stage (one thread each).
+__global__ void advance_batched_kernel(BatchTable t, int32_t from_stage) {
+    const int32_t count = *t.count;
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x) {
+        const Instance& in = t.inst[t.e[g].inst];
+        DeviceState* st = in.w.st;
+        if (st->stage != from_stage) continue;
+        const bool running = st->status == kRunning;
+        int32_t next = from_stage;
+        if (from_stage == kStageNew) {
+            next = !running ? kStageDone : (st->init_mode == 0 ? kStageGreedy : kStageStart);
+        } else if (from_stage == kStageGreedy) {
+            next = !running ? kStageDone : (st->greedy_remaining == 0 ? kStageStart : kStageGreedy);
+        } else if (from_stage == kStageStart) {
+            st->f_initial = st->f;
+            next = running ? kStageSwitch : kStageDone;
+        } else if (from_stage == kStageSwitch) {
+            next = running ? kStageSwitch : kStageDone;
+        }
+        st->stage = next;
+    }
 }
 
 }  // namespace
@@ -744,7 +875,7 @@ int32_t controller_smem_mode(int32_t n) {
     return min(mode, env_controller_mode_cap());
 }
 
-static int32_t ctl_list_cap(int32_t n, int32_t mode) {
+int32_t controller_list_cap(int32_t n, int32_t mode) {
     if (mode == 0) return 0;
     const size_t room = kCtlSmemLimit - ctl_fixed_bytes(n, mode) - 16;
     const size_t cap = room / 6;  // three 16-bit lists
@@ -754,13 +885,13 @@ static int32_t ctl_list_cap(int32_t n, int32_t mode) {
 size_t controller_smem_bytes(int32_t n) {
     const int32_t mode = controller_smem_mode(n);
     if (mode == 0) return 0;
-    return ctl_fixed_bytes(n, mode) + 6 * (size_t)ctl_list_cap(n, mode) + 16;
+    return ctl_fixed_bytes(n, mode) + 6 * (size_t)controller_list_cap(n, mode) + 16;
 }
 
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s) {
     const int32_t mode = controller_smem_mode(w.n);
     const size_t smem = controller_smem_bytes(w.n);
-    const int32_t cap = ctl_list_cap(w.n, mode);
+    const int32_t cap = controller_list_cap(w.n, mode);
     CtlScratch c{gs.res, gs.claimed, gs.estate, gs.edges, gs.acc, gs.und};
     const bool narrow = w.n <= 65535;
     const void* fn = narrow ? reinterpret_cast<const void*>(controller_kernel<uint32_t>)
@@ -813,6 +944,58 @@ cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, i
     int grid = (w.n + 255) / 256;
     if (grid > 152 * 4) grid = 152 * 4;
     start_from_tau_kernel<<<grid, 256, 0, s>>>(w, user_tau, mode, seen);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- batched launchers
+// rows: entries over the agents/slots of each instance (256 threads per
+// block); one: one entry per instance.
+
+cudaError_t launch_b_init(const BatchTable& rows, cudaStream_t s) {
+    init_batched_kernel<<<152 * 8, 256, 0, s>>>(rows, env_update_policy());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_start(const BatchTable& rows, cudaStream_t s) {
+    start_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s) {
+    mark_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    return cudaGetLastError();
+}
+
+// rowt: entries (instance, block) sharing each instance's listed rows.
+cudaError_t launch_b_row_tasks(const BatchTable& rowt, cudaStream_t s) {
+    row_tasks_batched_kernel<<<152 * 2, 512, 0, s>>>(rowt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_prepare_edges(const BatchTable& rows, cudaStream_t s) {
+    prepare_edges_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    return cudaGetLastError();
+}
+
+// Instances of a batched launch have n <= 32767 (16-bit edge positions and
+// 32-bit edge words); each CTA lays out its shared memory for its own n.
+cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s) {
+    const size_t smem = kCtlSmemLimit;
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(controller_batched_kernel), 5, smem);
+    if (e != cudaSuccess) return e;
+    const bool short_wrap = env_short_wraps() != 0;
+    controller_batched_kernel<<<152, kCtlThreads, smem, s>>>(one, short_wrap ? 4u : kRoundSpanMax,
+                                                            short_wrap ? 5u : 250u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_finish(const BatchTable& rows, cudaStream_t s) {
+    finish_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_advance(const BatchTable& one, int32_t from_stage, cudaStream_t s) {
+    advance_batched_kernel<<<8, 256, 0, s>>>(one, from_stage);
     return cudaGetLastError();
 }
 

@@ -54,11 +54,12 @@ struct TileCursor {
 
 // Work items (row block J, first column tile J + strip * c) are numbered
 // J * chunks + c; items whose first tile lies past the last block are empty
-// and skipped.  CTA b walks items b, b + G, b + 2G, ...
-__device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t nb, int32_t strip) {
+// and skipped.  Block b of the nblk blocks working on one instance walks
+// items b, b + nblk, b + 2 nblk, ...
+__device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t nb, int32_t strip, int32_t nblk) {
     const int32_t chunks = (nb + strip - 1) / strip;
     const int32_t total = nb * chunks;
-    for (; item < total; item += gridDim.x) {
+    for (; item < total; item += nblk) {
         const int32_t j = item / chunks;
         const int32_t k0 = j + strip * (item - j * chunks);
         if (k0 < nb) {
@@ -73,9 +74,9 @@ __device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t
     return false;
 }
 
-__device__ __forceinline__ bool cursor_next(TileCursor& c, int32_t nb, int32_t strip) {
+__device__ __forceinline__ bool cursor_next(TileCursor& c, int32_t nb, int32_t strip, int32_t nblk) {
     if (++c.k < c.kend) return true;
-    return cursor_load(c, c.item + gridDim.x, nb, strip);
+    return cursor_load(c, c.item + nblk, nb, strip, nblk);
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -279,12 +280,15 @@ __device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int3
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
-                                                                      int32_t strip) {
+// The evaluation of one instance by block bid of the nblk blocks assigned to
+// it (a CTA of the single-instance launch, or one entry of a batched work
+// table).  All threads of the CTA call it together.
+__device__ __forceinline__ void full_evaluation_body(const Workspace& w, int32_t conditional, int32_t strip,
+                                                     int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
     if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
-    if (conditional && blockIdx.x == 0 && threadIdx.x == 0) st->full_evals += 1;
+    if (conditional && bid == 0 && threadIdx.x == 0) st->full_evals += 1;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* stages = reinterpret_cast<Stage*>(smem_raw);
@@ -299,21 +303,21 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
     // producer cursor: kStages - 1 tiles ahead of the consumer; the rows
     // (sigma) it will copy are loaded two tiles before they are needed
     TileCursor prod;
-    bool prod_ok = cursor_load(prod, blockIdx.x, nb, strip);
+    bool prod_ok = cursor_load(prod, bid, nb, strip, nblk);
     for (int s = 0; s < kStages - 1; ++s) {
         if (prod_ok) {
             issue_tile(w, &stages[s], prod.j, prod.k, copy_rows(w, prod.j, prod.k));
-            prod_ok = cursor_next(prod, nb, strip);
+            prod_ok = cursor_next(prod, nb, strip, nblk);
         }
         cp_async_commit();
     }
     TileCursor ahead = prod;  // one tile after prod
-    bool ahead_ok = prod_ok && cursor_next(ahead, nb, strip);
+    bool ahead_ok = prod_ok && cursor_next(ahead, nb, strip, nblk);
     CopyRows rows_now = prod_ok ? copy_rows(w, prod.j, prod.k) : CopyRows{-1, -1, -1, -1};
     CopyRows rows_next = ahead_ok ? copy_rows(w, ahead.j, ahead.k) : CopyRows{-1, -1, -1, -1};
 
     TileCursor cons;
-    bool cons_ok = cursor_load(cons, blockIdx.x, nb, strip);
+    bool cons_ok = cursor_load(cons, bid, nb, strip, nblk);
     RowState rs;
     int32_t dj[kRows], sj[kRows];
     bool item_start = true;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
             prod_ok = ahead_ok;
             rows_now = rows_next;
             if (ahead_ok) {
-                ahead_ok = cursor_next(ahead, nb, strip);
+                ahead_ok = cursor_next(ahead, nb, strip, nblk);
                 if (ahead_ok) rows_next = copy_rows(w, ahead.j, ahead.k);
             }
         }
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
         prev_k0 = K0;
         ++t;
         if (++cons.k >= cons.kend) {
-            cons_ok = cursor_load(cons, cons.item + gridDim.x, nb, strip);
+            cons_ok = cursor_load(cons, cons.item + nblk, nb, strip, nblk);
             item_start = true;
         }
     }
@@ -377,6 +381,20 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
         const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
         commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
     }
+    __syncthreads();  // the stages and colbuf may be reused by the caller's next call
+}
+
+__global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
+                                                                      int32_t strip) {
+    full_evaluation_body(w, conditional, strip, blockIdx.x, gridDim.x);
+}
+
+// Batched: each table entry is one block of one instance's evaluation.
+__global__ void __launch_bounds__(kThreads, 1) full_evaluation_batched_kernel(BatchTable t, int32_t stage,
+                                                                              int32_t conditional, int32_t strip) {
+    for_each_entry(t, stage, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        full_evaluation_body(in.w, conditional, strip, bid, nblk);
+    });
 }
 
 // agent slot i <- key_a[tau(i)], job slot j <- key_j[j]  (public evaluation API)
@@ -408,6 +426,17 @@ cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cuda
 }
 
 int32_t evaluation_strip() { return kStrip; }
+
+// eval: entries (instance, block) of the tile-pair items; the instances in
+// `stage` are evaluated (conditional: only those whose update needs it).
+cudaError_t launch_b_evaluation(const BatchTable& eval, int32_t stage, int32_t conditional, int32_t strip,
+                                cudaStream_t s) {
+    const size_t smem = full_evaluation_smem_bytes();
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_batched_kernel), 4, smem);
+    if (e != cudaSuccess) return e;
+    full_evaluation_batched_kernel<<<152, kThreads, smem, s>>>(eval, stage, conditional, strip);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s) {

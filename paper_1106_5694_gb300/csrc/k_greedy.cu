@@ -20,7 +20,8 @@ namespace {
 
 constexpr int kT = 64;  // tile edge
 
-__global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t tiles_x, int32_t tiles_total) {
+__device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t tiles_x, int32_t tiles_total,
+                                                  int32_t bid, int32_t nblk) {
     __shared__ int32_t s[kT][kT + 1];
     __shared__ unsigned long long colpart[4][kT];
     const int32_t n = w.n;
@@ -28,7 +29,7 @@ __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t 
     const int lane16 = t & 15;
     bool bad = false;
     int32_t amax = 0;
-    for (int32_t tile = blockIdx.x; tile < tiles_total; tile += gridDim.x) {
+    for (int32_t tile = bid; tile < tiles_total; tile += nblk) {
         const int32_t I0 = (tile / tiles_x) * kT;
         const int32_t J0 = (tile % tiles_x) * kT;
         // load 64 rows x 64 cols with int4, 16 threads per row, 4 passes
@@ -100,11 +101,15 @@ __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t 
     }
 }
 
+__global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t tiles_x, int32_t tiles_total) {
+    greedy_pass1_body(w, tiles_x, tiles_total, blockIdx.x, gridDim.x);
+}
+
 // Match every mutually-best (agent, job) pair.
-__global__ void greedy_match_kernel(Workspace w) {
+__device__ __forceinline__ void greedy_match_body(const Workspace& w, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
     if (st->status != kRunning || st->greedy_remaining == 0) return;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x) {
+    for (int32_t i = bid * blockDim.x + threadIdx.x; i < w.n; i += nblk * blockDim.x) {
         if (!w.free_a[i]) continue;
         const int32_t j = key_index(w.g_row[i]);
         if (j < 0 || j >= w.n) {  // every free agent has a free best job
@@ -120,6 +125,44 @@ __global__ void greedy_match_kernel(Workspace w) {
             atomicSub(&st->greedy_remaining, 1);
             st->greedy_matched = 1;
         }
+    }
+}
+
+__global__ void greedy_match_kernel(Workspace w) { greedy_match_body(w, blockIdx.x, gridDim.x); }
+
+// Rescan for batched launches: one warp per owner, so that an instance's
+// owners spread over few blocks.  Same result as greedy_rescan_kernel.
+__device__ __forceinline__ void greedy_rescan_warp_body(const Workspace& w, const int32_t* mat, int32_t ld,
+                                                        unsigned long long* keys, const uint8_t* owner_free,
+                                                        const uint8_t* partner_free, int32_t count_round,
+                                                        int32_t bid, int32_t nblk) {
+    DeviceState* st = w.st;
+    if (count_round && bid == 0 && threadIdx.x == 0 && st->greedy_matched) {
+        st->greedy_rounds += 1;
+        st->greedy_matched = 0;
+    }
+    if (st->status != kRunning || st->greedy_remaining == 0) return;
+    const int32_t n = w.n;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int32_t o = bid * nw + (threadIdx.x >> 5); o < n; o += nblk * nw) {
+        if (!owner_free[o]) continue;
+        const int32_t b = key_index(keys[o]);
+        if (b >= 0 && b < n && partner_free[b]) continue;  // best partner still free
+        const int32_t* row = mat + (size_t)o * ld;
+        if (lane == 0) atomicAdd((unsigned long long*)&st->greedy_rescans, 1ull);
+        unsigned long long best = 0;
+#pragma unroll 4
+        for (int32_t c = lane * 4; c < n; c += 128) {
+            const int4 v = *reinterpret_cast<const int4*>(row + c);
+            const uint32_t fr = *reinterpret_cast<const uint32_t*>(partner_free + c);
+            const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c + e < n && ((fr >> (8 * e)) & 0xffu)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
+        if (lane == 0) keys[o] = best;
     }
 }
 
@@ -418,6 +461,28 @@ __global__ void range_check_kernel(Workspace w) {
     }
 }
 
+__global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageNew, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        const int32_t tx = (in.w.n + kT - 1) / kT;
+        greedy_pass1_body(in.w, tx, tx * tx, bid, nblk);
+    });
+}
+
+__global__ void __launch_bounds__(256) greedy_match_batched_kernel(BatchTable t) {
+    for_each_entry(t, kStageGreedy, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        greedy_match_body(in.w, bid, nblk);
+    });
+}
+
+// rows = 1: rescan agents over rows of a (and count the round); 0: jobs over rows of at.
+__global__ void __launch_bounds__(256) greedy_rescan_batched_kernel(BatchTable t, int32_t rows) {
+    for_each_entry(t, kStageGreedy, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        const Workspace& w = in.w;
+        if (rows) greedy_rescan_warp_body(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1, bid, nblk);
+        else greedy_rescan_warp_body(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0, bid, nblk);
+    });
+}
+
 }  // namespace
 
 cudaError_t launch_range_check(const Workspace& w, cudaStream_t s) {
@@ -439,6 +504,23 @@ cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
     const int32_t g = w.n < 152 * 8 ? w.n : 152 * 8;  // one owner per CTA at a time
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1);
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0);
+    return cudaGetLastError();
+}
+
+// tiles: entries (instance, block) over the 64x64 tiles of a (pass 1 of the
+// instances in kStageNew).
+cudaError_t launch_b_pass1(const BatchTable& tiles, cudaStream_t s) {
+    greedy_pass1_batched_kernel<<<152 * 8, 256, 0, s>>>(tiles);
+    return cudaGetLastError();
+}
+
+// One locally-dominant round of the instances in kStageGreedy.  rows:
+// entries over agents (256 per block and step); owners: entries over rows of
+// a and of at (8 warps per block, one owner per warp at a time).
+cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchTable& owners, cudaStream_t s) {
+    greedy_match_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(owners, 1);
+    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(owners, 0);
     return cudaGetLastError();
 }
 
