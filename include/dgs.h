@@ -54,8 +54,8 @@ typedef enum {
     DGS_ERR_CUDA = 4,     /* a CUDA call failed (see dgs_last_cuda_error) */
     DGS_TIMEOUT = 5,      /* sweep cap or deadline hit: outputs hold the valid
                              assignment reached so far and its objective */
-    DGS_PENDING = 6,      /* reserved for asynchronous entry points */
-    DGS_ERR_BUSY = 7,     /* reserved for admission control */
+    DGS_PENDING = 6,      /* dgs_poll / dgs_server_wait: not finished yet */
+    DGS_ERR_BUSY = 7,     /* dgs_submit: the request can never fit the budget */
     DGS_ERR_INTERNAL = 8  /* a device-side consistency check failed */
 } dgs_status;
 

@@ -41,36 +41,20 @@ namespace {
 constexpr int32_t kGreedyPerStep = 16;  // greedy rounds per step
 constexpr int32_t kSwitchPerStep = 8;   // switching iterations per step
 
-// Table partitions and the most entries one instance can take in each.
-enum : int32_t { kTabRows = 0, kTabTiles, kTabOwners, kTabEval, kTabRowTasks, kTabOne, kTabCount };
-constexpr int32_t kMaxPerInstance[kTabCount] = {
-    64,       // rows: ceil(n / 512), n <= 32767
-    152 * 8,  // tiles of pass 1
-    512,      // owners: ceil(n / 64)
-    152,      // evaluation blocks
-    152,      // row-task blocks
-    1         // one
-};
+// Static work tables (the per-instance work of these launches is known from
+// n alone) and the most entries one instance can take in each: rows =
+// ceil(n / 512) blocks of 256 threads over agents, jobs or slots; one = the
+// instance itself.  Work that depends on the device state (pass 1 of new
+// instances, greedy rescans, evaluations, row tasks) goes through the queues
+// of launch_b_scan instead.
+enum : int32_t { kTabRows = 0, kTabOne, kTabCount };
+constexpr int32_t kMaxPerInstance[kTabCount] = {64, 1};
 
 int32_t ceil_div(int64_t a, int64_t b) { return (int32_t)((a + b - 1) / b); }
 int32_t clampi(int32_t x, int32_t lo, int32_t hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-// Blocks that instance of size n gets in each partition.
 int32_t blocks_for(int32_t tab, int32_t n) {
-    switch (tab) {
-        case kTabRows: return clampi(ceil_div(n, 512), 1, kMaxPerInstance[kTabRows]);
-        case kTabTiles: {
-            const int64_t t = (int64_t)ceil_div(n, 64) * ceil_div(n, 64);
-            return clampi(ceil_div(t, 4), 1, kMaxPerInstance[kTabTiles]);
-        }
-        case kTabOwners: return clampi(ceil_div(n, 64), 1, kMaxPerInstance[kTabOwners]);
-        case kTabEval: {
-            const int32_t nb = ceil_div(n, 64), chunks = ceil_div(nb, evaluation_strip());
-            return clampi(ceil_div((int64_t)nb * chunks, 2), 1, kMaxPerInstance[kTabEval]);
-        }
-        case kTabRowTasks: return clampi(n / 16, 1, kMaxPerInstance[kTabRowTasks]);
-        default: return 1;
-    }
+    return tab == kTabRows ? clampi(ceil_div(n, 512), 1, kMaxPerInstance[kTabRows]) : 1;
 }
 
 thread_local char g_err[512];
@@ -115,7 +99,8 @@ void stats_of(const DeviceState& h, int64_t launches, dgs_stats* out) {
 // Slots, tables and the step graph of one batch of resident instances.
 class Engine {
   public:
-    explicit Engine(int32_t capacity) : cap_(capacity) {}
+    // capacity: slots; max_n: largest n any slot will hold.
+    Engine(int32_t capacity, int32_t max_n) : cap_(capacity), max_n_(max_n) {}
     Engine(const Engine&) = delete;
     Engine& operator=(const Engine&) = delete;
 
@@ -126,6 +111,7 @@ class Engine {
         if (d_st_) cudaFree(d_st_);
         if (d_ent_) cudaFree(d_ent_);
         if (d_cnt_) cudaFree(d_cnt_);
+        if (d_q_) cudaFree(d_q_);
         if (h_inst_) cudaFreeHost(h_inst_);
         if (h_st_) cudaFreeHost(h_st_);
         if (h_ent_) cudaFreeHost(h_ent_);
@@ -145,6 +131,7 @@ class Engine {
         }
         B_CUDA(cudaMalloc(&d_ent_, sizeof(BatchEntry) * total), "work tables");
         B_CUDA(cudaMalloc(&d_cnt_, sizeof(int32_t) * kTabCount), "work table counts");
+        B_CUDA(cudaMalloc(&d_q_, sizeof(int32_t) * 2 * (cap_ + 1)), "work queues");
         B_CUDA(cudaMallocHost(&h_inst_, sizeof(Instance) * cap_), "instance table (host)");
         B_CUDA(cudaMallocHost(&h_st_, sizeof(DeviceState) * cap_), "loop states (host)");
         B_CUDA(cudaMallocHost(&h_ent_, sizeof(BatchEntry) * total), "work tables (host)");
@@ -259,20 +246,24 @@ class Engine {
         if (_e != cudaSuccess) return fail(_e, what); \
         L += (n_kernels);                         \
     } while (0)
-        const BatchTable rows = table(kTabRows), tiles = table(kTabTiles), owners = table(kTabOwners),
-                         eval = table(kTabEval), rowt = table(kTabRowTasks), one = table(kTabOne);
+        const BatchTable rows = table(kTabRows), one = table(kTabOne);
+        const BatchQueues q{d_inst_, cap_, d_q_, d_q_ + cap_ + 1};
+        const int32_t strip = evaluation_strip();
         B_LAUNCH(launch_b_init(rows, s), 1, "init");
-        B_LAUNCH(launch_b_pass1(tiles, s), 1, "pass 1");
+        B_LAUNCH(launch_b_scan(q, kScanPass1, strip, s), 1, "scan");
+        B_LAUNCH(launch_b_pass1(q, s), 1, "pass 1");
         B_LAUNCH(launch_b_advance(one, kStageNew, s), 1, "advance");
-        for (int32_t r = 0; r < kGreedyPerStep; ++r) B_LAUNCH(launch_b_greedy_round(rows, owners, s), 3, "greedy round");
+        for (int32_t r = 0; r < kGreedyPerStep; ++r) B_LAUNCH(launch_b_greedy_round(rows, q, s), 4, "greedy round");
         B_LAUNCH(launch_b_advance(one, kStageGreedy, s), 1, "advance");
         B_LAUNCH(launch_b_start(rows, s), 1, "start");
-        B_LAUNCH(launch_b_evaluation(eval, kStageStart, 0, evaluation_strip(), s), 1, "evaluation");
+        B_LAUNCH(launch_b_scan(q, kScanStart, strip, s), 1, "scan");
+        B_LAUNCH(launch_b_evaluation(q, strip, s), 1, "evaluation");
         B_LAUNCH(launch_b_advance(one, kStageStart, s), 1, "advance");
         for (int32_t i = 0; i < kSwitchPerStep; ++i) {
             B_LAUNCH(launch_b_mark_rescan(rows, s), 1, "mark");
-            B_LAUNCH(launch_b_evaluation(eval, kStageSwitch, 1, evaluation_strip(), s), 1, "re-evaluation");
-            B_LAUNCH(launch_b_row_tasks(rowt, s), 1, "row tasks");
+            B_LAUNCH(launch_b_scan(q, kScanSwitch, strip, s), 1, "scan");
+            B_LAUNCH(launch_b_evaluation(q, strip, s), 1, "re-evaluation");
+            B_LAUNCH(launch_b_row_tasks(q, max_n_, s), 1, "row tasks");
             B_LAUNCH(launch_b_prepare_edges(rows, s), 1, "prepare");
             B_LAUNCH(launch_b_controller(one, s), 1, "controller");
         }
@@ -288,7 +279,7 @@ class Engine {
         // kernel attributes are set outside the capture (first launch of each
         // kernel on this device), by one uncaptured pass over empty tables
         {
-            const int32_t zero[kTabCount] = {0, 0, 0, 0, 0, 0};
+            const int32_t zero[kTabCount] = {0, 0};
             int32_t* saved = d_cnt_;
             int32_t* d_zero = nullptr;
             B_CUDA(cudaMallocAsync(&d_zero, sizeof(zero), stream_), "counts");
@@ -320,7 +311,9 @@ class Engine {
     }
 
     int32_t cap_;
+    int32_t max_n_;
     cudaStream_t stream_ = nullptr;
+    int32_t* d_q_ = nullptr;  // the two queue offset arrays (cap + 1 each)
     Instance* d_inst_ = nullptr;
     Instance* h_inst_ = nullptr;
     DeviceState* d_st_ = nullptr;
@@ -373,7 +366,7 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
         max_n = std::max(max_n, ns[k]);
     }
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-    Engine eng(count);
+    Engine eng(count, max_n);
     dgs_status st = eng.init();
     if (st != DGS_OK) return st;
     cudaStream_t s = eng.stream();
@@ -494,7 +487,7 @@ struct dgs_server {
     int32_t* h_sigma = nullptr;  // pinned staging for results
     size_t h_sigma_cap = 0;
 
-    explicit dgs_server(int32_t cap) : eng(cap), slots(cap) {}
+    explicit dgs_server(int32_t cap) : eng(cap, DGS_BATCH_MAX_N), slots(cap) {}
 
     void finish_all_pending(dgs_status why) {
         for (auto& kv : pending) {

@@ -159,6 +159,52 @@ __device__ __forceinline__ void for_each_entry(const BatchTable& t, int32_t stag
     }
 }
 
+// Work queue of one batched launch: off[k] = first item of slot k, off[cap] =
+// total (exclusive prefix of the per-slot item counts, written by the scan
+// kernel just before the consumer).  CTA b takes the contiguous items
+// [b * per, (b + 1) * per) and calls f(instance, local item, items of that
+// slot) for each, the whole CTA together.
+template <typename F>
+__device__ __forceinline__ void for_each_item(const Instance* inst, const int32_t* off, int32_t cap, F&& f) {
+    const int32_t total = off[cap];
+    if (total <= 0) return;
+    const int32_t per = (total + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+    int32_t item = (int32_t)blockIdx.x * per;
+    const int32_t end = min(total, item + per);
+    if (item >= end) return;
+    int32_t lo = 0, hi = cap;  // off[lo] <= item < off[hi]
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    int32_t k = lo, first = off[k], next = off[k + 1];
+    for (; item < end; ++item) {
+        while (item >= next) {
+            ++k;
+            first = next;
+            next = off[k + 1];
+        }
+        f(inst[k], item - first, next - first);
+    }
+}
+
+// Blocks of the batched pass 1 and evaluation of an instance of size n (the
+// scan kernel and the host agree on them).
+__host__ __device__ __forceinline__ int32_t batch_blocks_pass1(int32_t n) {
+    const int32_t t = (n + 63) / 64;
+    const int32_t b = (t * t + 3) / 4;
+    return b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b);
+}
+__host__ __device__ __forceinline__ int32_t batch_blocks_eval(int32_t n, int32_t strip) {
+    const int32_t nb = (n + 63) / 64, chunks = (nb + strip - 1) / strip;
+    const int32_t b = (nb * chunks + 1) / 2;
+    return b < 1 ? 1 : (b > 152 ? 152 : b);
+}
+
+// Phases whose work counts the scan kernel computes.
+enum : int32_t { kScanPass1 = 0, kScanGreedy = 1, kScanStart = 2, kScanSwitch = 3 };
+
 // Phase timer slots.
 enum : int32_t {
     kPtGreedyMatch = 0, kPtGreedyBar1, kPtGreedyCheck, kPtGreedyScan, kPtGreedyBar2, kPtGreedyScanMax,
@@ -291,14 +337,22 @@ size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in);
 // Batched launches (one persistent grid each; every kernel acts only on the
 // table's instances that are in `stage`).  The tables are described at each
 // launcher's definition.
+// Queues: q0 / q1 are the two offset arrays (cap + 1 entries) written by
+// launch_b_scan for the phase; the consumer launches read them.
+struct BatchQueues {
+    const Instance* inst;
+    int32_t cap;
+    int32_t* q0;
+    int32_t* q1;
+};
+cudaError_t launch_b_scan(const BatchQueues& q, int32_t phase, int32_t strip, cudaStream_t s);
 cudaError_t launch_b_init(const BatchTable& rows, cudaStream_t s);
-cudaError_t launch_b_pass1(const BatchTable& tiles, cudaStream_t s);
-cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchTable& owners, cudaStream_t s);
+cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s);
+cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchQueues& q, cudaStream_t s);
 cudaError_t launch_b_start(const BatchTable& rows, cudaStream_t s);
-cudaError_t launch_b_evaluation(const BatchTable& eval, int32_t stage, int32_t conditional, int32_t strip,
-                                cudaStream_t s);
+cudaError_t launch_b_evaluation(const BatchQueues& q, int32_t strip, cudaStream_t s);
 cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s);
-cudaError_t launch_b_row_tasks(const BatchTable& rowt, cudaStream_t s);
+cudaError_t launch_b_row_tasks(const BatchQueues& q, int32_t max_n, cudaStream_t s);
 cudaError_t launch_b_prepare_edges(const BatchTable& rows, cudaStream_t s);
 cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s);
 cudaError_t launch_b_finish(const BatchTable& rows, cudaStream_t s);

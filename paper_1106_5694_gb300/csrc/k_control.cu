@@ -26,6 +26,8 @@
 // is a read of the keys).  A sweep that commits exchanges stops it: the
 // update kernels re-evaluate the affected rows on the whole GPU, then the
 // controller is launched again and refreshes every slot not in C.
+#include <algorithm>
+
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -613,6 +615,83 @@ __global__ void mark_rescan_kernel(Workspace w) { mark_rescan_body(w, blockIdx.x
 // bulk copy).  Rows of changed jobs also push G[k][j] = G[j][k] into every
 // other row k (the only entries of row k that changed), through the same
 // atomic keys.
+// Row j of G recomputed in full by the CTA (row sigma(j) of a and row j of
+// at, the latter staged in shared memory by one TMA bulk copy when kStage);
+// a changed job's row also pushes G[k][j] = G[j][k] into every other row k.
+// red_a / red_j: 16 entries each.  Returns false (CTA-uniform) if the staged
+// copy did not arrive within the wait limit.
+template <bool kStage>
+__device__ __forceinline__ bool row_task_row(const Workspace& w, int32_t j, int32_t* atrow_s, uint64_t* bar,
+                                             uint32_t& phase, unsigned long long* red_a,
+                                             unsigned long long* red_j) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t n = w.n;
+    const int32_t n4 = (n + 3) / 4;
+    const int32_t* atrow = w.at + (size_t)j * w.ldt;
+    if (kStage) {
+        if (tid == 0) {
+            const uint32_t bytes = 16u * (uint32_t)n4;
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(atrow_s, atrow, bytes, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) return false;
+        atrow = atrow_s;
+    }
+    const int32_t sjj = w.sigma[j];
+    const int32_t dj = w.diag[j];
+    const bool scatter = w.in_y[j];
+    const int32_t* arow = w.a + (size_t)sjj * w.lda;
+    int32_t bg = 0, bc = -1, bs = 0x7fffffff;
+#pragma unroll 2
+    for (int32_t q = tid; q < n4; q += blockDim.x) {
+        const int32_t k0 = 4 * q;
+        const int4 x4 = *reinterpret_cast<const int4*>(arow + k0);
+        const int4 s4 = *reinterpret_cast<const int4*>(w.sigma + k0);
+        const int4 d4 = *reinterpret_cast<const int4*>(w.diag + k0);
+        const int32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        const int32_t ss[4] = {s4.x, s4.y, s4.z, s4.w};
+        const int32_t ds[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int32_t k = k0 + e;
+            if (k >= n) break;
+            const int32_t sk = ss[e];
+            const int32_t g = xs[e] + atrow[sk] - dj - ds[e];
+            const bool gt = g > bg, eq = g == bg;
+            bs = gt ? sk : (eq ? min(bs, sk) : bs);
+            bc = gt ? k : bc;
+            bg = max(bg, g);
+            if (scatter && g > 0 && k != j) {
+                if (g >= key_gain(w.key_a[k])) {
+                    atomicMax(&w.key_a[k], pack_gain(g, (uint32_t)j));
+                    atomicMax(&w.key_j[k], pack_gain(g, (uint32_t)sjj));
+                }
+            }
+        }
+    }
+    unsigned long long ka = bg > 0 ? pack_gain(bg, (uint32_t)bc) : 0ull;
+    unsigned long long kj = bg > 0 ? pack_gain(bg, (uint32_t)bs) : 0ull;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ka = umax64(ka, __shfl_xor_sync(0xffffffffu, ka, off));
+        kj = umax64(kj, __shfl_xor_sync(0xffffffffu, kj, off));
+    }
+    if (lane == 0) { red_a[warp] = ka; red_j[warp] = kj; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long ma = 0, mj = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { ma = umax64(ma, red_a[q]); mj = umax64(mj, red_j[q]); }
+        if (ma) {
+            atomicMax(&w.key_a[j], ma);
+            atomicMax(&w.key_j[j], mj);
+        }
+    }
+    __syncthreads();  // red_* and the staged row are reused by the next row
+    return true;
+}
+
 template <bool kStage>
 __device__ __forceinline__ void row_tasks_body(const Workspace& w, int32_t bid, int32_t nblk) {
     DeviceState* st = w.st;
@@ -628,83 +707,17 @@ __device__ __forceinline__ void row_tasks_body(const Workspace& w, int32_t bid, 
     int32_t* atrow_s = reinterpret_cast<int32_t*>(smem_raw);
     __shared__ unsigned long long red_a[16], red_j[16];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int32_t s_fail;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (kStage && tid == 0) {
+    if (kStage && threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
-        s_fail = 0;
     }
     __syncthreads();
     uint32_t phase = 0;
-    const int32_t n4 = (n + 3) / 4;
     for (int32_t t = bid; t < count; t += nblk) {
-        const int32_t j = w.rescan_list[t];
-        const int32_t* atrow = w.at + (size_t)j * w.ldt;
-        if (kStage) {
-            if (tid == 0) {
-                const uint32_t bytes = 16u * (uint32_t)n4;
-                mbar_arrive_expect_tx(&bar, bytes);
-                bulk_g2s(atrow_s, atrow, bytes, &bar);
-            }
-            const bool ok = mbar_wait_bounded(&bar, phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
-                return;
-            }
-            atrow = atrow_s;
+        if (!row_task_row<kStage>(w, w.rescan_list[t], atrow_s, &bar, phase, red_a, red_j)) {
+            if (threadIdx.x == 0) { st->error = kErrWaitTimeout; st->status = kError; }
+            return;
         }
-        const int32_t sjj = w.sigma[j];
-        const int32_t dj = w.diag[j];
-        const bool scatter = w.in_y[j];
-        const int32_t* arow = w.a + (size_t)sjj * w.lda;
-        int32_t bg = 0, bc = -1, bs = 0x7fffffff;
-#pragma unroll 2
-        for (int32_t q = tid; q < n4; q += blockDim.x) {
-            const int32_t k0 = 4 * q;
-            const int4 x4 = *reinterpret_cast<const int4*>(arow + k0);
-            const int4 s4 = *reinterpret_cast<const int4*>(w.sigma + k0);
-            const int4 d4 = *reinterpret_cast<const int4*>(w.diag + k0);
-            const int32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
-            const int32_t ss[4] = {s4.x, s4.y, s4.z, s4.w};
-            const int32_t ds[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int32_t k = k0 + e;
-                if (k >= n) break;
-                const int32_t sk = ss[e];
-                const int32_t g = xs[e] + atrow[sk] - dj - ds[e];
-                const bool gt = g > bg, eq = g == bg;
-                bs = gt ? sk : (eq ? min(bs, sk) : bs);
-                bc = gt ? k : bc;
-                bg = max(bg, g);
-                if (scatter && g > 0 && k != j) {
-                    if (g >= key_gain(w.key_a[k])) {
-                        atomicMax(&w.key_a[k], pack_gain(g, (uint32_t)j));
-                        atomicMax(&w.key_j[k], pack_gain(g, (uint32_t)sjj));
-                    }
-                }
-            }
-        }
-        unsigned long long ka = bg > 0 ? pack_gain(bg, (uint32_t)bc) : 0ull;
-        unsigned long long kj = bg > 0 ? pack_gain(bg, (uint32_t)bs) : 0ull;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            ka = umax64(ka, __shfl_xor_sync(0xffffffffu, ka, off));
-            kj = umax64(kj, __shfl_xor_sync(0xffffffffu, kj, off));
-        }
-        if (lane == 0) { red_a[warp] = ka; red_j[warp] = kj; }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long ma = 0, mj = 0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { ma = umax64(ma, red_a[q]); mj = umax64(mj, red_j[q]); }
-            if (ma) {
-                atomicMax(&w.key_a[j], ma);
-                atomicMax(&w.key_j[j], mj);
-            }
-        }
-        __syncthreads();  // red_* and the staged row are reused by the next row
     }
 }
 
@@ -770,10 +783,11 @@ __global__ void init_batched_kernel(BatchTable t, int32_t update_policy) {
         }
         if (in.a_src) {  // re-pitched copy of the caller's matrix (n % 4 != 0 or misaligned)
             int32_t* dst = const_cast<int32_t*>(w.a);
-            const size_t total = (size_t)w.n * w.lda;
-            for (size_t q = (size_t)e.bid * blockDim.x + threadIdx.x; q < total; q += stride) {
-                const size_t i = q / w.lda, j = q - i * w.lda;
-                dst[q] = j < (size_t)w.n ? in.a_src[i * w.n + j] : 0;
+            const int32_t n = w.n, lda = w.lda;  // n * lda < 2^31 for batched sizes
+            for (int32_t i = e.bid; i < n; i += e.nblk) {
+                const int32_t* src = in.a_src + (size_t)i * n;
+                int32_t* d = dst + (size_t)i * lda;
+                for (int32_t j = threadIdx.x; j < lda; j += blockDim.x) d[j] = j < n ? src[j] : 0;
             }
         }
         if (e.bid == 0 && threadIdx.x == 0) {
@@ -803,10 +817,97 @@ __global__ void mark_rescan_batched_kernel(BatchTable t) {
     });
 }
 
-__global__ void __launch_bounds__(512) row_tasks_batched_kernel(BatchTable t) {
-    for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t bid, int32_t nblk) {
-        row_tasks_body<false>(in.w, bid, nblk);
+// The rows queued by the kScanSwitch scan (q1): one row task per item, the
+// at row staged by TMA; one mbarrier for the CTA's whole sequence of rows.
+__global__ void __launch_bounds__(512) row_tasks_batched_kernel(BatchQueues q) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int32_t* atrow_s = reinterpret_cast<int32_t*>(smem_raw);
+    __shared__ unsigned long long red_a[16], red_j[16];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool dead = false;
+    for_each_item(q.inst, q.q1, q.cap, [&](const Instance& in, int32_t t, int32_t) {
+        if (dead) return;
+        const Workspace& w = in.w;
+        if (!row_task_row<true>(w, w.rescan_list[t], atrow_s, &bar, phase, red_a, red_j)) {
+            if (threadIdx.x == 0) { w.st->error = kErrWaitTimeout; w.st->status = kError; }
+            dead = true;  // the buffer may still be written: no further copies into it
+        }
     });
+}
+
+// Per-slot work counts of one phase as exclusive prefix offsets (q0, q1; cap
+// + 1 entries each), with the counters a single solve updates at the same
+// point.  One CTA of 1024 threads.
+//   kScanPass1:  q0 = pass-1 blocks of instances in kStageNew
+//   kScanGreedy: q0 = owners listed for rescan (greedy stage; the round is
+//                counted when the match matched pairs)
+//   kScanStart:  q0 = evaluation blocks of instances in kStageStart
+//   kScanSwitch: q0 = evaluation blocks of the updates that re-evaluate every
+//                row, q1 = rows of the updates that use row tasks
+__global__ void __launch_bounds__(1024) scan_batched_kernel(BatchQueues q, int32_t phase, int32_t strip) {
+    __shared__ int32_t warp_sums[33];
+    int32_t carry0 = 0, carry1 = 0;
+    for (int32_t c0 = 0; c0 < q.cap; c0 += 1024) {
+        const int32_t k = c0 + (int32_t)threadIdx.x;
+        int32_t x0 = 0, x1 = 0;
+        if (k < q.cap) {
+            const Instance& in = q.inst[k];
+            DeviceState* st = in.w.st;
+            const int32_t n = in.w.n;
+            if (st != nullptr && n > 0) {
+                const int32_t stage = st->stage;
+                const bool running = st->status == kRunning;
+                if (phase == kScanPass1) {
+                    if (stage == kStageNew) x0 = batch_blocks_pass1(n);
+                } else if (phase == kScanGreedy) {
+                    if (stage == kStageGreedy) {
+                        if (st->greedy_matched) {
+                            st->greedy_rounds += 1;
+                            st->greedy_matched = 0;
+                        }
+                        if (running && st->greedy_remaining > 0) {
+                            x0 = st->rescan_count;
+                            st->greedy_rescans += x0;
+                        }
+                        st->rescan_count = 0;
+                    }
+                } else if (phase == kScanStart) {
+                    if (stage == kStageStart && running) x0 = batch_blocks_eval(n, strip);
+                } else if (phase == kScanSwitch) {
+                    if (stage == kStageSwitch && running && st->need_update) {
+                        const int32_t count = st->rescan_count;
+                        if (use_full_update(count, n, st->update_policy)) {
+                            x0 = batch_blocks_eval(n, strip);
+                            st->full_evals += 1;
+                        } else {
+                            x1 = count;
+                            st->row_updates += 1;
+                            st->rows_recomputed += count;
+                        }
+                    }
+                }
+            }
+        }
+        int32_t t0, t1;
+        const int32_t p0 = block_scan(x0, warp_sums, &t0);
+        const int32_t p1 = block_scan(x1, warp_sums, &t1);
+        if (k < q.cap) {
+            q.q0[k] = carry0 + p0;
+            q.q1[k] = carry1 + p1;
+        }
+        carry0 += t0;
+        carry1 += t1;
+    }
+    if (threadIdx.x == 0) {
+        q.q0[q.cap] = carry0;
+        q.q1[q.cap] = carry1;
+    }
 }
 
 __global__ void prepare_edges_batched_kernel(BatchTable t) {
@@ -966,9 +1067,20 @@ cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// rowt: entries (instance, block) sharing each instance's listed rows.
-cudaError_t launch_b_row_tasks(const BatchTable& rowt, cudaStream_t s) {
-    row_tasks_batched_kernel<<<152 * 2, 512, 0, s>>>(rowt);
+// The row tasks queued in q.q1; max_n bounds every queued instance's n.
+cudaError_t launch_b_row_tasks(const BatchQueues& q, int32_t max_n, cudaStream_t s) {
+    const size_t smem = 4 * (size_t)((max_n + 63) / 64 * 64);
+    if (smem > 48 * 1024) {
+        cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(row_tasks_batched_kernel), 6, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int per_sm = (int)std::min<size_t>(4, (227 * 1024) / (smem + 1024));  // 512 threads, 2048 per SM
+    row_tasks_batched_kernel<<<152 * (per_sm < 1 ? 1 : per_sm), 512, smem, s>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_scan(const BatchQueues& q, int32_t phase, int32_t strip, cudaStream_t s) {
+    scan_batched_kernel<<<1, 1024, 0, s>>>(q, phase, strip);
     return cudaGetLastError();
 }
 

@@ -389,11 +389,11 @@ __global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace 
     full_evaluation_body(w, conditional, strip, blockIdx.x, gridDim.x);
 }
 
-// Batched: each table entry is one block of one instance's evaluation.
-__global__ void __launch_bounds__(kThreads, 1) full_evaluation_batched_kernel(BatchTable t, int32_t stage,
-                                                                              int32_t conditional, int32_t strip) {
-    for_each_entry(t, stage, [&](const Instance& in, int32_t bid, int32_t nblk) {
-        full_evaluation_body(in.w, conditional, strip, bid, nblk);
+// Batched: each queue item is one block of one instance's evaluation (the
+// scan kernel queued exactly the instances that need one).
+__global__ void __launch_bounds__(kThreads, 1) full_evaluation_batched_kernel(BatchQueues q, int32_t strip) {
+    for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t bid, int32_t nblk) {
+        full_evaluation_body(in.w, 0, strip, bid, nblk);
     });
 }
 
@@ -427,14 +427,12 @@ cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cuda
 
 int32_t evaluation_strip() { return kStrip; }
 
-// eval: entries (instance, block) of the tile-pair items; the instances in
-// `stage` are evaluated (conditional: only those whose update needs it).
-cudaError_t launch_b_evaluation(const BatchTable& eval, int32_t stage, int32_t conditional, int32_t strip,
-                                cudaStream_t s) {
+// The evaluations queued in q.q0 (batch_blocks_eval(n, strip) blocks each).
+cudaError_t launch_b_evaluation(const BatchQueues& q, int32_t strip, cudaStream_t s) {
     const size_t smem = full_evaluation_smem_bytes();
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_batched_kernel), 4, smem);
     if (e != cudaSuccess) return e;
-    full_evaluation_batched_kernel<<<152, kThreads, smem, s>>>(eval, stage, conditional, strip);
+    full_evaluation_batched_kernel<<<152, kThreads, smem, s>>>(q, strip);
     return cudaGetLastError();
 }
 

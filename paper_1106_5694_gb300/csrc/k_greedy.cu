@@ -130,42 +130,6 @@ __device__ __forceinline__ void greedy_match_body(const Workspace& w, int32_t bi
 
 __global__ void greedy_match_kernel(Workspace w) { greedy_match_body(w, blockIdx.x, gridDim.x); }
 
-// Rescan for batched launches: one warp per owner, so that an instance's
-// owners spread over few blocks.  Same result as greedy_rescan_kernel.
-__device__ __forceinline__ void greedy_rescan_warp_body(const Workspace& w, const int32_t* mat, int32_t ld,
-                                                        unsigned long long* keys, const uint8_t* owner_free,
-                                                        const uint8_t* partner_free, int32_t count_round,
-                                                        int32_t bid, int32_t nblk) {
-    DeviceState* st = w.st;
-    if (count_round && bid == 0 && threadIdx.x == 0 && st->greedy_matched) {
-        st->greedy_rounds += 1;
-        st->greedy_matched = 0;
-    }
-    if (st->status != kRunning || st->greedy_remaining == 0) return;
-    const int32_t n = w.n;
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int32_t o = bid * nw + (threadIdx.x >> 5); o < n; o += nblk * nw) {
-        if (!owner_free[o]) continue;
-        const int32_t b = key_index(keys[o]);
-        if (b >= 0 && b < n && partner_free[b]) continue;  // best partner still free
-        const int32_t* row = mat + (size_t)o * ld;
-        if (lane == 0) atomicAdd((unsigned long long*)&st->greedy_rescans, 1ull);
-        unsigned long long best = 0;
-#pragma unroll 4
-        for (int32_t c = lane * 4; c < n; c += 128) {
-            const int4 v = *reinterpret_cast<const int4*>(row + c);
-            const uint32_t fr = *reinterpret_cast<const uint32_t*>(partner_free + c);
-            const int32_t vals[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (c + e < n && ((fr >> (8 * e)) & 0xffu)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
-        if (lane == 0) keys[o] = best;
-    }
-}
-
 // Rescan: for each free "owner" whose best partner was taken, find the best
 // free partner in its row of mat (a for agents over jobs, at for jobs over
 // agents).  One CTA per owner; 16-byte loads, several in flight per thread.
@@ -461,8 +425,8 @@ __global__ void range_check_kernel(Workspace w) {
     }
 }
 
-__global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchTable t) {
-    for_each_entry(t, kStageNew, [&](const Instance& in, int32_t bid, int32_t nblk) {
+__global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchQueues q) {
+    for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t bid, int32_t nblk) {
         const int32_t tx = (in.w.n + kT - 1) / kT;
         greedy_pass1_body(in.w, tx, tx * tx, bid, nblk);
     });
@@ -474,12 +438,60 @@ __global__ void __launch_bounds__(256) greedy_match_batched_kernel(BatchTable t)
     });
 }
 
-// rows = 1: rescan agents over rows of a (and count the round); 0: jobs over rows of at.
-__global__ void __launch_bounds__(256) greedy_rescan_batched_kernel(BatchTable t, int32_t rows) {
+// After a match: list the owners to rescan (owners 0..n-1 are agents, rows of
+// a; n..2n-1 are jobs, rows of at): free owners whose best partner was just
+// taken.  The list lives in ctl_slot (unused until the switching loop) and
+// its length in rescan_count (the scan kernel reads and clears it).
+__global__ void __launch_bounds__(256) greedy_dirty_batched_kernel(BatchTable t) {
     for_each_entry(t, kStageGreedy, [&](const Instance& in, int32_t bid, int32_t nblk) {
         const Workspace& w = in.w;
-        if (rows) greedy_rescan_warp_body(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1, bid, nblk);
-        else greedy_rescan_warp_body(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0, bid, nblk);
+        DeviceState* st = w.st;
+        if (st->status != kRunning || st->greedy_remaining == 0) return;
+        const int32_t n = w.n;
+        for (int32_t o = bid * blockDim.x + threadIdx.x; o < 2 * n; o += nblk * blockDim.x) {
+            const bool is_row = o < n;
+            const int32_t x = is_row ? o : o - n;
+            if (!(is_row ? w.free_a[x] : w.free_j[x])) continue;
+            const int32_t b = key_index(is_row ? w.g_row[x] : w.g_col[x]);
+            if (b >= 0 && b < n && (is_row ? w.free_j[b] : w.free_a[b])) continue;
+            w.ctl_slot[atomicAdd(&st->rescan_count, 1)] = o;
+        }
+    });
+}
+
+// One listed owner per item: its best free partner over its whole row, with
+// the CTA (the same scan as greedy_rescan_kernel).
+__global__ void __launch_bounds__(256) greedy_rescan_batched_kernel(BatchQueues q) {
+    __shared__ unsigned long long red[8];
+    for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t t, int32_t) {
+        const Workspace& w = in.w;
+        const int32_t n = w.n;
+        const int32_t o2 = w.ctl_slot[t];
+        const bool is_row = o2 < n;
+        const int32_t o = is_row ? o2 : o2 - n;
+        const int32_t* row = is_row ? w.a + (size_t)o * w.lda : w.at + (size_t)o * w.ldt;
+        const uint8_t* partner_free = is_row ? w.free_j : w.free_a;
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        unsigned long long best = 0;
+#pragma unroll 4
+        for (int32_t c = tid * 4; c < n; c += 1024) {
+            const int4 v = *reinterpret_cast<const int4*>(row + c);
+            const uint32_t fr = *reinterpret_cast<const uint32_t*>(partner_free + c);
+            const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c + e < n && ((fr >> (8 * e)) & 0xffu)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long m = 0;
+            for (int k = 0; k < 8; ++k) m = umax64(m, red[k]);
+            (is_row ? w.g_row : w.g_col)[o] = m;
+        }
+        __syncthreads();
     });
 }
 
@@ -507,20 +519,22 @@ cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// tiles: entries (instance, block) over the 64x64 tiles of a (pass 1 of the
-// instances in kStageNew).
-cudaError_t launch_b_pass1(const BatchTable& tiles, cudaStream_t s) {
-    greedy_pass1_batched_kernel<<<152 * 8, 256, 0, s>>>(tiles);
+// Pass 1 of the instances queued by the kScanPass1 scan (blocks over the
+// 64x64 tiles of a).
+cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s) {
+    greedy_pass1_batched_kernel<<<152 * 8, 256, 0, s>>>(q);
     return cudaGetLastError();
 }
 
-// One locally-dominant round of the instances in kStageGreedy.  rows:
-// entries over agents (256 per block and step); owners: entries over rows of
-// a and of at (8 warps per block, one owner per warp at a time).
-cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchTable& owners, cudaStream_t s) {
+// One locally-dominant round of the instances in kStageGreedy: match (rows:
+// entries over agents and jobs), list the owners to rescan, queue them
+// (scan), rescan each with one CTA.
+cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchQueues& q, cudaStream_t s) {
     greedy_match_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
-    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(owners, 1);
-    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(owners, 0);
+    greedy_dirty_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    cudaError_t e = launch_b_scan(q, kScanGreedy, 0, s);
+    if (e != cudaSuccess) return e;
+    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(q);
     return cudaGetLastError();
 }
 
