@@ -254,6 +254,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    # launch shapes of the evaluation for this size class (autotuner)
+    st_t, tuning = B.dgs_autotune(args.n, device=dev)
+    if st_t != B.DGS_OK:
+        tuning = {"error": B.dgs_status_string(st_t)}
     # warm-up, and the correctness gate against the oracle's stored result
     last = None
     for _ in range(max(args.warmup, 1)):
@@ -335,6 +339,10 @@ def run_ours(args):
     roofline_eval = roofline_entry("full_evaluation_kernel",
                                    "full difference evaluation (Algorithm 2 for all slots), every benefit once",
                                    4 * n * n + 24 * n, statistics.mean(eval_ms), n, args.workload, peak, peak_src)
+    roofline_eval["launch_shape"] = {k: tuning.get(k) for k in ("rows_per_thread", "strip")} \
+        if "error" not in tuning else tuning
+    roofline_eval["autotune_candidates_ms"] = {f"rows{c['rows_per_thread']}_strip{c['strip']}": round(c["ms"], 4)
+                                               for c in tuning.get("candidates", [])}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -140,6 +140,33 @@ DGS_API dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* s
                            dgs_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuning of launch shapes.  The paper fixes its block sizes by hand
+ * (Section 4); here the shape of the full difference evaluation (Algorithm 2
+ * for all slots: rows per thread and column tiles per work item) is chosen
+ * per size class by timing.  dgs_autotune times every candidate shape on a
+ * synthetic n x n instance (values in [0, 10016), a random assignment; it
+ * allocates about 4*n*n bytes for it) on `stream`, keeps the fastest for all
+ * sizes in the same class (n in (2^(b-1), 2^b]) for the rest of the process,
+ * and reports every candidate's time in *result (may be NULL).  The shape
+ * never changes a result (every key is a maximum over the same pairs); it
+ * only changes the time.  n in [2, 131072]; blocks until done.
+ * dgs_get_tuning reports the shape that solves of size n use now. */
+#define DGS_TUNE_MAX_CANDIDATES 16
+typedef struct {
+    int32_t n_lo, n_hi;       /* the size class the result applies to */
+    int32_t rows_per_thread;  /* chosen: 4 (1024-thread CTAs) or 8 (512) */
+    int32_t strip;            /* chosen: column tiles per work item, 0 = one
+                                 contiguous, equal range of tiles per CTA */
+    double best_ms;           /* evaluation time of the chosen shape */
+    int32_t candidates;       /* shapes timed */
+    int32_t cand_rows[DGS_TUNE_MAX_CANDIDATES];
+    int32_t cand_strip[DGS_TUNE_MAX_CANDIDATES];
+    double cand_ms[DGS_TUNE_MAX_CANDIDATES];  /* best of three launches each */
+} dgs_tuning;
+DGS_API dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream);
+DGS_API dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip);
+
+/* ------------------------------------------------------------------------
  * Batched solves.  The paper solves one instance at a time; its motivating
  * setting (Section 1: a central node that repeatedly assigns peers) solves
  * many.  dgs_solve_batched runs Algorithm 3 (from the start of Section 3.1)

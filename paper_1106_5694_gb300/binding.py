@@ -32,7 +32,7 @@ DGS_INIT_USER = 3
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
-            "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy"]
+            "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -84,6 +84,20 @@ class dgs_server_info(ctypes.Structure):
         ("completed", ctypes.c_int64),
         ("bytes_in_use", ctypes.c_size_t),
         ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+class dgs_tuning(ctypes.Structure):
+    _fields_ = [
+        ("n_lo", ctypes.c_int32),
+        ("n_hi", ctypes.c_int32),
+        ("rows_per_thread", ctypes.c_int32),
+        ("strip", ctypes.c_int32),
+        ("best_ms", ctypes.c_double),
+        ("candidates", ctypes.c_int32),
+        ("cand_rows", ctypes.c_int32 * 16),
+        ("cand_strip", ctypes.c_int32 * 16),
+        ("cand_ms", ctypes.c_double * 16),
     ]
 
 
@@ -142,6 +156,10 @@ def load():
     lib.dgs_server_get_info.restype = ctypes.c_int
     lib.dgs_server_destroy.argtypes = [P]
     lib.dgs_server_destroy.restype = None
+    lib.dgs_autotune.argtypes = [i32, ctypes.POINTER(dgs_tuning), P]
+    lib.dgs_autotune.restype = ctypes.c_int
+    lib.dgs_get_tuning.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.dgs_get_tuning.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -364,3 +382,24 @@ class Server:
 
 def dgs_server_create(budget_bytes: int, max_resident: int = 0) -> Server:
     return Server(budget_bytes, max_resident)
+
+
+def dgs_autotune(n: int, stream=None, device=None):
+    """dgs_autotune: returns (status, dict with the chosen shape, its size
+    class and every candidate's time)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    s_obj = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = dgs_tuning()
+    st = load().dgs_autotune(int(n), ctypes.byref(r), ctypes.c_void_p(s_obj.cuda_stream))
+    out = {"n_lo": r.n_lo, "n_hi": r.n_hi, "rows_per_thread": r.rows_per_thread, "strip": r.strip,
+           "best_ms": r.best_ms,
+           "candidates": [{"rows_per_thread": r.cand_rows[k], "strip": r.cand_strip[k], "ms": r.cand_ms[k]}
+                          for k in range(r.candidates)]}
+    return st, out
+
+
+def dgs_get_tuning(n: int):
+    """Returns (status, rows_per_thread, strip) used for solves of size n."""
+    rows, strip = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = load().dgs_get_tuning(int(n), ctypes.byref(rows), ctypes.byref(strip))
+    return st, int(rows.value), int(strip.value)

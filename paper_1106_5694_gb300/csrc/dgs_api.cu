@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <vector>
 
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
@@ -200,10 +202,11 @@ struct Solve {
         if (ar.base) cudaFreeAsync(ar.base, s);
     }
 
-    dgs_status setup(const int32_t* a, int32_t n, bool need_at) {
+    // pitched_lda > 0: a is already laid out with that pitch (used in place).
+    dgs_status setup(const int32_t* a, int32_t n, bool need_at, int32_t pitched_lda = 0) {
         plan.need_at = need_at;
-        plan.need_copy = (n % 4) != 0 || (reinterpret_cast<uintptr_t>(a) % 16) != 0;
-        plan.lda = plan.need_copy ? round_up32(n, 4) : n;
+        plan.need_copy = pitched_lda > 0 ? false : ((n % 4) != 0 || (reinterpret_cast<uintptr_t>(a) % 16) != 0);
+        plan.lda = pitched_lda > 0 ? pitched_lda : (plan.need_copy ? round_up32(n, 4) : n);
         plan.ldt = round_up32(n, 64);
         Arena sizing;
         Workspace tmp{};
@@ -247,6 +250,10 @@ struct Solve {
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         return DGS_OK;
     }
+
+    // Workspace for a matrix already laid out with pitch lda (lda % 4 == 0,
+    // 16-byte aligned), without the transposed copy.
+    dgs_status setup_pitched(const int32_t* a, int32_t n, int32_t lda) { return setup(a, n, false, lda); }
 
     dgs_status init_state(int32_t max_sweeps, const dgs_options* o) {
         DeviceState h{};
@@ -305,6 +312,20 @@ __global__ void arm_deadline_kernel(DeviceState* st, int64_t deadline_us) {
 }
 
 __global__ void record_initial_objective_kernel(DeviceState* st) { st->f_initial = st->f; }
+
+// Synthetic benefits for timing launch shapes: values in [0, 10016) from a
+// per-element hash (the range of peer-shaped instances, so the packed-key
+// path of the evaluation is the one timed).  Pitch lda, padding zero.
+__global__ void fill_synthetic_kernel(int32_t* a, int32_t n, int32_t lda, uint64_t seed) {
+    const size_t total = (size_t)n * lda;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + q * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        a[q] = (q % (size_t)lda) < (size_t)n ? (int32_t)(z % 10016u) : 0;
+    }
+}
 
 dgs_status map_device_status(const DeviceState& h) {
     if (h.status == kDone) return DGS_OK;
@@ -528,6 +549,98 @@ dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* sigma_out
     DeviceState h;
     DGS_TRY(S.read_state(&h));
     return map_device_status(h);
+}
+
+dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
+    if (n < 2 || n > kMaxN) return DGS_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t lda = round_up32(n, 4);
+    int32_t* buf = nullptr;
+    const size_t abytes = (size_t)n * lda * sizeof(int32_t);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), abytes + align_up((size_t)n * 4, 256), s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return DGS_ERR_OOM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    int32_t* a = buf;
+    int32_t* sigma = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(buf) + abytes);
+    dgs_status st = DGS_OK;
+    {
+        Solve S(s);
+        // a synthetic instance of this size with peer-like values, under a
+        // random assignment (the evaluation's time does not depend on which)
+        fill_synthetic_kernel<<<152 * 8, 256, 0, s>>>(a, n, lda, 0x9E3779B97F4A7C15ull ^ (uint64_t)n);
+        std::vector<int32_t> perm(n);
+        for (int32_t i = 0; i < n; ++i) perm[i] = i;
+        uint64_t x = 0xD1B54A32D192ED03ull ^ (uint64_t)n;
+        for (int32_t i = n - 1; i > 0; --i) {  // Fisher-Yates with splitmix64
+            x += 0x9E3779B97F4A7C15ull;
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            std::swap(perm[i], perm[z % (uint64_t)(i + 1)]);
+        }
+        e = cudaMemcpyAsync(sigma, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy assignment");
+        if (st == DGS_OK) st = S.setup_pitched(a, n, lda);
+        if (st == DGS_OK) st = S.init_state(0, nullptr);
+        if (st == DGS_OK && (e = launch_range_check(S.w, s)) != cudaSuccess) st = cuda_fail(e, "range check");
+        if (st == DGS_OK && (e = launch_start_from_tau(S.w, sigma, DGS_INIT_USER, S.seen, s)) != cudaSuccess)
+            st = cuda_fail(e, "start");
+        const int32_t rows_c[2] = {8, 4};
+        const int32_t strips[6] = {0, 4, 8, 16, 32, 64};  // 0: contiguous balanced ranges
+        dgs_tuning r{};
+        r.best_ms = 1e30;
+        EventPair ev;
+        if (st == DGS_OK) st = ev.begin(s);
+        for (int32_t ri = 0; ri < 2 && st == DGS_OK; ++ri) {
+            for (int32_t si = 0; si < 6 && st == DGS_OK; ++si) {
+                const EvalShape sh{rows_c[ri], strips[si]};
+                e = launch_full_evaluation_shape(S.w, 0, sh, s);  // warm-up
+                double best = 1e30;
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    e = cudaEventRecord(ev.a, s);
+                    if (e == cudaSuccess) e = launch_full_evaluation_shape(S.w, 0, sh, s);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev.b, s);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
+                    if (e == cudaSuccess) best = std::min(best, ev.elapsed_ms());
+                }
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "timing an evaluation shape");
+                    break;
+                }
+                const int32_t c = r.candidates++;
+                r.cand_rows[c] = sh.rows;
+                r.cand_strip[c] = sh.strip;
+                r.cand_ms[c] = best;
+                if (best < r.best_ms) {
+                    r.best_ms = best;
+                    r.rows_per_thread = sh.rows;
+                    r.strip = sh.strip;
+                }
+            }
+        }
+        if (st == DGS_OK) {
+            set_evaluation_shape(n, EvalShape{r.rows_per_thread, r.strip});
+            const int32_t b = size_bucket(n);
+            r.n_lo = b == 0 ? 1 : (1 << (b - 1)) + 1;
+            r.n_hi = 1 << b;
+            if (result) *result = r;
+        }
+    }
+    cudaFreeAsync(buf, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip) {
+    if (n <= 0 || n > kMaxN) return DGS_ERR_INVALID;
+    const EvalShape sh = evaluation_shape(n);
+    if (rows_per_thread) *rows_per_thread = sh.rows;
+    if (strip) *strip = sh.strip;
+    return DGS_OK;
 }
 
 const char* dgs_status_string(dgs_status status) {

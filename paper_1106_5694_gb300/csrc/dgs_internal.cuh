@@ -319,6 +319,15 @@ cudaError_t launch_range_check(const Workspace& w, cudaStream_t s);
 cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, int32_t mode, uint8_t* seen,
                                   cudaStream_t s);
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
+// Launch shape of the full evaluation (rows per thread 4 or 8; strip: column
+// tiles per work item, 0 = one contiguous balanced range of tiles per CTA).
+struct EvalShape {
+    int32_t rows, strip;
+};
+EvalShape evaluation_shape(int32_t n);
+void set_evaluation_shape(int32_t n, EvalShape shape);
+int32_t size_bucket(int32_t n);
+cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional, EvalShape shape, cudaStream_t s);
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s);
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s);

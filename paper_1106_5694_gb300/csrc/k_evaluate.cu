@@ -24,6 +24,10 @@
 // column-side maxima of each tile are combined across the CTA in shared
 // memory at the next barrier and committed with 64-bit atomicMax, which is
 // order independent and therefore deterministic.
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -32,9 +36,17 @@ namespace {
 constexpr int kT = 64;         // tile edge
 constexpr int kYP = kT + 4;    // Y row pitch (ints): 16-B aligned and int4-conflict-free
 constexpr int kStages = 5;
-constexpr int kThreads = 512;  // 8 row groups x 64 columns
-constexpr int kRows = 8;       // rows per thread
-constexpr int kGroups = kThreads / kT;
+
+// Thread geometry for kRows rows per thread: kThreads = 64 columns x
+// (64 / kRows) row groups; each thread copies kCopies row segments of X and
+// of Y per tile.
+template <int kRows>
+struct Geo {
+    static constexpr int kThreads = kT * kT / kRows;
+    static constexpr int kGroups = kThreads / kT;
+    static constexpr int kCopies = 1024 / kThreads;
+    static constexpr int kRowStep = kThreads / 16;
+};
 
 struct Stage {
     int32_t x[kT * kT];
@@ -46,17 +58,25 @@ struct Stage {
 };
 
 struct TileCursor {
-    int32_t item;   // index into the item table
-    int32_t k;      // current column tile
-    int32_t kend;   // one past the last column tile of the item
-    int32_t j;      // row block
+    int32_t j;      // row block of the current tile
+    int32_t k;      // column tile of the current tile
+    int32_t kend;   // one past the last column tile of the current row run
+    int32_t item;   // strided schedule: index of the current item
+    int32_t lin;    // contiguous schedule: linear index of the current tile
+    int32_t lend;   //   and one past the last tile of this block's range (< 2^31: nb <= 2048)
 };
 
-// Work items (row block J, first column tile J + strip * c) are numbered
-// J * chunks + c; items whose first tile lies past the last block are empty
-// and skipped.  Block b of the nblk blocks working on one instance walks
-// items b, b + nblk, b + 2 nblk, ...
-__device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t nb, int32_t strip, int32_t nblk) {
+// Two schedules of the upper-triangle tiles (J <= K) over the nblk blocks of
+// one instance.
+//  strip > 0 (strided items): item (J, c) = tiles J + strip*c .. + strip - 1
+//    of row block J, numbered J * chunks + c; block b walks items b, b +
+//    nblk, ...; items past the last tile are empty and skipped.
+//  strip == 0 (contiguous): the tiles in row-major order, split into nblk
+//    equal contiguous ranges; block b walks range b, one row run per row
+//    block it touches.
+// Either way every tile is visited by exactly one block.
+__device__ __forceinline__ bool cursor_strided(TileCursor& c, int32_t item, int32_t nb, int32_t strip,
+                                               int32_t nblk) {
     const int32_t chunks = (nb + strip - 1) / strip;
     const int32_t total = nb * chunks;
     for (; item < total; item += nblk) {
@@ -74,9 +94,39 @@ __device__ __forceinline__ bool cursor_load(TileCursor& c, int32_t item, int32_t
     return false;
 }
 
+// first tile of row block J in row-major upper-triangle order
+__device__ __forceinline__ int32_t tri_offset(int32_t J, int32_t nb) { return J * nb - J * (J - 1) / 2; }
+
+__device__ __forceinline__ bool cursor_first(TileCursor& c, int32_t nb, int32_t strip, int32_t bid, int32_t nblk) {
+    if (strip > 0) return cursor_strided(c, bid, nb, strip, nblk);
+    const int64_t total = tri_offset(nb, nb);
+    c.lin = (int32_t)(total * bid / nblk);
+    c.lend = (int32_t)(total * (bid + 1) / nblk);
+    if (c.lin >= c.lend) return false;
+    int32_t lo = 0, hi = nb;  // tri_offset(lo) <= lin < tri_offset(hi)
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (tri_offset(mid, nb) <= c.lin) lo = mid;
+        else hi = mid;
+    }
+    c.j = lo;
+    c.k = lo + (c.lin - tri_offset(lo, nb));
+    c.kend = min(nb, c.k + (c.lend - c.lin));
+    return true;
+}
+
 __device__ __forceinline__ bool cursor_next(TileCursor& c, int32_t nb, int32_t strip, int32_t nblk) {
-    if (++c.k < c.kend) return true;
-    return cursor_load(c, c.item + nblk, nb, strip, nblk);
+    if (strip > 0) {
+        if (++c.k < c.kend) return true;
+        return cursor_strided(c, c.item + nblk, nb, strip, nblk);
+    }
+    if (++c.lin >= c.lend) return false;
+    if (++c.k >= nb) {
+        ++c.j;
+        c.k = c.j;
+        c.kend = min(nb, c.k + (c.lend - c.lin));
+    }
+    return true;
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -86,52 +136,56 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// sigma of the rows this thread copies for tile (J, K): X rows J0+rq, J0+rq+32
-// and Y rows K0+rq, K0+rq+32 (row rq = threadIdx.x / 16).
+// sigma of the rows this thread copies for tile (J, K): X rows J0 + rq + c *
+// kRowStep and Y rows K0 + rq + c * kRowStep (rq = threadIdx.x / 16).
+template <int kRows>
 struct CopyRows {
-    int32_t x0, x1, y0, y1;
+    int32_t x[Geo<kRows>::kCopies], y[Geo<kRows>::kCopies];
 };
 
-__device__ __forceinline__ CopyRows copy_rows(const Workspace& w, int32_t J, int32_t K) {
+template <int kRows>
+__device__ __forceinline__ CopyRows<kRows> copy_rows(const Workspace& w, int32_t J, int32_t K) {
     const int32_t rq = threadIdx.x >> 4;
     const int32_t J0 = J * kT, K0 = K * kT, n = w.n;
-    CopyRows c;
-    c.x0 = (J0 + rq < n) ? w.sigma[J0 + rq] : -1;
-    c.x1 = (J0 + rq + 32 < n) ? w.sigma[J0 + rq + 32] : -1;
-    c.y0 = (K0 + rq < n) ? w.sigma[K0 + rq] : -1;
-    c.y1 = (K0 + rq + 32 < n) ? w.sigma[K0 + rq + 32] : -1;
+    CopyRows<kRows> c;
+#pragma unroll
+    for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
+        const int32_t r = rq + q * Geo<kRows>::kRowStep;
+        c.x[q] = (J0 + r < n) ? w.sigma[J0 + r] : -1;
+        c.y[q] = (K0 + r < n) ? w.sigma[K0 + r] : -1;
+    }
     return c;
 }
 
-// Issue this thread's four 16-byte copies of tile (J, K) into stage.
+template <int kRows>
+__device__ __forceinline__ CopyRows<kRows> no_rows() {
+    CopyRows<kRows> c;
+#pragma unroll
+    for (int q = 0; q < Geo<kRows>::kCopies; ++q) c.x[q] = c.y[q] = -1;
+    return c;
+}
+
+// Issue this thread's 16-byte copies of tile (J, K) into stage.
+template <int kRows>
 __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int32_t J, int32_t K,
-                                           const CopyRows& c) {
+                                           const CopyRows<kRows>& c) {
     const int32_t chunk = (threadIdx.x & 15) * 4;  // first int of the 16-byte chunk
     const int32_t rq = threadIdx.x >> 4;
     const int32_t J0 = J * kT, K0 = K * kT;
     const bool in_x = chunk < w.lda - K0;  // X rows hold columns K0.. (row pitch lda)
     const bool in_y = chunk < w.lda - J0;  // Y rows hold columns J0..
-    if (in_x && c.x0 >= 0) cp_async16(stage->x + rq * kT + chunk, w.a + (size_t)c.x0 * w.lda + K0 + chunk);
-    if (in_x && c.x1 >= 0) cp_async16(stage->x + (rq + 32) * kT + chunk, w.a + (size_t)c.x1 * w.lda + K0 + chunk);
-    if (in_y && c.y0 >= 0) cp_async16(stage->y + rq * kYP + chunk, w.a + (size_t)c.y0 * w.lda + J0 + chunk);
-    if (in_y && c.y1 >= 0) cp_async16(stage->y + (rq + 32) * kYP + chunk, w.a + (size_t)c.y1 * w.lda + J0 + chunk);
+#pragma unroll
+    for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
+        const int32_t r = rq + q * Geo<kRows>::kRowStep;
+        if (in_x && c.x[q] >= 0) cp_async16(stage->x + r * kT + chunk, w.a + (size_t)c.x[q] * w.lda + K0 + chunk);
+        if (in_y && c.y[q] >= 0) cp_async16(stage->y + r * kYP + chunk, w.a + (size_t)c.y[q] * w.lda + J0 + chunk);
+    }
     // sigma and D of the columns (arrays hold at least round_up(n, 64) entries)
     if (threadIdx.x < 16) cp_async16(stage->sk + chunk, w.sigma + K0 + chunk);
     else if (threadIdx.x < 32) cp_async16(stage->dk + chunk, w.diag + K0 + chunk);
     else if (threadIdx.x < 48) cp_async16(stage->sj + chunk, w.sigma + J0 + chunk);
     else if (threadIdx.x < 64) cp_async16(stage->dj + chunk, w.diag + J0 + chunk);
 }
-
-// Row-side state of a thread's 8 rows across a strip.  Exact path: best gain,
-// its lowest column, lowest partner agent among columns reaching it.  Packed
-// path (when |gain| * 2^s fits in int32, s = index bits): two int32 keys per
-// row, (gain << s) + (mask - column) and (gain << s) + (mask - partner agent),
-// where max picks the larger gain, then the lower index.
-struct RowState {
-    int32_t g[kRows];
-    int32_t c[kRows];
-    int32_t s[kRows];
-};
 
 // Packed-key geometry for this n and value range; pw = 0 means "exact path".
 struct Packing {
@@ -155,12 +209,48 @@ __device__ __forceinline__ unsigned long long unpack_key(int32_t key, const Pack
     return pack_gain(key >> __popc(pk.mask), (uint32_t)(pk.mask - (key & pk.mask)));
 }
 
-// One tile: thread (ty, tx) covers column k = K0 + tx and rows J0 + ty*8 .. +7.
-// Column-side partial keys go to colbuf (combined at the next barrier).
-template <bool kRagged, bool kPacked>
-__device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, const int32_t (&dj)[kRows],
-                                             const int32_t (&sj)[kRows], int32_t J0, int32_t K0, int32_t n,
-                                             const Packing& pk, unsigned long long* col_a,
+// Per-thread state of its kRows rows across a strip (tiles with the same row
+// block J).  Packed path (when |gain| * 2^s fits in int32, s = index bits):
+// two int32 keys per row, (gain << s) + (mask - column) in g and (gain << s) +
+// (mask - partner agent) in s, whose max picks the larger gain, then the lower
+// index; ca / cj: mask - row and mask - sigma(row), the column-side tie
+// offsets.  Exact path: best gain g, its lowest column c, lowest partner
+// agent s among the columns reaching it; sj = sigma of the rows.
+template <int kRows, bool kPacked>
+struct Rows {
+    int32_t g[kRows], s[kRows], d[kRows];
+    int32_t c[kPacked ? 1 : kRows];
+    int32_t ca[kPacked ? kRows : 1], cj[kPacked ? kRows : 1];
+    int32_t sj[kPacked ? 1 : kRows];
+};
+
+template <int kRows, bool kPacked>
+__device__ __forceinline__ void rows_start(Rows<kRows, kPacked>& rs, const Stage* stage, int32_t J0,
+                                           const Packing& pk) {
+    const int ty = threadIdx.x >> 6;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        rs.d[r] = stage->dj[ty * kRows + r];
+        if (kPacked) {
+            rs.g[r] = pk.mask;
+            rs.s[r] = pk.mask;
+            rs.ca[r] = pk.mask - (J0 + ty * kRows + r);
+            rs.cj[r] = pk.mask - stage->sj[ty * kRows + r];
+        } else {
+            rs.g[r] = 0;
+            rs.c[r] = -1;
+            rs.s[r] = 0x7fffffff;
+            rs.sj[r] = stage->sj[ty * kRows + r];
+        }
+    }
+}
+
+// One tile: thread (ty, tx) covers column k = K0 + tx and rows J0 + ty*kRows
+// .. + kRows - 1.  Column-side partial keys go to colbuf (combined at the
+// next barrier).
+template <int kRows, bool kRagged, bool kPacked>
+__device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPacked>& rs, int32_t J0, int32_t K0,
+                                             int32_t n, const Packing& pk, unsigned long long* col_a,
                                              unsigned long long* col_j) {
     const int tx = threadIdx.x & 63;
     const int ty = threadIdx.x >> 6;
@@ -181,13 +271,13 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, c
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int r = q * 4 + e;
-                    const int32_t jr = J0 + ty * kRows + r;
-                    if (kRagged && jr >= n) continue;
-                    const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
-                    rs.g[r] = max(rs.g[r], g * pk.pw + cka);          // row jr, lowest column
-                    rs.s[r] = max(rs.s[r], g * pk.pw + ckj);          // row jr, lowest partner agent
-                    ca = max(ca, g * pk.pw + (pk.mask - jr));          // row k, lowest column
-                    cj = max(cj, g * pk.pw + (pk.mask - sj[r]));       // row k, lowest partner agent
+                    if (kRagged && J0 + ty * kRows + r >= n) continue;
+                    const int32_t g = xrow[r * kT] + yv[e] - (rs.d[r] + dk);
+                    const int32_t gs = g * pk.pw;
+                    rs.g[r] = max(rs.g[r], gs + cka);  // row jr, lowest column
+                    rs.s[r] = max(rs.s[r], gs + ckj);  // row jr, lowest partner agent
+                    ca = max(ca, gs + rs.ca[r]);       // row k, lowest column
+                    cj = max(cj, gs + rs.cj[r]);       // row k, lowest partner agent
                 }
             }
             ka = unpack_key(ca, pk);
@@ -203,7 +293,7 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, c
                     const int r = q * 4 + e;
                     const int32_t jr = J0 + ty * kRows + r;
                     if (kRagged && jr >= n) continue;
-                    const int32_t g = xrow[r * kT] + yv[e] - dj[r] - dk;
+                    const int32_t g = xrow[r * kT] + yv[e] - rs.d[r] - dk;
                     // row side: row jr, partner column k (ascending in this thread)
                     {
                         const bool gt = g > rs.g[r];
@@ -216,7 +306,7 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, c
                     {
                         const bool gt = g > cg;
                         const bool eq = g == cg;
-                        cs = gt ? sj[r] : (eq ? min(cs, sj[r]) : cs);
+                        cs = gt ? rs.sj[r] : (eq ? min(cs, rs.sj[r]) : cs);
                         cc = gt ? jr : cc;
                         cg = max(cg, g);
                     }
@@ -232,7 +322,8 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, RowState& rs, c
     col_j[ty * kT + tx] = kj;
 }
 
-// Combine the 8 row-group partials of the previous tile's columns.
+// Combine the row-group partials of the previous tile's columns.
+template <int kRows>
 __device__ __forceinline__ void commit_columns(const unsigned long long* col_a, const unsigned long long* col_j,
                                                int32_t K0, int32_t n, const Workspace& w) {
     const int t = threadIdx.x;
@@ -241,14 +332,14 @@ __device__ __forceinline__ void commit_columns(const unsigned long long* col_a, 
     const unsigned long long* src = (t < kT) ? col_a : col_j;
     unsigned long long m = 0ull;
 #pragma unroll
-    for (int g = 0; g < kGroups; ++g) m = umax64(m, src[g * kT + q]);
+    for (int g = 0; g < Geo<kRows>::kGroups; ++g) m = umax64(m, src[g * kT + q]);
     const int32_t k = K0 + q;
     if (m != 0ull && k < n) atomicMax((t < kT) ? &w.key_a[k] : &w.key_j[k], m);
 }
 
-template <bool kPacked>
-__device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int32_t n, const Workspace& w,
-                                            const Packing& pk) {
+template <int kRows, bool kPacked>
+__device__ __forceinline__ void commit_rows(const Rows<kRows, kPacked>& rs, int32_t J0, int32_t n,
+                                            const Workspace& w, const Packing& pk) {
     const int lane = threadIdx.x & 31;
     const int ty = threadIdx.x >> 6;
 #pragma unroll
@@ -280,46 +371,43 @@ __device__ __forceinline__ void commit_rows(const RowState& rs, int32_t J0, int3
     }
 }
 
-// The evaluation of one instance by block bid of the nblk blocks assigned to
-// it (a CTA of the single-instance launch, or one entry of a batched work
-// table).  All threads of the CTA call it together.
-__device__ __forceinline__ void full_evaluation_body(const Workspace& w, int32_t conditional, int32_t strip,
-                                                     int32_t bid, int32_t nblk) {
-    DeviceState* st = w.st;
-    if (st->status != kRunning) return;
-    if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
-    if (conditional && bid == 0 && threadIdx.x == 0) st->full_evals += 1;
+template <int kRows>
+constexpr size_t eval_smem_bytes() {
+    return sizeof(Stage) * kStages + 2 * 2 * Geo<kRows>::kGroups * kT * sizeof(unsigned long long);
+}
 
+// The tile loop of one block of one instance's evaluation.
+template <int kRows, bool kPacked>
+__device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t strip, int32_t bid, int32_t nblk,
+                                                const Packing& pk) {
+    constexpr int kGroups = Geo<kRows>::kGroups;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* stages = reinterpret_cast<Stage*>(smem_raw);
     unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(Stage) * kStages);
-    // colbuf[b][0: agent keys 8x64 | 1: job keys 8x64], b = tile parity
+    // colbuf[b][0: agent keys kGroups x 64 | 1: job keys kGroups x 64], b = tile parity
 
     const int32_t n = w.n;
     const int32_t nb = (n + kT - 1) / kT;
-    const Packing pk = packing_for(n, st->max_abs);
-    const bool packed = pk.pw != 0 && !w.exact_keys;
 
     // producer cursor: kStages - 1 tiles ahead of the consumer; the rows
     // (sigma) it will copy are loaded two tiles before they are needed
     TileCursor prod;
-    bool prod_ok = cursor_load(prod, bid, nb, strip, nblk);
+    bool prod_ok = cursor_first(prod, nb, strip, bid, nblk);
     for (int s = 0; s < kStages - 1; ++s) {
         if (prod_ok) {
-            issue_tile(w, &stages[s], prod.j, prod.k, copy_rows(w, prod.j, prod.k));
+            issue_tile<kRows>(w, &stages[s], prod.j, prod.k, copy_rows<kRows>(w, prod.j, prod.k));
             prod_ok = cursor_next(prod, nb, strip, nblk);
         }
         cp_async_commit();
     }
     TileCursor ahead = prod;  // one tile after prod
     bool ahead_ok = prod_ok && cursor_next(ahead, nb, strip, nblk);
-    CopyRows rows_now = prod_ok ? copy_rows(w, prod.j, prod.k) : CopyRows{-1, -1, -1, -1};
-    CopyRows rows_next = ahead_ok ? copy_rows(w, ahead.j, ahead.k) : CopyRows{-1, -1, -1, -1};
+    CopyRows<kRows> rows_now = prod_ok ? copy_rows<kRows>(w, prod.j, prod.k) : no_rows<kRows>();
+    CopyRows<kRows> rows_next = ahead_ok ? copy_rows<kRows>(w, ahead.j, ahead.k) : no_rows<kRows>();
 
     TileCursor cons;
-    bool cons_ok = cursor_load(cons, bid, nb, strip, nblk);
-    RowState rs;
-    int32_t dj[kRows], sj[kRows];
+    bool cons_ok = cursor_first(cons, nb, strip, bid, nblk);
+    Rows<kRows, kPacked> rs;
     bool item_start = true;
     int32_t t = 0, prev_k0 = -1;
     while (cons_ok) {
@@ -328,72 +416,72 @@ __device__ __forceinline__ void full_evaluation_body(const Workspace& w, int32_t
         __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
         const Stage* stage = &stages[t % kStages];
         if (item_start) {
-            const int ty = threadIdx.x >> 6;
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                dj[r] = stage->dj[ty * kRows + r];
-                sj[r] = stage->sj[ty * kRows + r];
-                rs.g[r] = packed ? pk.mask : 0;
-                rs.c[r] = -1;
-                rs.s[r] = packed ? pk.mask : 0x7fffffff;
-            }
+            rows_start<kRows, kPacked>(rs, stage, J0, pk);
             item_start = false;
         }
         if (prev_k0 >= 0) {
             const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
-            commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
+            commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
         }
         if (prod_ok) {
-            issue_tile(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, rows_now);
+            issue_tile<kRows>(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, rows_now);
             prod = ahead;
             prod_ok = ahead_ok;
             rows_now = rows_next;
             if (ahead_ok) {
                 ahead_ok = cursor_next(ahead, nb, strip, nblk);
-                if (ahead_ok) rows_next = copy_rows(w, ahead.j, ahead.k);
+                if (ahead_ok) rows_next = copy_rows<kRows>(w, ahead.j, ahead.k);
             }
         }
         cp_async_commit();
         const int32_t K0 = cons.k * kT;
         unsigned long long* cb = colbuf + (t & 1) * 2 * kGroups * kT;
-        const bool ragged = (J0 + kT > n) || (K0 + kT > n);
-        if (packed) {
-            if (ragged) compute_tile<true, true>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
-            else compute_tile<false, true>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
-        } else {
-            if (ragged) compute_tile<true, false>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
-            else compute_tile<false, false>(stage, rs, dj, sj, J0, K0, n, pk, cb, cb + kGroups * kT);
-        }
-        if (cons.k + 1 >= cons.kend) {
-            if (packed) commit_rows<true>(rs, J0, n, w, pk);
-            else commit_rows<false>(rs, J0, n, w, pk);
-        }
+        if ((J0 + kT > n) || (K0 + kT > n)) compute_tile<kRows, true, kPacked>(stage, rs, J0, K0, n, pk, cb, cb + kGroups * kT);
+        else compute_tile<kRows, false, kPacked>(stage, rs, J0, K0, n, pk, cb, cb + kGroups * kT);
+        const bool run_end = cons.k + 1 >= cons.kend;  // last tile of this row run
+        if (run_end) commit_rows<kRows, kPacked>(rs, J0, n, w, pk);
         prev_k0 = K0;
         ++t;
-        if (++cons.k >= cons.kend) {
-            cons_ok = cursor_load(cons, cons.item + nblk, nb, strip, nblk);
-            item_start = true;
-        }
+        cons_ok = cursor_next(cons, nb, strip, nblk);
+        item_start = run_end;
     }
     cp_async_wait<0>();
     __syncthreads();
     if (prev_k0 >= 0) {
         const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
-        commit_columns(cb, cb + kGroups * kT, prev_k0, n, w);
+        commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
     }
     __syncthreads();  // the stages and colbuf may be reused by the caller's next call
 }
 
-__global__ void __launch_bounds__(kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
-                                                                      int32_t strip) {
-    full_evaluation_body(w, conditional, strip, blockIdx.x, gridDim.x);
+// The evaluation of one instance by block bid of the nblk blocks assigned to
+// it (a CTA of the single-instance launch, or one item of a batched queue).
+// All threads of the CTA call it together.
+template <int kRows>
+__device__ __forceinline__ void full_evaluation_body(const Workspace& w, int32_t conditional, int32_t strip,
+                                                     int32_t bid, int32_t nblk) {
+    DeviceState* st = w.st;
+    if (st->status != kRunning) return;
+    if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
+    if (conditional && bid == 0 && threadIdx.x == 0) st->full_evals += 1;
+    const Packing pk = packing_for(w.n, st->max_abs);
+    if (pk.pw != 0 && !w.exact_keys) evaluation_loop<kRows, true>(w, strip, bid, nblk, pk);
+    else evaluation_loop<kRows, false>(w, strip, bid, nblk, pk);
+}
+
+template <int kRows>
+__global__ void __launch_bounds__(Geo<kRows>::kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
+                                                                                  int32_t strip) {
+    full_evaluation_body<kRows>(w, conditional, strip, blockIdx.x, gridDim.x);
 }
 
 // Batched: each queue item is one block of one instance's evaluation (the
 // scan kernel queued exactly the instances that need one).
-__global__ void __launch_bounds__(kThreads, 1) full_evaluation_batched_kernel(BatchQueues q, int32_t strip) {
+template <int kRows>
+__global__ void __launch_bounds__(Geo<kRows>::kThreads, 1) full_evaluation_batched_kernel(BatchQueues q,
+                                                                                          int32_t strip) {
     for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t bid, int32_t nblk) {
-        full_evaluation_body(in.w, 0, strip, bid, nblk);
+        full_evaluation_body<kRows>(in.w, 0, strip, bid, nblk);
     });
 }
 
@@ -411,28 +499,69 @@ __global__ void keys_to_slots_kernel(Workspace w, int32_t* ag, int32_t* aj, int3
 
 }  // namespace
 
+// Launch shape of the single-instance evaluation: rows per thread (4: 1024
+// threads per CTA; 8: 512) and strip (column tiles per work item; 0: one
+// contiguous balanced range of tiles per CTA), per size
+// class (bucket = bit length of n - 1).  Defaults until an autotune sets a
+// class; DGS_EVAL_ROWS / DGS_EVAL_STRIP override every class (tests).  The
+// shape never changes a result: every key is a maximum over the same pairs.
 constexpr int kStrip = 8;
+constexpr int32_t kBuckets = 18;
+std::atomic<int32_t> g_shape[kBuckets];  // 0: default, else rows * 256 + strip
 
-size_t full_evaluation_smem_bytes() { return sizeof(Stage) * kStages + 2 * 2 * kGroups * kT * sizeof(unsigned long long); }
+int32_t size_bucket(int32_t n) { return n <= 1 ? 0 : std::min<int32_t>(kBuckets - 1, 32 - __builtin_clz((uint32_t)(n - 1))); }
+
+int32_t env_int(const char* name) {
+    const char* e = std::getenv(name);
+    return e ? std::atoi(e) : 0;
+}
+
+EvalShape evaluation_shape(int32_t n) {
+    static const int32_t env_rows = env_int("DGS_EVAL_ROWS");
+    static const int32_t env_strip = env_int("DGS_EVAL_STRIP");
+    EvalShape sh{8, kStrip};
+    const int32_t v = g_shape[size_bucket(n)].load(std::memory_order_relaxed);
+    if (v != 0) sh = EvalShape{v >> 8, v & 255};
+    if (env_rows == 4 || env_rows == 8) sh.rows = env_rows;
+    if (env_strip >= 0 && env_strip <= 255 && std::getenv("DGS_EVAL_STRIP")) sh.strip = env_strip;
+    return sh;
+}
+
+void set_evaluation_shape(int32_t n, EvalShape sh) {
+    g_shape[size_bucket(n)].store(sh.rows * 256 + sh.strip, std::memory_order_relaxed);
+}
+
+size_t full_evaluation_smem_bytes() { return eval_smem_bytes<8>(); }
+
+template <int kRows>
+static cudaError_t launch_eval_rows(const Workspace& w, int32_t conditional, int32_t strip, cudaStream_t s) {
+    constexpr size_t smem = eval_smem_bytes<kRows>();
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel<kRows>), kRows == 8 ? 0 : 7,
+                                      smem);
+    if (e != cudaSuccess) return e;
+    full_evaluation_kernel<kRows><<<152, Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional, EvalShape sh, cudaStream_t s) {
+    return sh.rows == 4 ? launch_eval_rows<4>(w, conditional, sh.strip, s)
+                        : launch_eval_rows<8>(w, conditional, sh.strip, s);
+}
 
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s) {
-    const size_t smem = full_evaluation_smem_bytes();
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel), 0, smem);
-    if (e != cudaSuccess) return e;
-    int grid = 152;
-    if (grid < 1) grid = 1;
-    full_evaluation_kernel<<<grid, kThreads, smem, s>>>(w, conditional, kStrip);
-    return cudaGetLastError();
+    return launch_full_evaluation_shape(w, conditional, evaluation_shape(w.n), s);
 }
 
 int32_t evaluation_strip() { return kStrip; }
 
-// The evaluations queued in q.q0 (batch_blocks_eval(n, strip) blocks each).
+// The evaluations queued in q.q0 (batch_blocks_eval(n, strip) blocks each),
+// 512 threads per CTA (the 1024-thread variant would spill the instance's
+// workspace pointers it reads from global memory).
 cudaError_t launch_b_evaluation(const BatchQueues& q, int32_t strip, cudaStream_t s) {
-    const size_t smem = full_evaluation_smem_bytes();
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_batched_kernel), 4, smem);
+    constexpr size_t smem = eval_smem_bytes<8>();
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_batched_kernel<8>), 4, smem);
     if (e != cudaSuccess) return e;
-    full_evaluation_batched_kernel<<<152, kThreads, smem, s>>>(q, strip);
+    full_evaluation_batched_kernel<8><<<152, Geo<8>::kThreads, smem, s>>>(q, strip);
     return cudaGetLastError();
 }
 

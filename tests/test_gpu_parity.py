@@ -239,12 +239,19 @@ print(json.dumps(out))
                                  {"DGS_CTL_MODE": "1"}, {"DGS_CTL_MODE": "0"},
                                  {"DGS_CTL_MODE": "0", "DGS_UPDATE_POLICY": "2"},
                                  {"DGS_SHORT_WRAPS": "1"}, {"DGS_SHORT_WRAPS": "1", "DGS_CTL_MODE": "1"},
-                                 {"DGS_EXACT_KEYS": "1"}])
+                                 {"DGS_EXACT_KEYS": "1"}, {"DGS_EVAL_ROWS": "8"},
+                                 {"DGS_EVAL_ROWS": "8", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_ROWS": "4", "DGS_EVAL_STRIP": "3", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_STRIP": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_STRIP": "32", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_STRIP": "0", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_STRIP": "0", "DGS_EVAL_ROWS": "4", "DGS_EXACT_KEYS": "1"}])
 def test_internal_paths_agree_with_oracle(env):
     """Forcing the full-evaluation or row-task update path, placing the
     controller's scratch in global memory, making its reservation keys and
-    claim stamps wrap every few rounds, or disabling the evaluation kernel's
-    packed 32-bit keys, must not change any result."""
+    claim stamps wrap every few rounds, disabling the evaluation kernel's
+    packed 32-bit keys, or running it with other launch shapes (rows per
+    thread, strip length), must not change any result."""
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
