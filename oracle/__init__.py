@@ -27,10 +27,13 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 INIT_GREEDY = 0
+INIT_RANDOM = 1
 INIT_IDENTITY = 2
 INIT_USER = 3
 CC_SLOTS = 0
 CC_LITERAL_AGENTS = 1
+REEVAL_BOX = 0
+REEVAL_ALL = 1
 OK = 0
 ERR_INVALID = 1
 ERR_RANGE = 2
@@ -85,7 +88,11 @@ def _load():
     lib.oracle_evaluate_all.restype = None
     lib.oracle_check_conflicts.argtypes = [i32, P, P, P, P, P, P, P]
     lib.oracle_check_conflicts.restype = None
-    lib.oracle_dgs_parallel.argtypes = [P, i32, i32, P, i32, i32, P, P, P, i32, P, P, P]
+    lib.oracle_dgs_parallel.argtypes = [P, i32, i32, P, ctypes.c_uint64, i32, i32, i32, P, P, P, i32, P, P, P]
+    lib.oracle_random_permutation.argtypes = [i32, ctypes.c_uint64, P]
+    lib.oracle_random_permutation.restype = None
+    lib.oracle_splitmix64_next.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_splitmix64_next.restype = ctypes.c_uint64
     lib.oracle_dgs_parallel.restype = ctypes.c_int
     lib.oracle_hungarian.argtypes = [P, i32, P]
     lib.oracle_hungarian.restype = i64
@@ -173,9 +180,25 @@ class SolveResult:
     trace_objective: np.ndarray
 
 
+def random_permutation(n: int, seed: int) -> np.ndarray:
+    """The random start: splitmix64 from seed, Fisher-Yates (Durstenfeld)."""
+    tau = np.empty(max(n, 1), np.int32)
+    _load().oracle_random_permutation(n, ctypes.c_uint64(seed), _p(tau))
+    return tau[:n].copy()
+
+
+def splitmix64(seed: int, count: int):
+    """The first `count` outputs of splitmix64 started at seed."""
+    state = ctypes.c_uint64(seed)
+    return [int(_load().oracle_splitmix64_next(ctypes.byref(state))) for _ in range(count)]
+
+
 def dgs_parallel(a, init: int = INIT_GREEDY, init_tau=None, max_sweeps: int = 0,
-                 cc_rule: int = CC_SLOTS, trace_cap: int = 0) -> SolveResult:
-    """Algorithm 3 (parallel DGS) with the readings R1-R5."""
+                 cc_rule: int = CC_SLOTS, trace_cap: int = 0, seed: int = 0,
+                 reeval: int = REEVAL_BOX) -> SolveResult:
+    """Algorithm 3 (parallel DGS) with the readings R1-R5 (reeval=REEVAL_ALL:
+    every slot re-evaluated after each parallel switch; init=INIT_RANDOM:
+    random start from seed)."""
     a = _c(a)
     n = a.shape[0]
     tau = np.zeros(max(n, 1), np.int32)
@@ -186,7 +209,7 @@ def dgs_parallel(a, init: int = INIT_GREEDY, init_tau=None, max_sweeps: int = 0,
     tf = np.zeros(max(trace_cap, 1), np.int64)
     it = _c(init_tau) if init_tau is not None else None
     status = _load().oracle_dgs_parallel(
-        _p(a), n, init, _p(it), max_sweeps, cc_rule, _p(tau), ctypes.byref(f),
+        _p(a), n, init, _p(it), ctypes.c_uint64(seed), max_sweeps, cc_rule, reeval, _p(tau), ctypes.byref(f),
         ctypes.byref(st), trace_cap, _p(ta), _p(tp), _p(tf))
     k = min(st.sweeps, trace_cap)
     return SolveResult(status, tau[:n].copy(), f.value, st.sweeps, st.passes,

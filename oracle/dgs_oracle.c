@@ -214,10 +214,33 @@ static void do_exchange(int32_t* sigma, int32_t* tau, int32_t u, int32_t v)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Random start (Section 3.1): splitmix64 (Steele, Lea, Flood 2014) and the
+ * Fisher-Yates shuffle in Durstenfeld's form. */
+uint64_t oracle_splitmix64_next(uint64_t* state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void oracle_random_permutation(int32_t n, uint64_t seed, int32_t* tau_out)
+{
+    uint64_t state = seed;
+    for (int32_t i = 0; i < n; ++i) tau_out[i] = i;
+    for (int32_t i = n - 1; i > 0; --i) {
+        int32_t j = (int32_t)(oracle_splitmix64_next(&state) % (uint64_t)(i + 1));
+        int32_t t = tau_out[i];
+        tau_out[i] = tau_out[j];
+        tau_out[j] = t;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 3 (parallel DGS). */
 int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
-                        const int32_t* init_tau, int32_t max_sweeps,
-                        int32_t cc_rule, int32_t* tau_out, int64_t* f_out,
+                        const int32_t* init_tau, uint64_t seed, int32_t max_sweeps,
+                        int32_t cc_rule, int32_t reeval_rule, int32_t* tau_out, int64_t* f_out,
                         oracle_stats* stats, int32_t trace_cap,
                         int32_t* trace_accepted, int32_t* trace_applied,
                         int64_t* trace_objective)
@@ -245,6 +268,8 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
         oracle_greedy_init(a, n, tau);
     } else if (init_mode == ORACLE_INIT_IDENTITY) {
         for (int32_t i = 0; i < n; ++i) tau[i] = i;
+    } else if (init_mode == ORACLE_INIT_RANDOM) {
+        oracle_random_permutation(n, seed, tau);
     } else if (init_mode == ORACLE_INIT_USER && init_tau != NULL) {
         memset(in_ca, 0, (size_t)n);
         for (int32_t i = 0; i < n; ++i) {
@@ -326,11 +351,13 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
             }
             st.swaps_applied += applied;
 
-            /* Re-evaluation of the agents and jobs not in C (reading R4). */
+            /* Re-evaluation of the agents and jobs not in C (reading R4), or
+             * of every agent and job (ORACLE_REEVAL_ALL). */
+            const int all = reeval_rule == ORACLE_REEVAL_ALL;
             for (int32_t i = 0; i < n; ++i)
-                if (!in_ca[i]) { oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]); st.evaluations++; }
+                if (all || !in_ca[i]) { oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]); st.evaluations++; }
             for (int32_t j = 0; j < n; ++j)
-                if (!in_cj[j]) { oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]); st.evaluations++; }
+                if (all || !in_cj[j]) { oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]); st.evaluations++; }
 
             if (st.sweeps < trace_cap) {
                 if (trace_accepted) trace_accepted[st.sweeps] = accepted;

@@ -23,7 +23,8 @@
  *   R3 the conflict set C of Algorithm 4 is a set of candidate SLOTS (agent
  *      slots and job slots), partners are looked up in the current sigma.
  *   R4 after the parallel switch, slots not in C are re-evaluated; slots in C
- *      keep their (stale) candidate.
+ *      keep their (stale) candidate (the alternative "re-evaluate every
+ *      slot" is the option ORACLE_REEVAL_ALL).
  *   R5 the outer repeat stops when a pass leaves f unchanged.
  *
  * Parity: the algorithm is a heuristic, so there is no closed form for its
@@ -40,8 +41,9 @@
 extern "C" {
 #endif
 
-enum { ORACLE_INIT_GREEDY = 0, ORACLE_INIT_IDENTITY = 2, ORACLE_INIT_USER = 3 };
+enum { ORACLE_INIT_GREEDY = 0, ORACLE_INIT_RANDOM = 1, ORACLE_INIT_IDENTITY = 2, ORACLE_INIT_USER = 3 };
 enum { ORACLE_CC_SLOTS = 0, ORACLE_CC_LITERAL_AGENTS = 1 };
+enum { ORACLE_REEVAL_BOX = 0, ORACLE_REEVAL_ALL = 1 };
 enum { ORACLE_OK = 0, ORACLE_ERR_INVALID = 1, ORACLE_ERR_RANGE = 2, ORACLE_TIMEOUT = 5 };
 
 typedef struct {
@@ -59,6 +61,15 @@ int oracle_range_ok(const int32_t* a, int32_t n);
 
 /* Global greedy initial solution (Section 3.1; reading R1). */
 void oracle_greedy_init(const int32_t* a, int32_t n, int32_t* tau_out);
+
+/* Random initial solution (Section 3.1, the start the paper itself uses):
+ * the identity shuffled by Fisher-Yates in Durstenfeld's form, for i = n-1
+ * down to 1 swap positions i and (next() mod (i + 1)), with next() the
+ * splitmix64 generator of Steele, Lea and Flood (2014) started at seed. */
+void oracle_random_permutation(int32_t n, uint64_t seed, int32_t* tau_out);
+
+/* One step of splitmix64: advances *state and returns the next output. */
+uint64_t oracle_splitmix64_next(uint64_t* state);
 
 /* Algorithm 2 (ADE) for agent i: best strictly positive 2-exchange gain and
  * the job it moves agent i to; gain 0 and job -1 when none improves. */
@@ -86,17 +97,20 @@ void oracle_check_conflicts(int32_t n, const int32_t* sigma,
 
 /* Algorithm 3 (parallel DGS) to termination or until max_sweeps switching
  * iterations have run (max_sweeps <= 0: no cap).  init_mode is one of
- * ORACLE_INIT_*; init_tau is read only for ORACLE_INIT_USER.  cc_rule selects
- * reading R3 (ORACLE_CC_SLOTS) or the literal agent-set C
- * (ORACLE_CC_LITERAL_AGENTS, kept only to show that it never terminates).
+ * ORACLE_INIT_*; init_tau is read only for ORACLE_INIT_USER, seed only for
+ * ORACLE_INIT_RANDOM.  cc_rule selects reading R3 (ORACLE_CC_SLOTS) or the
+ * literal agent-set C (ORACLE_CC_LITERAL_AGENTS, kept only to show that it
+ * never terminates).  reeval_rule selects which slots are re-evaluated after
+ * each parallel switch: ORACLE_REEVAL_BOX (reading R4: the slots not in C) or
+ * ORACLE_REEVAL_ALL (every slot).
  * Per-sweep trace arrays (may be NULL) receive, for sweep s < trace_cap, the
  * number of accepted candidate slots, the number of committed exchanges and
  * f after the sweep.  Returns ORACLE_OK, ORACLE_TIMEOUT (tau_out and f_out
  * still hold the valid assignment reached), ORACLE_ERR_INVALID or
  * ORACLE_ERR_RANGE. */
 int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
-                        const int32_t* init_tau, int32_t max_sweeps,
-                        int32_t cc_rule, int32_t* tau_out, int64_t* f_out,
+                        const int32_t* init_tau, uint64_t seed, int32_t max_sweeps,
+                        int32_t cc_rule, int32_t reeval_rule, int32_t* tau_out, int64_t* f_out,
                         oracle_stats* stats, int32_t trace_cap,
                         int32_t* trace_accepted, int32_t* trace_applied,
                         int64_t* trace_objective);

@@ -22,7 +22,9 @@ MUTATIONS = {
     "cc_partner_not_through_sigma": ("int32_t ip = sigma[agent_job[i]];\n        if (cr[i] || cr[ip]) {",
                                      "int32_t ip = agent_job[i];\n        if (cr[i] || cr[ip]) {"),
     "cc_job_owner_unchecked": ("if (cr[owner] || cr[partner]) {", "if (cr[partner]) {"),
-    "reevaluate_wrong_set": ("if (!in_ca[i]) { oracle_ade", "if (in_ca[i]) { oracle_ade"),
+    "reevaluate_wrong_set": ("if (all || !in_ca[i]) { oracle_ade", "if (all || in_ca[i]) { oracle_ade"),
+    "reevaluate_all_ignored": ("const int all = reeval_rule == ORACLE_REEVAL_ALL;", "const int all = 0;"),
+    "random_shuffle_off_by_one": ("% (uint64_t)(i + 1));", "% (uint64_t)i);"),
     "apply_non_improving": ("                if (g > 0) {\n                    do_exchange",
                             "                if (g >= 0) {\n                    do_exchange"),
     "greedy_tie_job_first": ("((uint64_t)i << 17) | (uint64_t)j;", "((uint64_t)j << 17) | (uint64_t)i;"),

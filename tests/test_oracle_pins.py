@@ -30,11 +30,12 @@ def _init_mode(name):
 
 
 # ---------------------------------------------------------------- hand traces
-@pytest.mark.parametrize("name", ["n3_identity", "n3_greedy", "n2_antidiagonal"])
+@pytest.mark.parametrize("name", ["n3_identity", "n3_greedy", "n2_antidiagonal", "n3_identity_reeval_all"])
 def test_hand_trace(name):
     t = _traces()[name]
     a = np.array(t["a"], np.int32)
-    r = oracle.dgs_parallel(a, init=_init_mode(t["init"]), trace_cap=64)
+    reeval = oracle.REEVAL_ALL if t.get("reeval") == "all" else oracle.REEVAL_BOX
+    r = oracle.dgs_parallel(a, init=_init_mode(t["init"]), trace_cap=64, reeval=reeval)
     assert r.status == oracle.OK
     assert r.tau.tolist() == t["tau"]
     assert r.objective == t["objective"]
@@ -352,3 +353,57 @@ def test_optimality_gap_is_small_soft_report(capsys):
         gaps.append(100.0 * (opt - r.objective) / opt)
     print("DGS optimality gap %:", [round(g, 3) for g in gaps])
     assert max(gaps) < 5.0
+
+
+# ------------------------------------------- random start, re-evaluate-all rule
+def test_splitmix64_reference_outputs():
+    """splitmix64 (Steele, Lea, Flood 2014): the published reference
+    generator's first outputs from state 0."""
+    assert oracle.splitmix64(0, 3) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_random_permutation_is_a_uniform_shuffle():
+    """Fisher-Yates (Durstenfeld) over a uniform generator: every one of the
+    3! permutations of n = 3 about equally often over 6000 seeds (chi-square
+    with 5 degrees of freedom below its 0.1% critical value 20.5)."""
+    from collections import Counter
+    counts = Counter(tuple(oracle.random_permutation(3, s).tolist()) for s in range(6000))
+    assert len(counts) == 6
+    chi2 = sum((c - 1000) ** 2 / 1000 for c in counts.values())
+    assert chi2 < 20.5, counts
+    for s in range(50):
+        p = oracle.random_permutation(37, s)
+        assert sorted(p.tolist()) == list(range(37))
+
+
+def test_random_start_is_the_user_start_of_its_permutation():
+    a = inputs.peer_shaped(70, 3)
+    for seed in (0, 1, 12345):
+        r = oracle.dgs_parallel(a, init=oracle.INIT_RANDOM, seed=seed)
+        u = oracle.dgs_parallel(a, init=oracle.INIT_USER, init_tau=oracle.random_permutation(70, seed))
+        assert r.status == u.status == oracle.OK
+        assert r.tau.tolist() == u.tau.tolist() and r.objective == u.objective and r.sweeps == u.sweeps
+
+
+@pytest.mark.parametrize("kind,n,seed", CASES)
+def test_reeval_all_invariants(kind, n, seed):
+    """Every slot fresh after each switch: each sweep accepts and applies at
+    least one exchange and strictly raises f; the result is a 2-exchange
+    local optimum below the optimum."""
+    a = _make(kind, n, seed)
+    for init in (oracle.INIT_GREEDY, oracle.INIT_IDENTITY, oracle.INIT_RANDOM):
+        r = oracle.dgs_parallel(a, init=init, seed=seed, reeval=oracle.REEVAL_ALL, trace_cap=100000)
+        assert r.status == oracle.OK
+        assert sorted(r.tau.tolist()) == list(range(n))
+        assert r.objective == _full_objective(a, r.tau)
+        assert _no_improving_exchange(a, r.tau)
+        opt = oracle.brute_force(a)[0] if n <= 9 else oracle.hungarian(a)[0]
+        assert r.objective <= opt
+        assert np.all(r.trace_applied >= 1)
+        if init == oracle.INIT_GREEDY:
+            f0 = _full_objective(a, oracle.greedy_init(a))
+        elif init == oracle.INIT_IDENTITY:
+            f0 = _full_objective(a, np.arange(n))
+        else:
+            f0 = _full_objective(a, oracle.random_permutation(n, seed))
+        assert np.all(np.diff(np.concatenate([[f0], r.trace_objective])) > 0)
