@@ -61,9 +61,22 @@ typedef enum {
 
 typedef enum {
     DGS_INIT_GREEDY = 0,   /* global greedy start (Section 3.1, default) */
+    DGS_INIT_RANDOM = 1,   /* random start (Section 3.1, the paper's own): the
+                              identity shuffled by Fisher-Yates (Durstenfeld:
+                              for i = n-1 .. 1 swap i with next() mod (i+1)),
+                              next() = splitmix64 (Steele, Lea, Flood 2014)
+                              started at dgs_options.seed */
     DGS_INIT_IDENTITY = 2, /* agent i starts on job i */
     DGS_INIT_USER = 3      /* caller's permutation in dgs_options.init_sigma */
 } dgs_init_mode;
+
+/* Which slots are re-evaluated after each parallel switch of Algorithm 3. */
+typedef enum {
+    DGS_REEVAL_BOX = 0,    /* the slots not in the conflict set C (the box of
+                              Algorithm 3; slots in C keep their candidates) */
+    DGS_REEVAL_ALL = 1     /* every slot (the text of Section 5 read as
+                              re-evaluating everything) */
+} dgs_reeval_rule;
 
 typedef struct {
     int32_t init;              /* a dgs_init_mode */
@@ -81,6 +94,8 @@ typedef struct {
      * CUDA events on the call's stream (dgs_stats.evaluation_ms, greedy_ms);
      * 0: no timing. */
     int32_t profile;
+    uint64_t seed;             /* DGS_INIT_RANDOM: generator start */
+    int32_t reeval_rule;       /* a dgs_reeval_rule (default DGS_REEVAL_BOX) */
 } dgs_options;
 
 typedef struct {
@@ -184,9 +199,10 @@ DGS_API dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* 
  *   ns[k]          1 <= ns[k] <= DGS_BATCH_MAX_N.
  *   sigma_outs[k]  DEVICE pointer to ns[k] int32 (agent -> job); host array.
  *   objectives_out HOST array of count int64.
- *   options        NULL or shared by all instances: init GREEDY or IDENTITY
- *                  (USER and traces are not supported: DGS_ERR_INVALID),
- *                  max_sweeps and deadline_us apply to each instance.
+ *   options        NULL or shared by all instances: init GREEDY, RANDOM
+ *                  (every instance from the same seed) or IDENTITY (USER and
+ *                  traces are not supported: DGS_ERR_INVALID); max_sweeps,
+ *                  deadline_us and reeval_rule apply to each instance.
  *   statuses_out   NULL or HOST array of count statuses (per instance).
  *   stats_out      NULL or HOST array of count dgs_stats.
  * Returns DGS_OK when every instance returned DGS_OK, else the status of the

@@ -26,8 +26,11 @@ DGS_ERR_BUSY = 7
 DGS_ERR_INTERNAL = 8
 
 DGS_INIT_GREEDY = 0
+DGS_INIT_RANDOM = 1
 DGS_INIT_IDENTITY = 2
 DGS_INIT_USER = 3
+DGS_REEVAL_BOX = 0
+DGS_REEVAL_ALL = 1
 
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
@@ -49,6 +52,8 @@ class dgs_options(ctypes.Structure):
         ("trace_applied", ctypes.c_void_p),
         ("trace_objective", ctypes.c_void_p),
         ("profile", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("reeval_rule", ctypes.c_int32),
     ]
 
 
@@ -195,9 +200,12 @@ def dgs_default_options() -> dgs_options:
     return o
 
 
-def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None, profile=0):
+def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None, profile=0, seed=0,
+             reeval=DGS_REEVAL_BOX):
     o = dgs_default_options()
     o.init = init
+    o.seed = int(seed)
+    o.reeval_rule = int(reeval)
     o.profile = int(profile)
     o.init_sigma = _dev(init_sigma, "init_sigma") if init_sigma is not None else None
     o.max_sweeps = max_sweeps
@@ -225,9 +233,10 @@ def dgs_solve(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stre
 def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, **opts):
     """dgs_solve_ex: returns (status, sigma_out, objective, stats dict).
 
-    Keyword options: init, init_sigma (int32 CUDA tensor), max_sweeps,
-    deadline_us, trace=(accepted int32, applied int32, objective int64) CUDA
-    tensors of equal length."""
+    Keyword options: init, init_sigma (int32 CUDA tensor), seed (random
+    start), reeval (DGS_REEVAL_BOX / DGS_REEVAL_ALL), max_sweeps, deadline_us,
+    trace=(accepted int32, applied int32, objective int64) CUDA tensors of
+    equal length."""
     n = _n(benefit)
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)

@@ -150,6 +150,24 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
 }  // namespace
 
 namespace dgs {
+// DGS_INIT_RANDOM: the identity shuffled by Fisher-Yates in Durstenfeld's
+// form (for i = n-1 .. 1, swap i with next() mod (i + 1)), next() being
+// splitmix64 (Steele, Lea, Flood 2014) started at seed.
+void random_start(int32_t n, uint64_t seed, int32_t* tau) {
+    uint64_t state = seed;
+    auto next = [&state]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int32_t i = 0; i < n; ++i) tau[i] = i;
+    for (int32_t i = n - 1; i > 0; --i) {
+        const int32_t j = (int32_t)(next() % (uint64_t)(i + 1));
+        std::swap(tau[i], tau[j]);
+    }
+}
+
 // Workspace of one batched or served instance inside a caller-provided block
 // (base == nullptr: only the size).  need_copy: w.a is a re-pitched copy in
 // the block (pitch round_up(n, 4)); otherwise the caller sets w.a.
@@ -263,6 +281,7 @@ struct Solve {
         h.greedy_remaining = w.n;
         h.update_policy = env_update_policy();
         if (o) {
+            h.reeval_all = o->reeval_rule == DGS_REEVAL_ALL ? 1 : 0;
             h.trace_capacity = o->trace_capacity > 0 ? o->trace_capacity : 0;
             h.trace_accepted = o->trace_accepted;
             h.trace_applied = o->trace_applied;
@@ -278,6 +297,25 @@ struct Solve {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "reading loop state");
         return DGS_OK;
+    }
+};
+
+// A stream-ordered device allocation released with the call.
+struct DeviceBuffer {
+    cudaStream_t s;
+    void* p = nullptr;
+    explicit DeviceBuffer(cudaStream_t st) : s(st) {}
+    ~DeviceBuffer() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    dgs_status alloc(size_t bytes) {
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            p = nullptr;
+            return DGS_ERR_OOM;
+        }
+        return e == cudaSuccess ? DGS_OK : cuda_fail(e, "cudaMallocAsync");
     }
 };
 
@@ -390,11 +428,26 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     dgs_options o;
     dgs_default_options(&o);
     if (opt) o = *opt;
-    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY && o.init != DGS_INIT_USER) return DGS_ERR_INVALID;
+    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_RANDOM && o.init != DGS_INIT_IDENTITY &&
+        o.init != DGS_INIT_USER)
+        return DGS_ERR_INVALID;
     if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
+    if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
 
     Solve S(stream);
     DGS_TRY(S.setup(benefit, n, true));
+    // the random start is drawn on the host and enters as the caller's start
+    DeviceBuffer rnd(stream);
+    if (o.init == DGS_INIT_RANDOM) {
+        std::vector<int32_t> perm(n);
+        random_start(n, o.seed, perm.data());
+        DGS_TRY(rnd.alloc((size_t)n * sizeof(int32_t)));
+        DGS_CUDA(cudaMemcpyAsync(rnd.p, perm.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
+                 "copy random start");
+        DGS_CUDA(cudaStreamSynchronize(stream), "copy random start");  // perm is released on return
+        o.init = DGS_INIT_USER;
+        o.init_sigma = static_cast<const int32_t*>(rnd.p);
+    }
     DGS_TRY(S.init_state(o.max_sweeps, &o));
     if (o.deadline_us > 0) {
         arm_deadline_kernel<<<1, 1, 0, stream>>>(S.w.st, o.deadline_us);

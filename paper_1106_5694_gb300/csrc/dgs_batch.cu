@@ -159,7 +159,8 @@ class Engine {
     // the init kernel re-pitches into the region, and a == null means the
     // region already holds the pitched matrix.
     void place(int32_t k, char* mem, int32_t n, bool with_copy, const int32_t* a, int32_t* sigma_out,
-               int32_t init_mode, int32_t max_sweeps, int64_t deadline_us) {
+               int32_t init_mode, int32_t max_sweeps, int64_t deadline_us, const int32_t* user_tau = nullptr,
+               bool reeval_all = false) {
         Instance in{};
         carve_instance(mem, n, with_copy, &in);
         if (!with_copy) in.w.a = a;
@@ -168,6 +169,8 @@ class Engine {
         in.fresh = 1;
         in.max_sweeps = max_sweeps;
         in.init_mode = init_mode;
+        in.user_tau = user_tau;
+        in.reeval_all = reeval_all ? 1 : 0;
         in.deadline_us = deadline_us;
         in.sigma_out = sigma_out;
         h_inst_[k] = in;
@@ -358,7 +361,8 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
     dgs_options o;
     dgs_default_options(&o);
     if (options) o = *options;
-    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY) return DGS_ERR_INVALID;
+    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY && o.init != DGS_INIT_RANDOM) return DGS_ERR_INVALID;
+    if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
     if (o.trace_capacity > 0) return DGS_ERR_INVALID;
     int32_t max_n = 0;
     for (int32_t k = 0; k < count; ++k) {
@@ -384,6 +388,21 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
         off[k] = total;
         total += carve_instance(nullptr, ns[k], copy[k] != 0, nullptr);
     }
+    // random starts (drawn on the host, one per instance from the same seed)
+    // follow the workspaces in the same allocation
+    std::vector<int32_t> starts;
+    std::vector<size_t> start_off(count, 0);
+    if (o.init == DGS_INIT_RANDOM) {
+        size_t sum = 0;
+        for (int32_t k = 0; k < count; ++k) {
+            start_off[k] = sum;
+            sum += (size_t)ns[k];
+        }
+        starts.resize(sum);
+        for (int32_t k = 0; k < count; ++k) random_start(ns[k], o.seed, starts.data() + start_off[k]);
+    }
+    const size_t ws_total = total;
+    total += starts.size() * sizeof(int32_t);
     char* mem = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), total, s);
     if (e == cudaErrorMemoryAllocation) {
@@ -397,9 +416,22 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
         cudaEventDestroy(ev);
         return fail(e, "cudaMallocAsync");
     }
-    for (int32_t k = 0; k < count; ++k)
-        eng.place(k, mem + off[k], ns[k], copy[k] != 0, benefits[k], sigma_outs[k], o.init, o.max_sweeps,
-                  o.deadline_us);
+    int32_t* d_starts = reinterpret_cast<int32_t*>(mem + ws_total);
+    if (!starts.empty()) {
+        e = cudaMemcpyAsync(d_starts, starts.data(), starts.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(mem, s);
+            cudaEventDestroy(ev);
+            return fail(e, "copy random starts");
+        }
+    }
+    for (int32_t k = 0; k < count; ++k) {
+        const bool rnd = o.init == DGS_INIT_RANDOM;
+        eng.place(k, mem + off[k], ns[k], copy[k] != 0, benefits[k], sigma_outs[k], rnd ? DGS_INIT_USER : o.init,
+                  o.max_sweeps, o.deadline_us, rnd ? d_starts + start_off[k] : nullptr,
+                  o.reeval_rule == DGS_REEVAL_ALL);
+    }
     const int64_t max_steps = max_steps_for(max_n);
     bool all_done = false;
     for (int64_t it = 0; it < max_steps && st == DGS_OK; ++it) {

@@ -54,6 +54,8 @@ struct DeviceState {
     long long greedy_rescans;  // rows of a / at rescanned by the greedy start
     uint32_t bar_count;      // grid barrier of cooperative launches: arrivals
     uint32_t bar_gen;        //   and generation
+    int32_t reeval_all;      // 1: every slot is re-evaluated after a switch (DGS_REEVAL_ALL)
+    int32_t pad_state;
     int32_t stage;           // kStage* (batched and served solves only)
     int32_t init_mode;       // batched: DGS_INIT_* of the instance (from Instance::init_mode)
     int64_t f;               // current objective
@@ -120,8 +122,8 @@ struct Instance {
     int32_t ctl_cap;           // entries of each controller list in shared memory
     int32_t fresh;             // 1: the next step initialises this instance
     int32_t max_sweeps;        // options of the instance
-    int32_t init_mode;         // DGS_INIT_GREEDY / _IDENTITY / _USER
-    int32_t pad_;
+    int32_t init_mode;         // DGS_INIT_GREEDY / _IDENTITY / _USER (a random start arrives as USER)
+    int32_t reeval_all;        // DGS_REEVAL_ALL
     int64_t deadline_us;
     const int32_t* a_src;      // caller's matrix when w.a is a re-pitched copy, else null
     const int32_t* user_tau;   // DGS_INIT_USER start
@@ -342,6 +344,8 @@ cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
 
 size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in);
+// The random start of DGS_INIT_RANDOM (splitmix64 + Fisher-Yates) on the host.
+void random_start(int32_t n, uint64_t seed, int32_t* tau);
 
 // Batched launches (one persistent grid each; every kernel acts only on the
 // table's instances that are in `stage`).  The tables are described at each

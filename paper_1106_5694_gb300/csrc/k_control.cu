@@ -554,7 +554,7 @@ __device__ __forceinline__ void prepare_edges_body(const Workspace& w, int32_t b
             key = w.key_a[w.tau[t]];
             ru = t;
             rv = key ? w.sigma[key_index(key)] : t;
-            in_c = w.in_ca[t];
+            in_c = w.in_ca[t] && !st->reeval_all;
             if (!in_c) {
                 w.ag_gain[t] = key ? key_gain(key) : 0;
                 w.ag_job[t] = key ? key_index(key) : -1;
@@ -566,7 +566,7 @@ __device__ __forceinline__ void prepare_edges_body(const Workspace& w, int32_t b
             key = w.key_j[j];
             ru = w.sigma[j];
             rv = key ? key_index(key) : ru;
-            in_c = w.in_cj[j];
+            in_c = w.in_cj[j] && !st->reeval_all;
             if (!in_c) {
                 w.jb_gain[j] = key ? key_gain(key) : 0;
                 w.jb_agent[j] = key ? key_index(key) : -1;
@@ -799,6 +799,7 @@ __global__ void init_batched_kernel(BatchTable t, int32_t update_policy) {
             h.update_policy = update_policy;
             h.stage = kStageNew;
             h.init_mode = in.init_mode;
+            h.reeval_all = in.reeval_all;
             if (in.deadline_us > 0) h.deadline_ns = globaltimer_ns() + (uint64_t)in.deadline_us * 1000ull;
             *w.st = h;
         }

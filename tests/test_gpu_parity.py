@@ -266,3 +266,54 @@ def test_internal_paths_agree_with_oracle(env):
         ref = oracle.dgs_parallel(a)
         assert st == B.DGS_OK and f == ref.objective and sweeps == ref.sweeps
         assert tau == ref.tau.tolist()
+
+
+# ------------------- the paper's random start and the re-evaluate-all rule
+RULE_CASES = [(k, n, s) for k in ("uniform", "peer", "geom", "ties") for n in (2, 9, 64, 129, 300) for s in (0, 1)]
+
+
+@pytest.mark.parametrize("kind,n,seed", RULE_CASES)
+def test_random_start_and_reeval_rules_match_oracle(kind, n, seed):
+    a = _make(kind, n, seed)
+    for init, reeval in ((oracle.INIT_RANDOM, oracle.REEVAL_BOX), (oracle.INIT_RANDOM, oracle.REEVAL_ALL),
+                         (oracle.INIT_GREEDY, oracle.REEVAL_ALL)):
+        ref = oracle.dgs_parallel(a, init=init, seed=1000 + seed, reeval=reeval, trace_cap=100000)
+        assert ref.status == oracle.OK
+        tr = _trace_tensors(max(ref.sweeps, 1))
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=init, seed=1000 + seed, reeval=reeval, trace=tr)
+        assert st == B.DGS_OK, B.dgs_status_string(st)
+        np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+        assert f == ref.objective and stats["sweeps"] == ref.sweeps and stats["swaps_applied"] == ref.swaps_applied
+        k = ref.sweeps
+        np.testing.assert_array_equal(tr[0][:k].cpu().numpy(), ref.trace_accepted)
+        np.testing.assert_array_equal(tr[1][:k].cpu().numpy(), ref.trace_applied)
+
+
+def test_hand_trace_reeval_all_on_gpu():
+    with open(GOLDEN) as fh:
+        t = {x["name"]: x for x in json.load(fh)["traces"]}["n3_identity_reeval_all"]
+    tr = _trace_tensors(4)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(np.array(t["a"], np.int32)), init=B.DGS_INIT_IDENTITY,
+                                       reeval=B.DGS_REEVAL_ALL, trace=tr)
+    assert st == B.DGS_OK
+    assert sig.cpu().tolist() == t["tau"] and f == t["objective"] and stats["sweeps"] == t["sweeps"]
+    assert tr[0][:1].cpu().tolist() == t["accepted"] and tr[1][:1].cpu().tolist() == t["applied"]
+
+
+def test_batched_random_start_and_reeval_all_match_oracle():
+    cases = [("geom", 150, 3), ("peer", 97, 5), ("uniform", 301, 6), ("ties", 64, 7), ("geom", 40, 8)]
+    mats = [_make(*c) for c in cases]
+    for reeval in (B.DGS_REEVAL_BOX, B.DGS_REEVAL_ALL):
+        st, sigs, objs, sts, stats = B.dgs_solve_batched([_cuda(a) for a in mats], init=B.DGS_INIT_RANDOM, seed=77,
+                                                         reeval=reeval)
+        assert st == B.DGS_OK, B.dgs_last_cuda_error()
+        for a, sig, f, s in zip(mats, sigs, objs, stats):
+            ref = oracle.dgs_parallel(a, init=oracle.INIT_RANDOM, seed=77, reeval=reeval)
+            np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+            assert f == ref.objective and s["sweeps"] == ref.sweeps
+
+
+def test_invalid_rule_and_start_rejected():
+    a = _cuda(_make("uniform", 20, 0))
+    assert B.dgs_solve_ex(a, reeval=7)[0] == B.DGS_ERR_INVALID
+    assert B.dgs_solve_ex(a, init=9)[0] == B.DGS_ERR_INVALID
