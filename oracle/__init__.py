@@ -94,6 +94,8 @@ def _load():
     lib.oracle_splitmix64_next.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.oracle_splitmix64_next.restype = ctypes.c_uint64
     lib.oracle_dgs_parallel.restype = ctypes.c_int
+    lib.oracle_dgs_sequential.argtypes = [P, i32, i32, P, ctypes.c_uint64, i32, P, P, P, i32, P, P, P, P, P, P]
+    lib.oracle_dgs_sequential.restype = ctypes.c_int
     lib.oracle_hungarian.argtypes = [P, i32, P]
     lib.oracle_hungarian.restype = i64
     lib.oracle_brute_force.argtypes = [P, i32, P]
@@ -214,6 +216,30 @@ def dgs_parallel(a, init: int = INIT_GREEDY, init_tau=None, max_sweeps: int = 0,
     k = min(st.sweeps, trace_cap)
     return SolveResult(status, tau[:n].copy(), f.value, st.sweeps, st.passes,
                        st.swaps_applied, st.evaluations, ta[:k].copy(), tp[:k].copy(), tf[:k].copy())
+
+
+def dgs_sequential(a, init: int = INIT_GREEDY, init_tau=None, max_iters: int = 0, seed: int = 0,
+                   trace_cap: int = 0) -> SolveResult:
+    """Algorithm 1 (sequential DGS) with readings R1, R2, R5, R6.  ``sweeps``
+    counts while-loop iterations; trace_applied holds 1 for each iteration
+    that committed its exchange (trace_accepted is all ones)."""
+    a = _c(a)
+    n = a.shape[0]
+    tau = np.zeros(max(n, 1), np.int32)
+    f = ctypes.c_int64()
+    st = _Stats()
+    tp = np.zeros(max(trace_cap, 1), np.int32)
+    tf = np.zeros(max(trace_cap, 1), np.int64)
+    extra = [np.zeros(max(trace_cap, 1), np.int32) for _ in range(4)]
+    it = _c(init_tau) if init_tau is not None else None
+    status = _load().oracle_dgs_sequential(_p(a), n, init, _p(it), ctypes.c_uint64(seed), max_iters, _p(tau),
+                                           ctypes.byref(f), ctypes.byref(st), trace_cap, _p(tp), _p(tf),
+                                           *[_p(x) for x in extra])
+    k = min(st.sweeps, trace_cap)
+    r = SolveResult(status, tau[:n].copy(), f.value, st.sweeps, st.passes, st.swaps_applied, st.evaluations,
+                    np.ones(k, np.int32), tp[:k].copy(), tf[:k].copy())
+    r.trace_slot, r.trace_target, r.trace_u, r.trace_v = (x[:k].copy() for x in extra)
+    return r
 
 
 def hungarian(a):

@@ -382,6 +382,119 @@ out:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Algorithm 1 (sequential DGS). */
+int oracle_dgs_sequential(const int32_t* a, int32_t n, int32_t init_mode,
+                          const int32_t* init_tau, uint64_t seed, int32_t max_iters,
+                          int32_t* tau_out, int64_t* f_out, oracle_stats* stats,
+                          int32_t trace_cap, int32_t* trace_applied, int64_t* trace_objective,
+                          int32_t* trace_slot, int32_t* trace_target, int32_t* trace_u, int32_t* trace_v)
+{
+    if (n <= 0 || a == NULL || tau_out == NULL || f_out == NULL) return ORACLE_ERR_INVALID;
+    if (n > (1 << 17)) return ORACLE_ERR_INVALID;
+    if (!oracle_range_ok(a, n)) return ORACLE_ERR_RANGE;
+
+    size_t nb = (size_t)n * sizeof(int32_t);
+    int32_t* sigma = (int32_t*)malloc(nb);
+    int32_t* tau = (int32_t*)malloc(nb);
+    int32_t* dbar = (int32_t*)malloc(nb);   /* delta-bar_i and its job j_i */
+    int32_t* jbar = (int32_t*)malloc(nb);
+    int32_t* dund = (int32_t*)malloc(nb);   /* delta-underbar_j and its agent i_j */
+    int32_t* iund = (int32_t*)malloc(nb);
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    oracle_stats st = {0, 0, 0, 0};
+    int status = ORACLE_OK;
+
+    /* Section 3.1: initial solution. */
+    if (init_mode == ORACLE_INIT_GREEDY) {
+        oracle_greedy_init(a, n, tau);
+    } else if (init_mode == ORACLE_INIT_IDENTITY) {
+        for (int32_t i = 0; i < n; ++i) tau[i] = i;
+    } else if (init_mode == ORACLE_INIT_RANDOM) {
+        oracle_random_permutation(n, seed, tau);
+    } else if (init_mode == ORACLE_INIT_USER && init_tau != NULL) {
+        for (int32_t i = 0; i < n; ++i) {
+            if (init_tau[i] < 0 || init_tau[i] >= n || seen[init_tau[i]]) {
+                status = ORACLE_ERR_INVALID;
+                goto out;
+            }
+            seen[init_tau[i]] = 1;
+            tau[i] = init_tau[i];
+        }
+    } else {
+        status = ORACLE_ERR_INVALID;
+        goto out;
+    }
+    for (int32_t i = 0; i < n; ++i) sigma[tau[i]] = i;
+    int64_t f = oracle_objective(a, n, tau);
+
+    for (;;) { /* repeat ... until f(sigma_start) = f(sigma') (R5) */
+        st.passes++;
+        int64_t f_start = f;
+        for (int32_t i = 0; i < n; ++i) oracle_ade(a, n, sigma, tau, i, &dbar[i], &jbar[i]);
+        for (int32_t j = 0; j < n; ++j) oracle_jde(a, n, sigma, tau, j, &dund[j], &iund[j]);
+        st.evaluations += 2 * (int64_t)n;
+        for (;;) { /* switching phase: while some delta > 0 */
+            int32_t is = 0, js = 0;
+            for (int32_t i = 1; i < n; ++i) if (dbar[i] > dbar[is]) is = i;
+            for (int32_t j = 1; j < n; ++j) if (dund[j] > dund[js]) js = j;
+            if (dbar[is] <= 0 && dund[js] <= 0) break;
+            if (max_iters > 0 && st.sweeps >= max_iters) {
+                status = ORACLE_TIMEOUT;
+                goto finish;
+            }
+            int32_t u, v; /* agent u takes the target job, v is the current holder */
+            int32_t slot, target;
+            if (dbar[is] > dund[js]) {
+                dbar[is] = 0;
+                slot = is;
+                target = jbar[is];
+                u = is;
+                v = sigma[jbar[is]];
+            } else {
+                dund[js] = 0;
+                slot = n + js;
+                target = iund[js];
+                u = iund[js];
+                v = sigma[js];
+            }
+            int64_t g = exchange_gain(a, n, tau, u, v);
+            int applied = 0;
+            if (g > 0) {
+                do_exchange(sigma, tau, u, v);
+                f += g;
+                applied = 1;
+                st.swaps_applied++;
+                /* the agents and jobs of the exchange: ADE and JDE again */
+                oracle_ade(a, n, sigma, tau, u, &dbar[u], &jbar[u]);
+                oracle_ade(a, n, sigma, tau, v, &dbar[v], &jbar[v]);
+                oracle_jde(a, n, sigma, tau, tau[u], &dund[tau[u]], &iund[tau[u]]);
+                oracle_jde(a, n, sigma, tau, tau[v], &dund[tau[v]], &iund[tau[v]]);
+                st.evaluations += 4;
+            }
+            if (st.sweeps < trace_cap) {
+                if (trace_applied) trace_applied[st.sweeps] = applied;
+                if (trace_objective) trace_objective[st.sweeps] = f;
+                if (trace_slot) trace_slot[st.sweeps] = slot;
+                if (trace_target) trace_target[st.sweeps] = target;
+                if (trace_u) trace_u[st.sweeps] = u;
+                if (trace_v) trace_v[st.sweeps] = v;
+            }
+            st.sweeps++;
+        }
+        if (f == f_start) break;
+    }
+
+finish:
+    memcpy(tau_out, tau, nb);
+    *f_out = oracle_objective(a, n, tau);
+    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;
+out:
+    if (stats) *stats = st;
+    free(sigma); free(tau); free(dbar); free(jbar); free(dund); free(iund); free(seen);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact optimum, Hungarian method (Kuhn 1955) in its shortest augmenting
  * path form: rows are inserted one at a time; a Dijkstra-like scan over
  * reduced costs c[i][j] - u[i] - v[j] (c = -a, minimised) finds the

@@ -115,6 +115,27 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
                         int32_t* trace_accepted, int32_t* trace_applied,
                         int64_t* trace_objective);
 
+/* Algorithm 1 (sequential DGS, Section 3.3): after a full difference
+ * evaluation, repeatedly take the agent slot with the largest delta-bar and
+ * the job slot with the largest delta-underbar (ties: lowest index), keep the
+ * agent's candidate if its delta is strictly larger, else the job's; zero
+ * that delta; apply the exchange (partner looked up in the current sigma) if
+ * it raises f, then re-run ADE for the two agents and JDE for the two jobs it
+ * touched (reading R6).  The while loop ends when no delta is positive; the
+ * outer repeat (reading R5) re-evaluates everything and runs again until a
+ * pass leaves f unchanged.  init_mode / init_tau / seed as for
+ * oracle_dgs_parallel; max_iters caps while-loop iterations (<= 0: none).
+ * stats->sweeps counts while-loop iterations; trace arrays (may be NULL)
+ * receive for iteration s < trace_cap 1/0 for a committed exchange, f, the
+ * chosen slot (agent i as i, job j as n + j), its target (job j_i or agent
+ * i_j) and the two agents of the exchange examined (u takes the target job,
+ * v is that job's holder in the current sigma). */
+int oracle_dgs_sequential(const int32_t* a, int32_t n, int32_t init_mode,
+                          const int32_t* init_tau, uint64_t seed, int32_t max_iters,
+                          int32_t* tau_out, int64_t* f_out, oracle_stats* stats,
+                          int32_t trace_cap, int32_t* trace_applied, int64_t* trace_objective,
+                          int32_t* trace_slot, int32_t* trace_target, int32_t* trace_u, int32_t* trace_v);
+
 /* Exact LSAP maximum by the Hungarian method (Kuhn 1955, in the
  * shortest-augmenting-path form with dual potentials).  O(n^3). */
 int64_t oracle_hungarian(const int32_t* a, int32_t n, int32_t* tau_out);

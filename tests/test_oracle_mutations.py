@@ -30,6 +30,10 @@ MUTATIONS = {
     "greedy_tie_job_first": ("((uint64_t)i << 17) | (uint64_t)j;", "((uint64_t)j << 17) | (uint64_t)i;"),
     "hungarian_sign": ("-A(row - 1, c - 1) - u[row] - v[c]", "-A(row - 1, c - 1) - u[row] + v[c]"),
     "objective_sign": ("f += A(i, tau[i]);", "f -= A(i, tau[i]);"),
+    "sequential_ties_to_agent": ("if (dbar[is] > dund[js]) {", "if (dbar[is] >= dund[js]) {"),
+    "sequential_no_outer_repeat": ("        if (f == f_start) break;\n    }\n\nfinish:\n    memcpy(tau_out, tau, nb);\n    *f_out = oracle_objective(a, n, tau);\n    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;\nout:\n    if (stats) *stats = st;\n    free(sigma); free(tau); free(dbar);",
+                                   "        break;\n    }\n\nfinish:\n    memcpy(tau_out, tau, nb);\n    *f_out = oracle_objective(a, n, tau);\n    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;\nout:\n    if (stats) *stats = st;\n    free(sigma); free(tau); free(dbar);"),
+    "sequential_stale_partner": ("                u = is;\n                v = sigma[jbar[is]];", "                u = is;\n                v = jbar[is];"),
 }
 
 

@@ -407,3 +407,70 @@ def test_reeval_all_invariants(kind, n, seed):
         else:
             f0 = _full_objective(a, oracle.random_permutation(n, seed))
         assert np.all(np.diff(np.concatenate([[f0], r.trace_objective])) > 0)
+
+
+# ------------------------------------------------- Algorithm 1 (sequential DGS)
+def test_hand_trace_sequential():
+    t = _traces()["n3_identity_sequential"]
+    r = oracle.dgs_sequential(np.array(t["a"], np.int32), init=oracle.INIT_IDENTITY, trace_cap=16)
+    assert r.status == oracle.OK
+    assert r.tau.tolist() == t["tau"] and r.objective == t["objective"]
+    assert r.sweeps == t["sweeps"] and r.passes == t["passes"]
+    assert r.trace_applied.tolist() == t["applied"] and r.trace_objective.tolist() == t["trace_objective"]
+    assert r.trace_slot.tolist() == t["slots"] and r.trace_target.tolist() == t["targets"]
+    assert [[int(u), int(v)] for u, v in zip(r.trace_u, r.trace_v)] == t["exchanges"]
+
+
+@pytest.mark.parametrize("kind,n,seed", CASES)
+def test_sequential_invariants(kind, n, seed):
+    """Algorithm 1 ends at a 2-exchange local optimum (its last pass found no
+    positive fresh delta), below the optimum, with f non-decreasing and each
+    committed exchange strictly raising f."""
+    a = _make(kind, n, seed)
+    for init in (oracle.INIT_GREEDY, oracle.INIT_RANDOM):
+        r = oracle.dgs_sequential(a, init=init, seed=seed, trace_cap=1 << 20)
+        assert r.status == oracle.OK
+        assert sorted(r.tau.tolist()) == list(range(n))
+        assert r.objective == _full_objective(a, r.tau)
+        assert _no_improving_exchange(a, r.tau)
+        opt = oracle.brute_force(a)[0] if n <= 9 else oracle.hungarian(a)[0]
+        assert r.objective <= opt
+        f0 = _full_objective(a, oracle.greedy_init(a) if init == oracle.INIT_GREEDY
+                             else oracle.random_permutation(n, seed))
+        steps = np.diff(np.concatenate([[f0], r.trace_objective]))
+        assert np.all(steps >= 0) and np.all((steps > 0) == (r.trace_applied == 1))
+        assert r.swaps_applied == int(r.trace_applied.sum())
+
+
+def test_sequential_single_exchange_instance():
+    """n = 2 anti-diagonal from the identity: one exchange (gain 10) and a
+    confirming pass."""
+    r = oracle.dgs_sequential(np.array([[0, 5], [5, 0]], np.int32), init=oracle.INIT_IDENTITY, trace_cap=8)
+    assert r.tau.tolist() == [1, 0] and r.objective == 10 and r.swaps_applied == 1 and r.passes == 2
+
+
+@pytest.mark.parametrize("kind,n,seed", CASES[::2])
+def test_sequential_exchanges_follow_switch_definition(kind, n, seed):
+    """switch(i, j, sigma) gives agent i job j: a 2-exchange between agents i
+    and sigma(j) in the CURRENT assignment (Section 3.3).  Replaying the
+    committed exchanges from the start, every examined exchange must be that
+    one for its slot: agent slot i with target j -> (i, sigma(j)); job slot j
+    with target agent i -> (i, sigma(j)); committed iff it raises f."""
+    a = _make(kind, n, seed)
+    r = oracle.dgs_sequential(a, init=oracle.INIT_RANDOM, seed=seed, trace_cap=1 << 20)
+    assert r.status == oracle.OK
+    tau = oracle.random_permutation(n, seed).astype(np.int64)
+    a64 = a.astype(np.int64)
+    for s in range(r.sweeps):
+        sigma = np.empty(n, np.int64)
+        sigma[tau] = np.arange(n)
+        slot, target, u, v = int(r.trace_slot[s]), int(r.trace_target[s]), int(r.trace_u[s]), int(r.trace_v[s])
+        if slot < n:
+            assert u == slot and v == sigma[target]
+        else:
+            assert u == target and v == sigma[slot - n]
+        gain = a64[u, tau[v]] + a64[v, tau[u]] - a64[u, tau[u]] - a64[v, tau[v]]
+        assert (gain > 0) == (r.trace_applied[s] == 1)
+        if gain > 0:
+            tau[u], tau[v] = tau[v], tau[u]
+    assert tau.tolist() == r.tau.tolist()
