@@ -353,6 +353,22 @@ def run_ours(args):
                           f"same instance; ms/solve = t_greedy + (1 + {stats['sweeps']} sweeps) x t_eval")}
 
     extra = {}
+    # Algorithm 1 (sequential DGS) on the same instance, for comparison
+    try:
+        B.dgs_solve_ex(at, sigma_out=sig, algorithm=B.DGS_ALG_SEQUENTIAL)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        st_s, _, f_s, stats_s = B.dgs_solve_ex(at, sigma_out=sig, algorithm=B.DGS_ALG_SEQUENTIAL)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        extra["sequential"] = {
+            "algorithm": "Algorithm 1 (one switch per iteration), same start and instance",
+            "status": B.dgs_status_string(st_s) + ("" if st_s == B.DGS_OK else f" ({B.dgs_last_cuda_error()})"),
+            "ms": round(e0.elapsed_time(e1), 3), "objective": f_s,
+            "iterations": stats_s["sweeps"], "swaps_applied": stats_s["swaps_applied"],
+            "parallel_objective": f, "parallel_ms": round(ms_per_step, 3)}
+    except Exception as exc:
+        extra["sequential"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batched:
         for key, fn in (("batched", run_batched), ("serving", run_serving)):
             try:

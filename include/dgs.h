@@ -70,6 +70,19 @@ typedef enum {
     DGS_INIT_USER = 3      /* caller's permutation in dgs_options.init_sigma */
 } dgs_init_mode;
 
+/* Which algorithm runs after the start. */
+typedef enum {
+    DGS_ALG_PARALLEL = 0,   /* Algorithm 3, parallel DGS (Section 5, default) */
+    DGS_ALG_SEQUENTIAL = 1  /* Algorithm 1, sequential DGS (Section 3.3): one
+                               switch per iteration, the largest delta over all
+                               agent and job slots (ties: lowest index; the
+                               agent slot only when strictly larger), ADE/JDE
+                               of the two agents and jobs after a commit, the
+                               outer repeat until a pass leaves f unchanged.
+                               dgs_stats.sweeps counts while-loop iterations,
+                               max_sweeps caps them. */
+} dgs_algorithm;
+
 /* Which slots are re-evaluated after each parallel switch of Algorithm 3. */
 typedef enum {
     DGS_REEVAL_BOX = 0,    /* the slots not in the conflict set C (the box of
@@ -96,6 +109,9 @@ typedef struct {
     int32_t profile;
     uint64_t seed;             /* DGS_INIT_RANDOM: generator start */
     int32_t reeval_rule;       /* a dgs_reeval_rule (default DGS_REEVAL_BOX) */
+    int32_t algorithm;         /* a dgs_algorithm (default DGS_ALG_PARALLEL);
+                                  dgs_solve_batched and the server take
+                                  DGS_ALG_PARALLEL only */
 } dgs_options;
 
 typedef struct {

@@ -31,6 +31,8 @@ DGS_INIT_IDENTITY = 2
 DGS_INIT_USER = 3
 DGS_REEVAL_BOX = 0
 DGS_REEVAL_ALL = 1
+DGS_ALG_PARALLEL = 0
+DGS_ALG_SEQUENTIAL = 1
 
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
@@ -54,6 +56,7 @@ class dgs_options(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("reeval_rule", ctypes.c_int32),
+        ("algorithm", ctypes.c_int32),
     ]
 
 
@@ -201,8 +204,9 @@ def dgs_default_options() -> dgs_options:
 
 
 def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None, profile=0, seed=0,
-             reeval=DGS_REEVAL_BOX):
+             reeval=DGS_REEVAL_BOX, algorithm=DGS_ALG_PARALLEL):
     o = dgs_default_options()
+    o.algorithm = int(algorithm)
     o.init = init
     o.seed = int(seed)
     o.reeval_rule = int(reeval)

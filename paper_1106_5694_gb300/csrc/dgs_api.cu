@@ -416,6 +416,57 @@ dgs_status run_greedy(Solve& S, EventPair* timer) {
     return DGS_ERR_INTERNAL;
 }
 
+// Algorithm 1 after the start: passes of (fresh evaluation of every slot,
+// switching loop on one CTA) until a pass leaves f unchanged.
+dgs_status run_sequential(Solve& S, int32_t* sigma_out, int64_t* objective_out, const dgs_options& o,
+                          dgs_stats* stats, EventPair& gev) {
+    cudaStream_t stream = S.s;
+    S.launches += 2;
+    DeviceState h;
+    const int64_t max_passes = 4 * (int64_t)S.w.n + 16;
+    bool ended = false;
+    for (int64_t pass = 0; pass < max_passes && !ended; ++pass) {
+        DGS_TRY(S.read_state(&h));
+        if (h.status != kRunning) break;
+        const int64_t f_start = h.f;
+        DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
+        DGS_CUDA(launch_slots_from_keys(S.w, stream), "slots");
+        S.launches += 2;
+        for (int64_t launch = 0;; ++launch) {
+            DGS_CUDA(launch_sequential(S.w, stream), "switching loop");
+            S.launches += 1;
+            DGS_TRY(S.read_state(&h));
+            if (h.status != kRunning || !h.need_update) break;
+            if (launch > 64) {
+                snprintf(g_last_error, sizeof(g_last_error), "switching loop did not finish");
+                return DGS_ERR_INTERNAL;
+            }
+        }
+        if (h.status != kRunning || h.f == f_start) ended = true;
+    }
+    if (!ended) {
+        snprintf(g_last_error, sizeof(g_last_error), "sequential passes did not finish");
+        return DGS_ERR_INTERNAL;
+    }
+    DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
+    S.launches += 1;
+    DGS_TRY(S.read_state(&h));
+    const dgs_status status = h.status == kRunning ? DGS_OK : map_device_status(h);
+    *objective_out = h.f;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->sweeps = h.sweeps;
+        stats->events = h.events;
+        stats->swaps_applied = h.swaps;
+        stats->greedy_rounds = h.greedy_rounds;
+        stats->initial_objective = h.f_initial;
+        stats->kernel_launches = S.launches;
+        stats->greedy_ms = (o.profile && o.init == DGS_INIT_GREEDY) ? gev.elapsed_ms() : 0.0;
+        stats->greedy_rescans = h.greedy_rescans;
+    }
+    return status;
+}
+
 dgs_status check_common(const int32_t* benefit, int32_t n) {
     if (benefit == nullptr || n <= 0 || n > kMaxN) return DGS_ERR_INVALID;
     return DGS_OK;
@@ -433,6 +484,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         return DGS_ERR_INVALID;
     if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
     if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
+    if (o.algorithm != DGS_ALG_PARALLEL && o.algorithm != DGS_ALG_SEQUENTIAL) return DGS_ERR_INVALID;
 
     Solve S(stream);
     DGS_TRY(S.setup(benefit, n, true));
@@ -463,6 +515,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     }
     DGS_CUDA(launch_start_from_tau(S.w, o.init_sigma, o.init, S.seen, stream), "start");
     record_initial_objective_kernel<<<1, 1, 0, stream>>>(S.w.st);
+    if (o.algorithm == DGS_ALG_SEQUENTIAL) return run_sequential(S, sigma_out, objective_out, o, stats, gev);
     EventPair ev;
     if (o.profile) DGS_TRY(ev.begin(stream));
     DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");

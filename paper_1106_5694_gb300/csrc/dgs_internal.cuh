@@ -342,6 +342,11 @@ cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s);
 cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
+// Algorithm 1: slots of a fresh evaluation (from the keys, which it clears),
+// and one launch of the single-CTA switching loop (need_update = 1 when the
+// launch stopped at its iteration budget before the loop ended).
+cudaError_t launch_slots_from_keys(const Workspace& w, cudaStream_t s);
+cudaError_t launch_sequential(const Workspace& w, cudaStream_t s);
 
 size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in);
 // The random start of DGS_INIT_RANDOM (splitmix64 + Fisher-Yates) on the host.
@@ -374,11 +379,11 @@ cudaError_t launch_b_advance(const BatchTable& one, int32_t from_stage, cudaStre
 // Raise a kernel's dynamic shared memory limit once per device (slot = one
 // small integer per kernel).
 inline cudaError_t ensure_smem_limit(const void* func, int slot, size_t bytes) {
-    static int done[8][64] = {};
+    static int done[16][64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 8) return cudaErrorInvalidValue;
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 16) return cudaErrorInvalidValue;
     if (done[slot][dev] >= (int)bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) done[slot][dev] = (int)bytes;

@@ -317,3 +317,43 @@ def test_invalid_rule_and_start_rejected():
     a = _cuda(_make("uniform", 20, 0))
     assert B.dgs_solve_ex(a, reeval=7)[0] == B.DGS_ERR_INVALID
     assert B.dgs_solve_ex(a, init=9)[0] == B.DGS_ERR_INVALID
+
+
+# --------------------------------------------- Algorithm 1 (sequential DGS)
+SEQ_CASES = [(k, n, s) for k in ("uniform", "peer", "ties", "geom", "wide") for n in (2, 3, 9, 64, 130, 257) for s in (0, 1)] + \
+            [("peer", 1000, 2), ("uniform", 700, 3), ("peer", 6500, 4)]
+
+
+@pytest.mark.parametrize("kind,n,seed", SEQ_CASES)
+def test_sequential_matches_oracle(kind, n, seed):
+    a = _make(kind, n, seed)
+    for init in (oracle.INIT_GREEDY, oracle.INIT_RANDOM):
+        ref = oracle.dgs_sequential(a, init=init, seed=seed, trace_cap=1 << 20)
+        assert ref.status == oracle.OK
+        tr = _trace_tensors(max(ref.sweeps, 1))
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=init, seed=seed, algorithm=B.DGS_ALG_SEQUENTIAL, trace=tr)
+        assert st == B.DGS_OK, (B.dgs_status_string(st), B.dgs_last_cuda_error())
+        np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+        assert f == ref.objective and stats["sweeps"] == ref.sweeps and stats["swaps_applied"] == ref.swaps_applied
+        k = ref.sweeps
+        np.testing.assert_array_equal(tr[1][:k].cpu().numpy(), ref.trace_applied)
+        np.testing.assert_array_equal(tr[2][:k].cpu().numpy(), ref.trace_objective)
+
+
+def test_sequential_hand_trace_and_cap_on_gpu():
+    with open(GOLDEN) as fh:
+        t = {x["name"]: x for x in json.load(fh)["traces"]}["n3_identity_sequential"]
+    a = np.array(t["a"], np.int32)
+    tr = _trace_tensors(8)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_IDENTITY, algorithm=B.DGS_ALG_SEQUENTIAL, trace=tr)
+    assert st == B.DGS_OK
+    assert sig.cpu().tolist() == t["tau"] and f == t["objective"] and stats["sweeps"] == t["sweeps"]
+    assert tr[1][:3].cpu().tolist() == t["applied"]
+    big = _make("peer", 300, 4)
+    for cap in (1, 5, 40):
+        ref = oracle.dgs_sequential(big, max_iters=cap)
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(big), max_sweeps=cap, algorithm=B.DGS_ALG_SEQUENTIAL)
+        assert st == (B.DGS_TIMEOUT if ref.status == oracle.TIMEOUT else B.DGS_OK)
+        np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+        assert f == ref.objective and stats["sweeps"] == ref.sweeps
+    assert B.dgs_solve_batched([_cuda(big)], algorithm=B.DGS_ALG_SEQUENTIAL)[0] == B.DGS_ERR_INVALID
