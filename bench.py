@@ -540,6 +540,7 @@ def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
                   "p99_ms": pct(lat_plain, 99), "capacity_solves_per_s": round(capacity, 2),
                   "how": "FIFO queue over the same arrivals, service = measured dgs_solve_host per request"},
         "steps": info["steps"], "gpu_launches": info["kernel_launches"],
+        "server_upload_ms": round(info["upload_ms"], 1), "server_step_ms": round(info["step_ms"], 1),
         "parity": "every objective equal to the plain solve of the same request" if ok else "MISMATCH",
     }
 

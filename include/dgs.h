@@ -236,10 +236,12 @@ DGS_API dgs_status dgs_solve_batched(const int32_t* const* benefits, const int32
  * peer-assignment node (Section 1).  A server owns one worker thread and a
  * device-memory budget on the device that is current when it is created.
  * Requests are admitted in arrival order as soon as their workspace fits in
- * the budget (continuous batching): admitted instances join the running
- * batch at the next step, keep their matrix and loop state resident on the
- * device until they finish, and overlap on the GPU with every other resident
- * instance.  Results are bit-identical to dgs_solve of the instance alone.
+ * the budget (continuous batching): the server's upload thread copies an
+ * admitted request's matrix to the device while the resident instances keep
+ * stepping; the instance then joins the running batch at the next step,
+ * keeps its matrix and loop state resident on the device until it finishes,
+ * and overlaps on the GPU with every other resident instance.  Results are
+ * bit-identical to dgs_solve of the instance alone.
  *
  * dgs_server_create: budget_bytes > 0; max_resident = cap on instances
  *   resident at once (<= 0: 256).  *out receives the server.
@@ -272,6 +274,8 @@ typedef struct {
     int64_t completed;       /* requests finished so far */
     size_t bytes_in_use;     /* budget taken by resident instances */
     int64_t kernel_launches; /* kernels launched by all steps so far */
+    double upload_ms;        /* time the upload thread spent copying matrices */
+    double step_ms;          /* time the worker spent in steps (graph replays) */
 } dgs_server_info;
 DGS_API dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_server** out);
 DGS_API size_t dgs_server_request_bytes(int32_t n);

@@ -92,6 +92,8 @@ class dgs_server_info(ctypes.Structure):
         ("completed", ctypes.c_int64),
         ("bytes_in_use", ctypes.c_size_t),
         ("kernel_launches", ctypes.c_int64),
+        ("upload_ms", ctypes.c_double),
+        ("step_ms", ctypes.c_double),
     ]
 
 
@@ -373,7 +375,7 @@ class Server:
     def dgs_server_get_info(self):
         info = dgs_server_info()
         st = load().dgs_server_get_info(self._h, ctypes.byref(info))
-        return st, {name: int(getattr(info, name)) for name, _ in info._fields_}
+        return st, {name: (float if name.endswith("_ms") else int)(getattr(info, name)) for name, _ in info._fields_}
 
     def dgs_server_destroy(self):
         if self._h:

@@ -469,6 +469,10 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
 }
 
 // ------------------------------------------------------------------- server
+// Two host threads: the worker admits requests by budget, places uploaded
+// instances into free slots at step boundaries, runs steps and retires
+// finished instances; the uploader copies admitted requests' matrices into
+// their device memory on its own stream, so copies overlap the steps.
 struct dgs_server {
     struct Request {
         uint64_t ticket;
@@ -477,6 +481,11 @@ struct dgs_server {
         int32_t flags;
         size_t bytes;
         int64_t submit_ns;
+    };
+    struct Uploaded {
+        Request r;
+        char* mem;
+        int64_t admit_ns;
     };
     struct Resident {
         uint64_t ticket = 0;
@@ -496,32 +505,32 @@ struct dgs_server {
 
     int device = 0;
     size_t budget = 0;
-    size_t used = 0;  // guarded by mu
     Engine eng;
-    std::vector<Resident> slots;
-    std::thread worker;
+    std::vector<Resident> slots;  // worker only
+    std::thread worker, uploader;
+    cudaStream_t up_stream = nullptr;
+    // everything below is guarded by mu
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request> queue;
+    std::condition_variable cv_work, cv_up, cv_done;
+    std::deque<Request> queue;       // waiting for admission
+    std::deque<Request> to_upload;   // admitted, matrix not yet on the device
+    std::deque<Uploaded> ready;      // on the device, waiting for a slot
     std::unordered_map<uint64_t, Result> results;
-    std::unordered_map<uint64_t, int32_t> pending;  // ticket -> 0 queued / 1 resident
+    std::unordered_map<uint64_t, int32_t> pending;  // ticket -> 0 queued / 1 admitted
+    size_t used = 0;                 // budget taken by admitted requests
+    int32_t resident_count = 0;      // instances in slots
+    int32_t reserved = 0;            // admitted, not yet in a slot
     uint64_t next_ticket = 1;
     bool stop = false;
     dgs_status fatal = DGS_OK;
-    int64_t completed = 0;
-    int32_t resident_count = 0;  // guarded by mu (the worker alone changes it)
-    int64_t steps = 0, launches = 0;  // guarded by mu
-
-    int32_t eng_resident() {
-        std::lock_guard<std::mutex> lk(mu);
-        return resident_count;
-    }
-    int32_t* h_sigma = nullptr;  // pinned staging for results
+    int64_t completed = 0, steps = 0, launches = 0;
+    double upload_ms = 0.0, step_ms = 0.0;
+    int32_t* h_sigma = nullptr;      // pinned staging for results (worker only)
     size_t h_sigma_cap = 0;
 
     explicit dgs_server(int32_t cap) : eng(cap, DGS_BATCH_MAX_N), slots(cap) {}
 
-    void finish_all_pending(dgs_status why) {
+    void finish_all_pending(dgs_status why) {  // caller holds mu
         for (auto& kv : pending) {
             Result r{};
             r.status = why;
@@ -529,37 +538,108 @@ struct dgs_server {
         }
         pending.clear();
         queue.clear();
+        to_upload.clear();
+    }
+
+    void record_result(uint64_t ticket, Result&& res, size_t bytes) {  // caller holds mu
+        used -= bytes;
+        pending.erase(ticket);
+        results[ticket] = std::move(res);
+        ++completed;
+    }
+
+    void run_uploader() {
+        cudaSetDevice(device);
+        for (;;) {
+            Request r;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_up.wait(lk, [&] { return stop || !to_upload.empty(); });
+                if (to_upload.empty()) return;  // stopping
+                r = to_upload.front();
+                to_upload.pop_front();
+            }
+            const int64_t t0 = now_ns();
+            char* mem = nullptr;
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), r.bytes, up_stream);
+            if (e == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
+                cudaGetLastError();
+                Result res{};
+                res.status = DGS_ERR_OOM;
+                res.times.submit_ns = r.submit_ns;
+                res.times.admit_ns = res.times.done_ns = now_ns();
+                std::lock_guard<std::mutex> lk(mu);
+                --reserved;
+                record_result(r.ticket, std::move(res), r.bytes);
+                cv_done.notify_all();
+                cv_work.notify_one();
+                continue;
+            }
+            if (e == cudaSuccess) {
+                // the matrix, pitched (round_up(n, 4)) at the start of its workspace
+                Instance probe{};
+                carve_instance(mem, r.n, true, &probe);
+                const size_t lda = (size_t)probe.w.lda;
+                int32_t* a_dev = const_cast<int32_t*>(probe.w.a);
+                if (lda != (size_t)r.n) e = cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, up_stream);
+                const cudaMemcpyKind kind =
+                    (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, up_stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(up_stream);
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            upload_ms += (now_ns() - t0) * 1e-6;
+            if (e != cudaSuccess) {
+                fail(e, "request upload");
+                fatal = DGS_ERR_CUDA;
+                finish_all_pending(DGS_ERR_CUDA);
+                stop = true;
+                cv_done.notify_all();
+                cv_work.notify_one();
+                return;
+            }
+            ready.push_back(Uploaded{r, mem, t0});
+            cv_work.notify_one();
+        }
     }
 
     void run() {
         cudaSetDevice(device);
         for (;;) {
-            std::vector<Request> admit;
+            std::vector<Uploaded> place_now;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                if (resident_count == 0) {
-                    cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-                    if (stop && resident_count == 0) break;
+                // admission in arrival order while the budget and a slot allow
+                while (!stop && !queue.empty() && resident_count + reserved < eng.capacity() &&
+                       used + queue.front().bytes <= budget) {
+                    const Request r = queue.front();
+                    queue.pop_front();
+                    used += r.bytes;
+                    ++reserved;
+                    pending[r.ticket] = 1;
+                    to_upload.push_back(r);
+                    cv_up.notify_one();
                 }
-                if (!stop) {
-                    int32_t free_slots = eng.capacity() - resident_count;
-                    while (!queue.empty() && free_slots > 0 && used + queue.front().bytes <= budget) {
-                        admit.push_back(queue.front());
-                        used += queue.front().bytes;
-                        pending[queue.front().ticket] = 1;
-                        queue.pop_front();
-                        --free_slots;
-                    }
+                if (resident_count == 0 && ready.empty()) {
+                    if (stop && reserved == 0) break;
+                    cv_work.wait(lk, [&] {
+                        return !ready.empty() || (stop && reserved == 0) ||
+                               (!stop && !queue.empty() && resident_count + reserved < eng.capacity() &&
+                                used + queue.front().bytes <= budget);
+                    });
+                    continue;
                 }
+                for (Uploaded& u : ready) place_now.push_back(u);
+                ready.clear();
             }
             dgs_status st = DGS_OK;
-            for (const Request& r : admit) {
-                st = admit_one(r);
-                if (st != DGS_OK) break;
-            }
-            if (st == DGS_OK && eng_resident() > 0) {
+            for (const Uploaded& u : place_now) place(u);
+            if (resident_now() > 0) {
+                const int64_t t0 = now_ns();
                 st = eng.step();
                 std::lock_guard<std::mutex> lk(mu);
+                step_ms += (now_ns() - t0) * 1e-6;
                 steps = eng.steps();
                 launches = eng.launches_per_step() * steps;
             }
@@ -570,54 +650,45 @@ struct dgs_server {
                 finish_all_pending(st);
                 stop = true;
                 cv_done.notify_all();
+                cv_up.notify_all();
                 break;
             }
-            std::lock_guard<std::mutex> lk(mu);
-            if (stop && resident_count == 0) break;
         }
     }
 
-    dgs_status admit_one(const Request& r) {
-        cudaStream_t s = eng.stream();
+    int32_t resident_now() {
+        std::lock_guard<std::mutex> lk(mu);
+        return resident_count;
+    }
+
+    void place(const Uploaded& u) {
+        bool drop;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            drop = stop;
+            --reserved;
+            if (drop) {
+                used -= u.r.bytes;
+                pending.erase(u.r.ticket);
+            } else {
+                ++resident_count;
+            }
+        }
+        if (drop) {  // the server is being destroyed: the request is dropped
+            cudaFreeAsync(u.mem, eng.stream());
+            return;
+        }
         const int32_t k = eng.free_slot();
-        if (k < 0) return DGS_ERR_INTERNAL;
         Resident& R = slots[k];
         R = Resident{};
-        R.ticket = r.ticket;
-        R.n = r.n;
-        R.bytes = r.bytes;
-        R.submit_ns = r.submit_ns;
-        R.admit_ns = now_ns();
-        const cudaError_t ea = cudaMallocAsync(reinterpret_cast<void**>(&R.mem), r.bytes, s);
-        if (ea == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
-            cudaGetLastError();
-            Result res{};
-            res.status = DGS_ERR_OOM;
-            res.times.submit_ns = r.submit_ns;
-            res.times.admit_ns = res.times.done_ns = now_ns();
-            std::lock_guard<std::mutex> lk(mu);
-            used -= r.bytes;
-            pending.erase(r.ticket);
-            results[r.ticket] = std::move(res);
-            ++completed;
-            cv_done.notify_all();
-            R = Resident{};
-            return DGS_OK;
-        }
-        if (ea != cudaSuccess) return fail(ea, "request workspace");
-        // the instance's matrix, pitched (round_up(n, 4)) inside its workspace
-        Instance probe{};
-        const size_t ws = carve_instance(R.mem, r.n, true, &probe);
-        R.out = reinterpret_cast<int32_t*>(R.mem + ws);
-        const size_t lda = (size_t)probe.w.lda;
-        int32_t* a_dev = const_cast<int32_t*>(probe.w.a);
-        if (lda != (size_t)r.n) B_CUDA(cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, s), "pad");
-        const cudaMemcpyKind kind = (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        B_CUDA(cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, s), "upload");
-        eng.place(k, R.mem, r.n, true, nullptr, R.out, DGS_INIT_GREEDY, 0, 0);
-        std::lock_guard<std::mutex> lk(mu);
-        ++resident_count;
-        return DGS_OK;
+        R.ticket = u.r.ticket;
+        R.n = u.r.n;
+        R.bytes = u.r.bytes;
+        R.mem = u.mem;
+        R.submit_ns = u.r.submit_ns;
+        R.admit_ns = u.admit_ns;
+        R.out = reinterpret_cast<int32_t*>(u.mem + carve_instance(nullptr, u.r.n, true, nullptr));
+        eng.place(k, R.mem, R.n, true, nullptr, R.out, DGS_INIT_GREEDY, 0, 0);
     }
 
     dgs_status retire_done() {
@@ -650,12 +721,10 @@ struct dgs_server {
             {
                 std::lock_guard<std::mutex> lk(mu);
                 --resident_count;
-                used -= R.bytes;
-                pending.erase(R.ticket);
-                results[R.ticket] = std::move(res);
-                ++completed;
+                record_result(R.ticket, std::move(res), R.bytes);
             }
             cv_done.notify_all();
+            cv_work.notify_one();
             R = Resident{};
         }
         return DGS_OK;
@@ -696,14 +765,24 @@ dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_serv
     *out = nullptr;
     const int32_t cap = max_resident > 0 ? max_resident : 256;
     dgs_server* sv = new dgs_server(cap);
-    B_CUDA(cudaGetDevice(&sv->device), "cudaGetDevice");
+    cudaError_t e = cudaGetDevice(&sv->device);
+    if (e != cudaSuccess) {
+        delete sv;
+        return fail(e, "cudaGetDevice");
+    }
     sv->budget = budget_bytes;
     dgs_status st = sv->eng.init();
     if (st != DGS_OK) {
         delete sv;
         return st;
     }
+    e = cudaStreamCreateWithFlags(&sv->up_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete sv;
+        return fail(e, "upload stream");
+    }
     sv->worker = std::thread([sv] { sv->run(); });
+    sv->uploader = std::thread([sv] { sv->run_uploader(); });
     *out = sv;
     return DGS_OK;
 }
@@ -750,6 +829,8 @@ dgs_status dgs_server_get_info(dgs_server* sv, dgs_server_info* info) {
     info->completed = sv->completed;
     info->bytes_in_use = sv->used;
     info->kernel_launches = sv->launches;
+    info->upload_ms = sv->upload_ms;
+    info->step_ms = sv->step_ms;
     return sv->fatal;
 }
 
@@ -759,10 +840,19 @@ void dgs_server_destroy(dgs_server* sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
         sv->queue.clear();
+        for (const auto& r : sv->to_upload) {  // admitted, never uploaded: dropped
+            sv->used -= r.bytes;
+            --sv->reserved;
+        }
+        sv->to_upload.clear();
     }
+    sv->cv_up.notify_all();
+    sv->cv_work.notify_all();
+    if (sv->uploader.joinable()) sv->uploader.join();
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     if (sv->h_sigma) cudaFreeHost(sv->h_sigma);
+    if (sv->up_stream) cudaStreamDestroy(sv->up_stream);
     delete sv;
 }
 
