@@ -281,6 +281,15 @@ DGS_API dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, 
 DGS_API size_t dgs_server_request_bytes(int32_t n);
 DGS_API dgs_status dgs_submit(dgs_server* server, const int32_t* benefit, int32_t n, int32_t flags,
                               uint64_t* ticket);
+/* dgs_submit with per-request options (NULL: defaults): the start (GREEDY,
+ * RANDOM with options->seed, IDENTITY, or USER: options->init_sigma, n int32
+ * agent -> job in the same memory as benefit, e.g. the previous solution of
+ * a periodic re-solve -- a warm start), reeval_rule, max_sweeps and
+ * deadline_us (counted from admission).  algorithm must be
+ * DGS_ALG_PARALLEL and no trace is taken (DGS_ERR_INVALID otherwise).
+ * init_sigma follows the same lifetime rule as benefit. */
+DGS_API dgs_status dgs_submit_ex(dgs_server* server, const int32_t* benefit, int32_t n, int32_t flags,
+                                 const dgs_options* options, uint64_t* ticket);
 DGS_API dgs_status dgs_poll(dgs_server* server, uint64_t ticket, int32_t* sigma_out_host,
                             int64_t* objective_out, dgs_stats* stats, dgs_request_times* times);
 DGS_API dgs_status dgs_server_wait(dgs_server* server, uint64_t ticket, int64_t timeout_us,

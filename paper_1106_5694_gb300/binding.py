@@ -37,7 +37,8 @@ DGS_ALG_SEQUENTIAL = 1
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
-            "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning"]
+            "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning",
+            "dgs_submit_ex"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -156,6 +157,8 @@ def load():
     lib.dgs_server_request_bytes.restype = ctypes.c_size_t
     lib.dgs_submit.argtypes = [P, P, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
     lib.dgs_submit.restype = ctypes.c_int
+    lib.dgs_submit_ex.argtypes = [P, P, i32, i32, ctypes.POINTER(dgs_options), ctypes.POINTER(ctypes.c_uint64)]
+    lib.dgs_submit_ex.restype = ctypes.c_int
     lib.dgs_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_stats),
                              ctypes.POINTER(dgs_request_times)]
     lib.dgs_poll.restype = ctypes.c_int
@@ -350,6 +353,28 @@ class Server:
         st = load().dgs_submit(self._h, ptr, n, flags, ctypes.byref(t))
         if st == DGS_OK:
             self._keep[int(t.value)] = (benefit, n)
+        return st, int(t.value)
+
+    def dgs_submit_ex(self, benefit, init_sigma=None, **opts):
+        """Returns (status, ticket).  init_sigma (numpy for host matrices, an
+        int32 CUDA tensor for device ones) is a warm start; keyword options as
+        dgs_solve_ex (init, seed, reeval, max_sweeps, deadline_us)."""
+        if isinstance(benefit, torch.Tensor):
+            n, ptr, flags = _n(benefit), _dev(benefit, "benefit"), 0
+            o = _options(init_sigma=init_sigma, **opts)
+        else:
+            benefit = np.ascontiguousarray(benefit, dtype=np.int32)
+            n, ptr, flags = _n(benefit), ctypes.c_void_p(benefit.ctypes.data), DGS_SUBMIT_HOST
+            o = _options(**opts)
+            if init_sigma is not None:
+                init_sigma = np.ascontiguousarray(init_sigma, dtype=np.int32)
+                o.init_sigma = ctypes.c_void_p(init_sigma.ctypes.data)
+        if init_sigma is not None:
+            o.init = DGS_INIT_USER
+        t = ctypes.c_uint64(0)
+        st = load().dgs_submit_ex(self._h, ptr, n, flags, ctypes.byref(o), ctypes.byref(t))
+        if st == DGS_OK:
+            self._keep[int(t.value)] = (benefit, n, init_sigma)
         return st, int(t.value)
 
     def _take(self, fn, ticket, *extra):

@@ -481,6 +481,12 @@ struct dgs_server {
         int32_t flags;
         size_t bytes;
         int64_t submit_ns;
+        int32_t init;              // DGS_INIT_* of the request
+        int32_t reeval_all;
+        const int32_t* init_tau;   // USER start (same memory space as a), or null
+        uint64_t seed;
+        int32_t max_sweeps;
+        int64_t deadline_us;
     };
     struct Uploaded {
         Request r;
@@ -529,6 +535,12 @@ struct dgs_server {
     size_t h_sigma_cap = 0;
 
     explicit dgs_server(int32_t cap) : eng(cap, DGS_BATCH_MAX_N), slots(cap) {}
+
+    // A request's start (n int32) after its workspace and result.
+    static int32_t* start_of(char* mem, int32_t n) {
+        return reinterpret_cast<int32_t*>(mem + carve_instance(nullptr, n, true, nullptr) +
+                                          ((size_t)n * 4 + 255) / 256 * 256);
+    }
 
     void finish_all_pending(dgs_status why) {  // caller holds mu
         for (auto& kv : pending) {
@@ -586,6 +598,16 @@ struct dgs_server {
                     (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
                 if (e == cudaSuccess)
                     e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, up_stream);
+                // the start (USER: the caller's; RANDOM: drawn here) after the result
+                int32_t* start = start_of(mem, r.n);
+                std::vector<int32_t> perm;
+                if (e == cudaSuccess && r.init == DGS_INIT_USER)
+                    e = cudaMemcpyAsync(start, r.init_tau, (size_t)r.n * 4, kind, up_stream);
+                if (e == cudaSuccess && r.init == DGS_INIT_RANDOM) {
+                    perm.resize(r.n);
+                    random_start(r.n, r.seed, perm.data());
+                    e = cudaMemcpyAsync(start, perm.data(), (size_t)r.n * 4, cudaMemcpyHostToDevice, up_stream);
+                }
                 if (e == cudaSuccess) e = cudaStreamSynchronize(up_stream);
             }
             std::lock_guard<std::mutex> lk(mu);
@@ -688,7 +710,9 @@ struct dgs_server {
         R.submit_ns = u.r.submit_ns;
         R.admit_ns = u.admit_ns;
         R.out = reinterpret_cast<int32_t*>(u.mem + carve_instance(nullptr, u.r.n, true, nullptr));
-        eng.place(k, R.mem, R.n, true, nullptr, R.out, DGS_INIT_GREEDY, 0, 0);
+        const bool given = u.r.init == DGS_INIT_USER || u.r.init == DGS_INIT_RANDOM;
+        eng.place(k, R.mem, R.n, true, nullptr, R.out, given ? DGS_INIT_USER : u.r.init, u.r.max_sweeps,
+                  u.r.deadline_us, given ? start_of(u.mem, u.r.n) : nullptr, u.r.reeval_all != 0);
     }
 
     dgs_status retire_done() {
@@ -733,8 +757,8 @@ struct dgs_server {
 
 namespace {
 size_t request_bytes(int32_t n) {
-    // workspace with the pitched matrix, then the result
-    return carve_instance(nullptr, n, true, nullptr) + ((size_t)n * 4 + 255) / 256 * 256;
+    // workspace with the pitched matrix, then the result, then the start
+    return carve_instance(nullptr, n, true, nullptr) + 2 * (((size_t)n * 4 + 255) / 256 * 256);
 }
 
 dgs_status take_result(dgs_server* sv, uint64_t ticket, int32_t* sigma_out_host, int64_t* objective_out,
@@ -788,13 +812,34 @@ dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_serv
 }
 
 dgs_status dgs_submit(dgs_server* sv, const int32_t* benefit, int32_t n, int32_t flags, uint64_t* ticket) {
+    return dgs_submit_ex(sv, benefit, n, flags, nullptr, ticket);
+}
+
+dgs_status dgs_submit_ex(dgs_server* sv, const int32_t* benefit, int32_t n, int32_t flags,
+                         const dgs_options* options, uint64_t* ticket) {
     if (!sv || !benefit || !ticket || n <= 0 || n > DGS_BATCH_MAX_N) return DGS_ERR_INVALID;
+    dgs_options o;
+    dgs_default_options(&o);
+    if (options) o = *options;
+    if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_RANDOM && o.init != DGS_INIT_IDENTITY &&
+        o.init != DGS_INIT_USER)
+        return DGS_ERR_INVALID;
+    if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
+    if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
+    if (o.algorithm != DGS_ALG_PARALLEL || o.trace_capacity > 0) return DGS_ERR_INVALID;
     const size_t bytes = request_bytes(n);
     if (bytes > sv->budget) return DGS_ERR_BUSY;
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return sv->fatal != DGS_OK ? sv->fatal : DGS_ERR_INVALID;
     const uint64_t t = sv->next_ticket++;
-    sv->queue.push_back(dgs_server::Request{t, benefit, n, flags, bytes, now_ns()});
+    dgs_server::Request r{t, benefit, n, flags, bytes, now_ns()};
+    r.init = o.init;
+    r.reeval_all = o.reeval_rule == DGS_REEVAL_ALL ? 1 : 0;
+    r.init_tau = o.init == DGS_INIT_USER ? o.init_sigma : nullptr;
+    r.seed = o.seed;
+    r.max_sweeps = o.max_sweeps;
+    r.deadline_us = o.deadline_us;
+    sv->queue.push_back(r);
     sv->pending[t] = 0;
     *ticket = t;
     sv->cv_work.notify_one();

@@ -234,3 +234,40 @@ def test_server_range_error_and_continued_service():
         ref = oracle.dgs_parallel(a)
         np.testing.assert_array_equal(sig, ref.tau)
         assert f == ref.objective
+
+
+def test_server_warm_start_and_per_request_options():
+    """A periodic re-solve: the previous assignment of a slowly changing
+    matrix is the start of the next solve (dgs_submit_ex); results equal the
+    single solve with the same options."""
+    base = inputs.peer_shaped(500, 41)
+    st, sig0, _ = B.dgs_solve(_cuda(base))
+    prev = sig0.cpu().numpy()
+    rng = np.random.default_rng(5)
+    moved = base + rng.integers(0, 200, size=base.shape, dtype=np.int32)  # the peers' benefits drift
+    cases = [dict(init_sigma=prev), dict(init=B.DGS_INIT_RANDOM, seed=9, reeval=B.DGS_REEVAL_ALL),
+             dict(init=B.DGS_INIT_IDENTITY, max_sweeps=3)]
+    with B.Server(budget_bytes=2 << 30) as srv:
+        tickets = []
+        for k, c in enumerate(cases):
+            if k == 0:  # device memory for the first: matrix and start
+                t = srv.dgs_submit_ex(_cuda(moved), init_sigma=_cuda(prev))
+            else:
+                t = srv.dgs_submit_ex(moved, **c)
+            assert t[0] == B.DGS_OK
+            tickets.append(t[1])
+        bad = prev.copy()
+        bad[0] = bad[1]
+        t_bad = srv.dgs_submit_ex(moved, init_sigma=bad)[1]
+        for t, c in zip(tickets, cases):
+            st, sig, f, stats, _ = srv.dgs_server_wait(t)
+            single = dict(c)
+            if "init_sigma" in single:
+                single["init_sigma"] = _cuda(single["init_sigma"])
+                single["init"] = B.DGS_INIT_USER
+            st1, sig1, f1, stats1 = B.dgs_solve_ex(_cuda(moved), **single)
+            assert st == st1
+            np.testing.assert_array_equal(sig, sig1.cpu().numpy())
+            assert f == f1 and stats["sweeps"] == stats1["sweeps"]
+        assert srv.dgs_server_wait(t_bad)[0] == B.DGS_ERR_INVALID
+        assert srv.dgs_submit_ex(moved, algorithm=B.DGS_ALG_SEQUENTIAL)[0] == B.DGS_ERR_INVALID
