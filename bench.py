@@ -225,6 +225,31 @@ def oracle_sample(a, sweeps: int):
     return t_greedy, t_eval, tau
 
 
+# ------------------------------------------------------- ranks (replicas only)
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own independent instance (no data-path collective)."""
+    return rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time: a MAX all-reduce of one float64 (on `device`
+    for NCCL, on the CPU for gloo); the identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_solve(ms_per_step: float, world: int) -> float:
+    """Whole-job milliseconds per solve: `world` independent solves finish
+    within the slowest rank's step time."""
+    return ms_per_step / world
+
+
 # ---------------------------------------------------------------- our GPU arm
 def run_ours(args):
     import numpy as np
@@ -246,7 +271,7 @@ def run_ours(args):
             dist.barrier()
 
     B.load()
-    seed = rank
+    seed = replica_seed(rank)
     a = make_input(args.workload, args.n, seed)
     a_sha = sha(a)
     at = torch.from_numpy(a).to(dev)
@@ -305,11 +330,7 @@ def run_ours(args):
     barrier()
     sampler.mark(t_begin, time.perf_counter())
     clocks = sampler.stop()
-    ms_per_step = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(statistics.mean(step_ms), world, dev)
 
     # end to end through the host-buffer entry point (pinned host memory)
     pinned = torch.from_numpy(a).pin_memory()
@@ -322,11 +343,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         if st_h != B.DGS_OK or f_h != f:
             raise RuntimeError("host entry point result differs")
-    e2e = statistics.mean(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
 
     n = args.n
     peak, peak_src = measured_hbm_peak()
@@ -376,14 +393,14 @@ def run_ours(args):
             except Exception as exc:  # reported, never hides the main measurement
                 extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
 
-    value = ms_per_step / world  # job-wide ms per solve (world independent solves per step)
+    value = job_ms_per_solve(ms_per_step, world)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": workload_config(args.workload, n, seed),
         "roofline": roofline, "roofline_evaluation": roofline_eval, "cpu_baseline": cpu,
-        "e2e": {"value": round(e2e / world, 3), "unit": "ms", "h2d_bytes_per_step": 4 * n * n,
+        "e2e": {"value": round(job_ms_per_solve(e2e, world), 3), "unit": "ms", "h2d_bytes_per_step": 4 * n * n,
                 "d2h_bytes_per_step": 4 * n},
         "clocks": clocks, "gpu_launches": int(launches),
         "solve": {"sweeps": stats["sweeps"], "events": stats["events"], "swaps_applied": stats["swaps_applied"],
