@@ -356,10 +356,11 @@ def run_ours(args):
     roofline_eval = roofline_entry("full_evaluation_kernel",
                                    "full difference evaluation (Algorithm 2 for all slots), every benefit once",
                                    4 * n * n + 24 * n, statistics.mean(eval_ms), n, args.workload, peak, peak_src)
-    roofline_eval["launch_shape"] = {k: tuning.get(k) for k in ("rows_per_thread", "strip")} \
+    roofline_eval["launch_shape"] = {k: tuning.get(k) for k in ("rows_per_thread", "strip", "tma")} \
         if "error" not in tuning else tuning
-    roofline_eval["autotune_candidates_ms"] = {f"rows{c['rows_per_thread']}_strip{c['strip']}": round(c["ms"], 4)
-                                               for c in tuning.get("candidates", [])}
+    roofline_eval["autotune_candidates_ms"] = {
+        f"rows{c['rows_per_thread']}_strip{c['strip']}{'_tma' if c['tma'] else ''}": round(c["ms"], 4)
+        for c in tuning.get("candidates", [])}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -173,8 +173,9 @@ DGS_API dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* s
 /* ------------------------------------------------------------------------
  * Autotuning of launch shapes.  The paper fixes its block sizes by hand
  * (Section 4); here the shape of the full difference evaluation (Algorithm 2
- * for all slots: rows per thread and column tiles per work item) is chosen
- * per size class by timing.  dgs_autotune times every candidate shape on a
+ * for all slots: rows per thread, column tiles per work item, and whether
+ * the sigma-gathered rows arrive by TMA gathers or by per-thread copies) is
+ * chosen per size class by timing.  dgs_autotune times every candidate shape on a
  * synthetic n x n instance (values in [0, 10016), a random assignment; it
  * allocates about 4*n*n bytes for it) on `stream`, keeps the fastest for all
  * sizes in the same class (n in (2^(b-1), 2^b]) for the rest of the process,
@@ -193,9 +194,11 @@ typedef struct {
     int32_t cand_rows[DGS_TUNE_MAX_CANDIDATES];
     int32_t cand_strip[DGS_TUNE_MAX_CANDIDATES];
     double cand_ms[DGS_TUNE_MAX_CANDIDATES];  /* best of three launches each */
+    int32_t tma;              /* chosen: 1 = rows gathered by TMA (tile::gather4) */
+    int32_t cand_tma[DGS_TUNE_MAX_CANDIDATES];
 } dgs_tuning;
 DGS_API dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream);
-DGS_API dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip);
+DGS_API dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip, int32_t* tma);
 
 /* ------------------------------------------------------------------------
  * Batched solves.  The paper solves one instance at a time; its motivating

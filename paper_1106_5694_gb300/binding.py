@@ -109,6 +109,8 @@ class dgs_tuning(ctypes.Structure):
         ("cand_rows", ctypes.c_int32 * 16),
         ("cand_strip", ctypes.c_int32 * 16),
         ("cand_ms", ctypes.c_double * 16),
+        ("tma", ctypes.c_int32),
+        ("cand_tma", ctypes.c_int32 * 16),
     ]
 
 
@@ -171,7 +173,7 @@ def load():
     lib.dgs_server_destroy.restype = None
     lib.dgs_autotune.argtypes = [i32, ctypes.POINTER(dgs_tuning), P]
     lib.dgs_autotune.restype = ctypes.c_int
-    lib.dgs_get_tuning.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.dgs_get_tuning.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.dgs_get_tuning.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -431,15 +433,15 @@ def dgs_autotune(n: int, stream=None, device=None):
     s_obj = stream if stream is not None else torch.cuda.current_stream(dev)
     r = dgs_tuning()
     st = load().dgs_autotune(int(n), ctypes.byref(r), ctypes.c_void_p(s_obj.cuda_stream))
-    out = {"n_lo": r.n_lo, "n_hi": r.n_hi, "rows_per_thread": r.rows_per_thread, "strip": r.strip,
+    out = {"n_lo": r.n_lo, "n_hi": r.n_hi, "rows_per_thread": r.rows_per_thread, "strip": r.strip, "tma": r.tma,
            "best_ms": r.best_ms,
-           "candidates": [{"rows_per_thread": r.cand_rows[k], "strip": r.cand_strip[k], "ms": r.cand_ms[k]}
-                          for k in range(r.candidates)]}
+           "candidates": [{"rows_per_thread": r.cand_rows[k], "strip": r.cand_strip[k], "tma": r.cand_tma[k],
+                           "ms": r.cand_ms[k]} for k in range(r.candidates)]}
     return st, out
 
 
 def dgs_get_tuning(n: int):
-    """Returns (status, rows_per_thread, strip) used for solves of size n."""
-    rows, strip = ctypes.c_int32(0), ctypes.c_int32(0)
-    st = load().dgs_get_tuning(int(n), ctypes.byref(rows), ctypes.byref(strip))
-    return st, int(rows.value), int(strip.value)
+    """Returns (status, rows_per_thread, strip, tma) used for solves of size n."""
+    rows, strip, tma = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    st = load().dgs_get_tuning(int(n), ctypes.byref(rows), ctypes.byref(strip), ctypes.byref(tma))
+    return st, int(rows.value), int(strip.value), int(tma.value)

@@ -695,15 +695,21 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
         if (st == DGS_OK && (e = launch_range_check(S.w, s)) != cudaSuccess) st = cuda_fail(e, "range check");
         if (st == DGS_OK && (e = launch_start_from_tau(S.w, sigma, DGS_INIT_USER, S.seen, s)) != cudaSuccess)
             st = cuda_fail(e, "start");
-        const int32_t rows_c[2] = {8, 4};
-        const int32_t strips[6] = {0, 4, 8, 16, 32, 64};  // 0: contiguous balanced ranges
+        // candidate shapes: 8 rows per thread with every strip (0: contiguous
+        // balanced ranges), with and without TMA gathers; 4 rows per thread
+        // with two strips
+        std::vector<EvalShape> shapes;
+        for (int32_t tma = 0; tma < 2; ++tma) {
+            for (int32_t strip : {0, 4, 8, 16, 32, 64}) shapes.push_back(EvalShape{8, strip, tma});
+            for (int32_t strip : {0, 32}) shapes.push_back(EvalShape{4, strip, tma});
+        }
         dgs_tuning r{};
         r.best_ms = 1e30;
         EventPair ev;
         if (st == DGS_OK) st = ev.begin(s);
-        for (int32_t ri = 0; ri < 2 && st == DGS_OK; ++ri) {
-            for (int32_t si = 0; si < 6 && st == DGS_OK; ++si) {
-                const EvalShape sh{rows_c[ri], strips[si]};
+        for (size_t ci = 0; ci < shapes.size() && ci < DGS_TUNE_MAX_CANDIDATES && st == DGS_OK; ++ci) {
+            {
+                const EvalShape sh = shapes[ci];
                 e = launch_full_evaluation_shape(S.w, 0, sh, s);  // warm-up
                 double best = 1e30;
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
@@ -720,16 +726,18 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
                 const int32_t c = r.candidates++;
                 r.cand_rows[c] = sh.rows;
                 r.cand_strip[c] = sh.strip;
+                r.cand_tma[c] = sh.tma;
                 r.cand_ms[c] = best;
                 if (best < r.best_ms) {
                     r.best_ms = best;
                     r.rows_per_thread = sh.rows;
                     r.strip = sh.strip;
+                    r.tma = sh.tma;
                 }
             }
         }
         if (st == DGS_OK) {
-            set_evaluation_shape(n, EvalShape{r.rows_per_thread, r.strip});
+            set_evaluation_shape(n, EvalShape{r.rows_per_thread, r.strip, r.tma});
             const int32_t b = size_bucket(n);
             r.n_lo = b == 0 ? 1 : (1 << (b - 1)) + 1;
             r.n_hi = 1 << b;
@@ -741,11 +749,12 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
     return st;
 }
 
-dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip) {
+dgs_status dgs_get_tuning(int32_t n, int32_t* rows_per_thread, int32_t* strip, int32_t* tma) {
     if (n <= 0 || n > kMaxN) return DGS_ERR_INVALID;
     const EvalShape sh = evaluation_shape(n);
     if (rows_per_thread) *rows_per_thread = sh.rows;
     if (strip) *strip = sh.strip;
+    if (tma) *tma = sh.tma;
     return DGS_OK;
 }
 

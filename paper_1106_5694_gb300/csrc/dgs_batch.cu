@@ -513,8 +513,9 @@ struct dgs_server {
     size_t budget = 0;
     Engine eng;
     std::vector<Resident> slots;  // worker only
-    std::thread worker, uploader;
-    cudaStream_t up_stream = nullptr;
+    static constexpr int kUploaders = 2;  // uploads of different requests overlap
+    std::thread worker, uploader[kUploaders];
+    cudaStream_t up_stream[kUploaders] = {};
     // everything below is guarded by mu
     std::mutex mu;
     std::condition_variable cv_work, cv_up, cv_done;
@@ -560,8 +561,9 @@ struct dgs_server {
         ++completed;
     }
 
-    void run_uploader() {
+    void run_uploader(int u) {
         cudaSetDevice(device);
+        cudaStream_t up = up_stream[u];
         for (;;) {
             Request r;
             {
@@ -573,7 +575,7 @@ struct dgs_server {
             }
             const int64_t t0 = now_ns();
             char* mem = nullptr;
-            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), r.bytes, up_stream);
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), r.bytes, up);
             if (e == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
                 cudaGetLastError();
                 Result res{};
@@ -593,25 +595,25 @@ struct dgs_server {
                 carve_instance(mem, r.n, true, &probe);
                 const size_t lda = (size_t)probe.w.lda;
                 int32_t* a_dev = const_cast<int32_t*>(probe.w.a);
-                if (lda != (size_t)r.n) e = cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, up_stream);
+                if (lda != (size_t)r.n) e = cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, up);
                 const cudaMemcpyKind kind =
                     (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
                 if (e == cudaSuccess)
-                    e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, up_stream);
+                    e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, up);
                 // the start (USER: the caller's; RANDOM: drawn here) after the result
                 int32_t* start = start_of(mem, r.n);
                 std::vector<int32_t> perm;
                 if (e == cudaSuccess && r.init == DGS_INIT_USER)
-                    e = cudaMemcpyAsync(start, r.init_tau, (size_t)r.n * 4, kind, up_stream);
+                    e = cudaMemcpyAsync(start, r.init_tau, (size_t)r.n * 4, kind, up);
                 if (e == cudaSuccess && r.init == DGS_INIT_RANDOM) {
                     perm.resize(r.n);
                     random_start(r.n, r.seed, perm.data());
-                    e = cudaMemcpyAsync(start, perm.data(), (size_t)r.n * 4, cudaMemcpyHostToDevice, up_stream);
+                    e = cudaMemcpyAsync(start, perm.data(), (size_t)r.n * 4, cudaMemcpyHostToDevice, up);
                 }
-                if (e == cudaSuccess) e = cudaStreamSynchronize(up_stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(up);
             }
             std::lock_guard<std::mutex> lk(mu);
-            upload_ms += (now_ns() - t0) * 1e-6;
+            upload_ms += (now_ns() - t0) * 1e-6;  // summed over the upload threads
             if (e != cudaSuccess) {
                 fail(e, "request upload");
                 fatal = DGS_ERR_CUDA;
@@ -800,13 +802,16 @@ dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_serv
         delete sv;
         return st;
     }
-    e = cudaStreamCreateWithFlags(&sv->up_stream, cudaStreamNonBlocking);
+    for (int u = 0; u < dgs_server::kUploaders && e == cudaSuccess; ++u)
+        e = cudaStreamCreateWithFlags(&sv->up_stream[u], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        for (int u = 0; u < dgs_server::kUploaders; ++u)
+            if (sv->up_stream[u]) cudaStreamDestroy(sv->up_stream[u]);
         delete sv;
         return fail(e, "upload stream");
     }
     sv->worker = std::thread([sv] { sv->run(); });
-    sv->uploader = std::thread([sv] { sv->run_uploader(); });
+    for (int u = 0; u < dgs_server::kUploaders; ++u) sv->uploader[u] = std::thread([sv, u] { sv->run_uploader(u); });
     *out = sv;
     return DGS_OK;
 }
@@ -893,11 +898,13 @@ void dgs_server_destroy(dgs_server* sv) {
     }
     sv->cv_up.notify_all();
     sv->cv_work.notify_all();
-    if (sv->uploader.joinable()) sv->uploader.join();
+    for (auto& t : sv->uploader)
+        if (t.joinable()) t.join();
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     if (sv->h_sigma) cudaFreeHost(sv->h_sigma);
-    if (sv->up_stream) cudaStreamDestroy(sv->up_stream);
+    for (int u = 0; u < dgs_server::kUploaders; ++u)
+        if (sv->up_stream[u]) cudaStreamDestroy(sv->up_stream[u]);
     delete sv;
 }
 

@@ -322,9 +322,11 @@ cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, i
                                   cudaStream_t s);
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 // Launch shape of the full evaluation (rows per thread 4 or 8; strip: column
-// tiles per work item, 0 = one contiguous balanced range of tiles per CTA).
+// tiles per work item, 0 = one contiguous balanced range of tiles per CTA;
+// tma: X tiles by TMA gathers).
 struct EvalShape {
     int32_t rows, strip;
+    int32_t tma;  // 1: X tiles by TMA gathers (cp.async.bulk.tensor tile::gather4)
 };
 EvalShape evaluation_shape(int32_t n);
 void set_evaluation_shape(int32_t n, EvalShape shape);

@@ -24,6 +24,8 @@
 // column-side maxima of each tile are combined across the CTA in shared
 // memory at the next barrier and committed with 64-bit atomicMax, which is
 // order independent and therefore deterministic.
+#include <cuda.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
@@ -143,7 +145,7 @@ struct CopyRows {
     int32_t x[Geo<kRows>::kCopies], y[Geo<kRows>::kCopies];
 };
 
-template <int kRows>
+template <int kRows, bool kTma = false>
 __device__ __forceinline__ CopyRows<kRows> copy_rows(const Workspace& w, int32_t J, int32_t K) {
     const int32_t rq = threadIdx.x >> 4;
     const int32_t J0 = J * kT, K0 = K * kT, n = w.n;
@@ -151,7 +153,7 @@ __device__ __forceinline__ CopyRows<kRows> copy_rows(const Workspace& w, int32_t
 #pragma unroll
     for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
         const int32_t r = rq + q * Geo<kRows>::kRowStep;
-        c.x[q] = (J0 + r < n) ? w.sigma[J0 + r] : -1;
+        c.x[q] = (!kTma && J0 + r < n) ? w.sigma[J0 + r] : -1;
         c.y[q] = (K0 + r < n) ? w.sigma[K0 + r] : -1;
     }
     return c;
@@ -165,7 +167,8 @@ __device__ __forceinline__ CopyRows<kRows> no_rows() {
     return c;
 }
 
-// Issue this thread's 16-byte copies of tile (J, K) into stage.
+// Issue this thread's 16-byte copies of tile (J, K) into stage (the X rows
+// are skipped when copy_rows marked them -1, as it does under the TMA path).
 template <int kRows>
 __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int32_t J, int32_t K,
                                            const CopyRows<kRows>& c) {
@@ -185,6 +188,34 @@ __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int
     else if (threadIdx.x < 32) cp_async16(stage->dk + chunk, w.diag + K0 + chunk);
     else if (threadIdx.x < 48) cp_async16(stage->sj + chunk, w.sigma + J0 + chunk);
     else if (threadIdx.x < 64) cp_async16(stage->dj + chunk, w.diag + J0 + chunk);
+}
+
+// TMA path: the X tile of (J, K) (rows sigma(J0 .. J0 + 63), columns K0 ..
+// K0 + 63 of a) as 16 four-row gathers (cp.async.bulk.tensor tile::gather4,
+// box 64 x 1 of the tensor map over a), issued by lanes 0..15 of warp 0 and
+// completing on the stage's mbarrier (16 KB per tile).  xs: the four rows'
+// sigma of this lane (rows past n read row 0; their pairs are never used).
+__device__ __forceinline__ void gather_x(Stage* stage, const CUtensorMap* tm, int32_t K0, const int32_t (&xs)[4],
+                                         uint64_t* bar) {
+    const int lane = threadIdx.x;  // warp 0 only
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(kT * kT * sizeof(int32_t)));
+    __syncwarp();
+    if (lane < 16) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(stage->x + lane * 4 * kT)),
+            "l"(reinterpret_cast<uint64_t>(tm)), "r"(K0), "r"(xs[0]), "r"(xs[1]), "r"(xs[2]), "r"(xs[3]),
+            "r"(smem_u32(bar))
+            : "memory");
+    }
+}
+
+// This lane's four X rows of row block J (warp 0, lanes 0..15).
+__device__ __forceinline__ void x_rows(const Workspace& w, int32_t J, int32_t (&xs)[4]) {
+    const int32_t r0 = J * kT + 4 * (int32_t)(threadIdx.x & 15);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xs[q] = (r0 + q < w.n) ? w.sigma[r0 + q] : 0;
 }
 
 // Packed-key geometry for this n and value range; pw = 0 means "exact path".
@@ -376,18 +407,30 @@ constexpr size_t eval_smem_bytes() {
     return sizeof(Stage) * kStages + 2 * 2 * Geo<kRows>::kGroups * kT * sizeof(unsigned long long);
 }
 
-// The tile loop of one block of one instance's evaluation.
-template <int kRows, bool kPacked>
+// The tile loop of one block of one instance's evaluation.  kTma: the X
+// tiles arrive by TMA gathers (tm: tensor map over a) tracked by one mbarrier
+// per stage; the Y tiles and the sigma / D rows by 16-byte cp.async.
+template <int kRows, bool kPacked, bool kTma>
 __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t strip, int32_t bid, int32_t nblk,
-                                                const Packing& pk) {
+                                                const Packing& pk, const CUtensorMap* tm) {
     constexpr int kGroups = Geo<kRows>::kGroups;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* stages = reinterpret_cast<Stage*>(smem_raw);
     unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(Stage) * kStages);
     // colbuf[b][0: agent keys kGroups x 64 | 1: job keys kGroups x 64], b = tile parity
+    __shared__ __align__(8) uint64_t s_bar[kStages];
+    if (kTma) {
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < kStages; ++q) mbar_init(&s_bar[q], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
 
     const int32_t n = w.n;
     const int32_t nb = (n + kT - 1) / kT;
+    int32_t xs[4] = {0, 0, 0, 0};  // warp 0 under kTma: sigma of this lane's X rows of row block xs_j
+    int32_t xs_j = -1;
 
     // producer cursor: kStages - 1 tiles ahead of the consumer; the rows
     // (sigma) it will copy are loaded two tiles before they are needed
@@ -395,26 +438,46 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
     bool prod_ok = cursor_first(prod, nb, strip, bid, nblk);
     for (int s = 0; s < kStages - 1; ++s) {
         if (prod_ok) {
-            issue_tile<kRows>(w, &stages[s], prod.j, prod.k, copy_rows<kRows>(w, prod.j, prod.k));
+            issue_tile<kRows>(w, &stages[s], prod.j, prod.k, copy_rows<kRows, kTma>(w, prod.j, prod.k));
+            if (kTma && threadIdx.x < 32) {
+                if (prod.j != xs_j) {
+                    x_rows(w, prod.j, xs);
+                    xs_j = prod.j;
+                }
+                gather_x(&stages[s], tm, prod.k * kT, xs, &s_bar[s]);
+            }
             prod_ok = cursor_next(prod, nb, strip, nblk);
         }
         cp_async_commit();
     }
     TileCursor ahead = prod;  // one tile after prod
     bool ahead_ok = prod_ok && cursor_next(ahead, nb, strip, nblk);
-    CopyRows<kRows> rows_now = prod_ok ? copy_rows<kRows>(w, prod.j, prod.k) : no_rows<kRows>();
-    CopyRows<kRows> rows_next = ahead_ok ? copy_rows<kRows>(w, ahead.j, ahead.k) : no_rows<kRows>();
+    CopyRows<kRows> rows_now = prod_ok ? copy_rows<kRows, kTma>(w, prod.j, prod.k) : no_rows<kRows>();
+    CopyRows<kRows> rows_next = ahead_ok ? copy_rows<kRows, kTma>(w, ahead.j, ahead.k) : no_rows<kRows>();
 
     TileCursor cons;
     bool cons_ok = cursor_first(cons, nb, strip, bid, nblk);
     Rows<kRows, kPacked> rs;
     bool item_start = true;
     int32_t t = 0, prev_k0 = -1;
+    int32_t cs = 0;       // consumer stage (t mod kStages)
+    uint32_t cph = 0;     // its mbarrier phase
     while (cons_ok) {
         const int32_t J0 = cons.j * kT;
         cp_async_wait<kStages - 2>();
-        __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
-        const Stage* stage = &stages[t % kStages];
+        if (kTma) {
+            const bool ok = mbar_wait_bounded(&s_bar[cs], cph);
+            if (__syncthreads_or(!ok)) {  // a gather never arrived: stop with an error
+                if (threadIdx.x == 0) {
+                    w.st->error = kErrWaitTimeout;
+                    w.st->status = kError;
+                }
+                break;
+            }
+        } else {
+            __syncthreads();  // tile t landed for every thread; tile t-1 fully consumed
+        }
+        const Stage* stage = &stages[cs];
         if (item_start) {
             rows_start<kRows, kPacked>(rs, stage, J0, pk);
             item_start = false;
@@ -424,13 +487,21 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
             commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
         }
         if (prod_ok) {
-            issue_tile<kRows>(w, &stages[(t + kStages - 1) % kStages], prod.j, prod.k, rows_now);
+            const int32_t ps = cs == 0 ? kStages - 1 : cs - 1;  // the stage of tile t - 1, free now
+            issue_tile<kRows>(w, &stages[ps], prod.j, prod.k, rows_now);
+            if (kTma && threadIdx.x < 32) {
+                if (prod.j != xs_j) {
+                    x_rows(w, prod.j, xs);
+                    xs_j = prod.j;
+                }
+                gather_x(&stages[ps], tm, prod.k * kT, xs, &s_bar[ps]);
+            }
             prod = ahead;
             prod_ok = ahead_ok;
             rows_now = rows_next;
             if (ahead_ok) {
                 ahead_ok = cursor_next(ahead, nb, strip, nblk);
-                if (ahead_ok) rows_next = copy_rows<kRows>(w, ahead.j, ahead.k);
+                if (ahead_ok) rows_next = copy_rows<kRows, kTma>(w, ahead.j, ahead.k);
             }
         }
         cp_async_commit();
@@ -442,12 +513,16 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
         if (run_end) commit_rows<kRows, kPacked>(rs, J0, n, w, pk);
         prev_k0 = K0;
         ++t;
+        if (++cs == kStages) {
+            cs = 0;
+            cph ^= 1u;
+        }
         cons_ok = cursor_next(cons, nb, strip, nblk);
         item_start = run_end;
     }
     cp_async_wait<0>();
     __syncthreads();
-    if (prev_k0 >= 0) {
+    if (prev_k0 >= 0 && w.st->status == kRunning) {
         const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
         commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
     }
@@ -457,22 +532,23 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
 // The evaluation of one instance by block bid of the nblk blocks assigned to
 // it (a CTA of the single-instance launch, or one item of a batched queue).
 // All threads of the CTA call it together.
-template <int kRows>
+template <int kRows, bool kTma = false>
 __device__ __forceinline__ void full_evaluation_body(const Workspace& w, int32_t conditional, int32_t strip,
-                                                     int32_t bid, int32_t nblk) {
+                                                     int32_t bid, int32_t nblk, const CUtensorMap* tm = nullptr) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
     if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
     if (conditional && bid == 0 && threadIdx.x == 0) st->full_evals += 1;
     const Packing pk = packing_for(w.n, st->max_abs);
-    if (pk.pw != 0 && !w.exact_keys) evaluation_loop<kRows, true>(w, strip, bid, nblk, pk);
-    else evaluation_loop<kRows, false>(w, strip, bid, nblk, pk);
+    if (pk.pw != 0 && !w.exact_keys) evaluation_loop<kRows, true, kTma>(w, strip, bid, nblk, pk, tm);
+    else evaluation_loop<kRows, false, kTma>(w, strip, bid, nblk, pk, tm);
 }
 
-template <int kRows>
+template <int kRows, bool kTma>
 __global__ void __launch_bounds__(Geo<kRows>::kThreads, 1) full_evaluation_kernel(Workspace w, int32_t conditional,
-                                                                                  int32_t strip) {
-    full_evaluation_body<kRows>(w, conditional, strip, blockIdx.x, gridDim.x);
+                                                                                  int32_t strip,
+                                                                                  const __grid_constant__ CUtensorMap tm) {
+    full_evaluation_body<kRows, kTma>(w, conditional, strip, blockIdx.x, gridDim.x, &tm);
 }
 
 // Batched: each queue item is one block of one instance's evaluation (the
@@ -507,45 +583,86 @@ __global__ void keys_to_slots_kernel(Workspace w, int32_t* ag, int32_t* aj, int3
 // shape never changes a result: every key is a maximum over the same pairs.
 constexpr int kStrip = 8;
 constexpr int32_t kBuckets = 18;
-std::atomic<int32_t> g_shape[kBuckets];  // 0: default, else rows * 256 + strip
+std::atomic<int32_t> g_shape[kBuckets];  // 0: default, else tma << 16 | rows << 8 | strip
 
 int32_t size_bucket(int32_t n) { return n <= 1 ? 0 : std::min<int32_t>(kBuckets - 1, 32 - __builtin_clz((uint32_t)(n - 1))); }
 
-int32_t env_int(const char* name) {
+int32_t env_int(const char* name, int32_t fallback) {
     const char* e = std::getenv(name);
-    return e ? std::atoi(e) : 0;
+    return e ? std::atoi(e) : fallback;
 }
 
 EvalShape evaluation_shape(int32_t n) {
-    static const int32_t env_rows = env_int("DGS_EVAL_ROWS");
-    static const int32_t env_strip = env_int("DGS_EVAL_STRIP");
-    EvalShape sh{8, kStrip};
+    static const int32_t env_rows = env_int("DGS_EVAL_ROWS", 0);
+    static const int32_t env_strip = env_int("DGS_EVAL_STRIP", -1);
+    static const int32_t env_tma = env_int("DGS_EVAL_TMA", -1);
+    EvalShape sh{8, kStrip, 0};
     const int32_t v = g_shape[size_bucket(n)].load(std::memory_order_relaxed);
-    if (v != 0) sh = EvalShape{v >> 8, v & 255};
+    if (v != 0) sh = EvalShape{(v >> 8) & 255, v & 255, v >> 16};
     if (env_rows == 4 || env_rows == 8) sh.rows = env_rows;
-    if (env_strip >= 0 && env_strip <= 255 && std::getenv("DGS_EVAL_STRIP")) sh.strip = env_strip;
+    if (env_strip >= 0 && env_strip <= 255) sh.strip = env_strip;
+    if (env_tma == 0 || env_tma == 1) sh.tma = env_tma;
     return sh;
 }
 
 void set_evaluation_shape(int32_t n, EvalShape sh) {
-    g_shape[size_bucket(n)].store(sh.rows * 256 + sh.strip, std::memory_order_relaxed);
+    g_shape[size_bucket(n)].store((sh.tma ? 1 << 16 : 0) | sh.rows << 8 | sh.strip, std::memory_order_relaxed);
 }
 
 size_t full_evaluation_smem_bytes() { return eval_smem_bytes<8>(); }
 
-template <int kRows>
-static cudaError_t launch_eval_rows(const Workspace& w, int32_t conditional, int32_t strip, cudaStream_t s) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return static_cast<EncodeTiledFn>(nullptr);
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map over a (n rows of lda int32, row pitch lda) with 64 x 1 boxes,
+// the shape the gathers of the TMA path read.
+bool make_gather_map(const Workspace& w, CUtensorMap* tm) {
+    EncodeTiledFn fn = encode_tiled();
+    if (fn == nullptr) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)w.lda, (cuuint64_t)w.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)w.lda * sizeof(int32_t)};
+    const cuuint32_t box[2] = {(cuuint32_t)kT, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<int32_t*>(w.a), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int kRows, bool kTma>
+static cudaError_t launch_eval(const Workspace& w, int32_t conditional, int32_t strip, const CUtensorMap& tm,
+                               cudaStream_t s) {
     constexpr size_t smem = eval_smem_bytes<kRows>();
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel<kRows>), kRows == 8 ? 0 : 7,
-                                      smem);
+    const int slot = kRows == 8 ? (kTma ? 11 : 0) : (kTma ? 10 : 7);  // attribute cache slots
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel<kRows, kTma>), slot, smem);
     if (e != cudaSuccess) return e;
-    full_evaluation_kernel<kRows><<<152, Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip);
+    full_evaluation_kernel<kRows, kTma><<<152, Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip, tm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional, EvalShape sh, cudaStream_t s) {
-    return sh.rows == 4 ? launch_eval_rows<4>(w, conditional, sh.strip, s)
-                        : launch_eval_rows<8>(w, conditional, sh.strip, s);
+    alignas(64) CUtensorMap tm{};
+    const bool tma = sh.tma && make_gather_map(w, &tm);
+    if (sh.rows == 4) return tma ? launch_eval<4, true>(w, conditional, sh.strip, tm, s)
+                                 : launch_eval<4, false>(w, conditional, sh.strip, tm, s);
+    return tma ? launch_eval<8, true>(w, conditional, sh.strip, tm, s)
+               : launch_eval<8, false>(w, conditional, sh.strip, tm, s);
 }
 
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s) {

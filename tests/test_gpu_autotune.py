@@ -28,8 +28,9 @@ def test_autotune_picks_a_shape_and_solves_stay_exact(n):
     assert r["n_lo"] <= n <= r["n_hi"]
     assert len(r["candidates"]) >= 6 and all(c["ms"] > 0 for c in r["candidates"])
     assert r["best_ms"] == min(c["ms"] for c in r["candidates"])
-    st, rows, strip = B.dgs_get_tuning(n)
-    assert st == B.DGS_OK and (rows, strip) == (r["rows_per_thread"], r["strip"])
+    st, rows, strip, tma = B.dgs_get_tuning(n)
+    assert st == B.DGS_OK and (rows, strip, tma) == (r["rows_per_thread"], r["strip"], r["tma"])
+    assert {c["tma"] for c in r["candidates"]} == {0, 1}
     for kind, seed in (("peer", 1), ("uniform", 2)):
         a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
         ref = oracle.dgs_parallel(a)

@@ -245,7 +245,11 @@ print(json.dumps(out))
                                  {"DGS_EVAL_STRIP": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"},
                                  {"DGS_EVAL_STRIP": "32", "DGS_UPDATE_POLICY": "1"},
                                  {"DGS_EVAL_STRIP": "0", "DGS_UPDATE_POLICY": "1"},
-                                 {"DGS_EVAL_STRIP": "0", "DGS_EVAL_ROWS": "4", "DGS_EXACT_KEYS": "1"}])
+                                 {"DGS_EVAL_STRIP": "0", "DGS_EVAL_ROWS": "4", "DGS_EXACT_KEYS": "1"},
+                                 {"DGS_EVAL_TMA": "1", "DGS_EVAL_STRIP": "0", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_TMA": "1", "DGS_EVAL_STRIP": "8", "DGS_EVAL_ROWS": "4",
+                                  "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_TMA": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"}])
 def test_internal_paths_agree_with_oracle(env):
     """Forcing the full-evaluation or row-task update path, placing the
     controller's scratch in global memory, making its reservation keys and
