@@ -153,7 +153,7 @@ __device__ __forceinline__ CopyRows<kRows> copy_rows(const Workspace& w, int32_t
 #pragma unroll
     for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
         const int32_t r = rq + q * Geo<kRows>::kRowStep;
-        c.x[q] = (!kTma && J0 + r < n) ? w.sigma[J0 + r] : -1;
+        c.x[q] = -1;  // X rows come from the producer's per-run sources (or TMA)
         c.y[q] = (K0 + r < n) ? w.sigma[K0 + r] : -1;
     }
     return c;
@@ -167,11 +167,31 @@ __device__ __forceinline__ CopyRows<kRows> no_rows() {
     return c;
 }
 
-// Issue this thread's 16-byte copies of tile (J, K) into stage (the X rows
-// are skipped when copy_rows marked them -1, as it does under the TMA path).
+// This thread's X source rows for row block J (the rows of a at sigma(J0 +
+// r), at this thread's chunk; null past n).  They do not change along a row
+// run, so the producer computes them once per run.
+template <int kRows>
+struct XRows {
+    const int32_t* p[Geo<kRows>::kCopies];
+};
+
+template <int kRows>
+__device__ __forceinline__ void x_sources(const Workspace& w, int32_t J, XRows<kRows>& xr) {
+    const int32_t chunk = (threadIdx.x & 15) * 4;
+    const int32_t rq = threadIdx.x >> 4;
+#pragma unroll
+    for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
+        const int32_t r = J * kT + rq + q * Geo<kRows>::kRowStep;
+        xr.p[q] = r < w.n ? w.a + (size_t)w.sigma[r] * w.lda + chunk : nullptr;
+    }
+}
+
+// Issue this thread's 16-byte copies of tile (J, K) into stage: the X rows
+// from xr (skipped when xr is null, as under the TMA path), the Y rows of
+// sigma c.y, sigma and D of the tile's columns and rows.
 template <int kRows>
 __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int32_t J, int32_t K,
-                                           const CopyRows<kRows>& c) {
+                                           const CopyRows<kRows>& c, const XRows<kRows>* xr) {
     const int32_t chunk = (threadIdx.x & 15) * 4;  // first int of the 16-byte chunk
     const int32_t rq = threadIdx.x >> 4;
     const int32_t J0 = J * kT, K0 = K * kT;
@@ -180,7 +200,7 @@ __device__ __forceinline__ void issue_tile(const Workspace& w, Stage* stage, int
 #pragma unroll
     for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
         const int32_t r = rq + q * Geo<kRows>::kRowStep;
-        if (in_x && c.x[q] >= 0) cp_async16(stage->x + r * kT + chunk, w.a + (size_t)c.x[q] * w.lda + K0 + chunk);
+        if (xr != nullptr && in_x && xr->p[q] != nullptr) cp_async16(stage->x + r * kT + chunk, xr->p[q] + K0);
         if (in_y && c.y[q] >= 0) cp_async16(stage->y + r * kYP + chunk, w.a + (size_t)c.y[q] * w.lda + J0 + chunk);
     }
     // sigma and D of the columns (arrays hold at least round_up(n, 64) entries)
@@ -277,16 +297,18 @@ __device__ __forceinline__ void rows_start(Rows<kRows, kPacked>& rs, const Stage
 }
 
 // One tile: thread (ty, tx) covers column k = K0 + tx and rows J0 + ty*kRows
-// .. + kRows - 1.  Column-side partial keys go to colbuf (combined at the
-// next barrier).
+// .. + kRows - 1.  Column-side partial keys go to the tile's column buffer cb
+// (combined at the next barrier): packed 32-bit keys when kPacked (unpacked
+// once per column by commit_columns), else 64-bit keys.
 template <int kRows, bool kRagged, bool kPacked>
 __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPacked>& rs, int32_t J0, int32_t K0,
-                                             int32_t n, const Packing& pk, unsigned long long* col_a,
-                                             unsigned long long* col_j) {
+                                             int32_t n, const Packing& pk, void* cb) {
+    constexpr int kGroups = Geo<kRows>::kGroups;
     const int tx = threadIdx.x & 63;
     const int ty = threadIdx.x >> 6;
     const int32_t k = K0 + tx;
     unsigned long long ka = 0ull, kj = 0ull;
+    int32_t ca = pk.mask, cj = pk.mask;  // packed column-side keys ("none")
     if (!kRagged || k < n) {
         const int32_t sk = stage->sk[tx];
         const int32_t dk = stage->dk[tx];
@@ -294,7 +316,6 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPa
         const int4* yrow = reinterpret_cast<const int4*>(stage->y + tx * kYP + ty * kRows);
         if (kPacked) {
             const int32_t cka = pk.mask - k, ckj = pk.mask - sk;
-            int32_t ca = pk.mask, cj = pk.mask;
 #pragma unroll
             for (int q = 0; q < kRows / 4; ++q) {
                 const int4 y4 = yrow[q];
@@ -311,8 +332,6 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPa
                     cj = max(cj, gs + rs.cj[r]);       // row k, lowest partner agent
                 }
             }
-            ka = unpack_key(ca, pk);
-            kj = unpack_key(cj, pk);
         } else {
             int32_t cg = 0, cc = -1, cs = 0x7fffffff;
 #pragma unroll
@@ -349,23 +368,40 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPa
             }
         }
     }
-    col_a[ty * kT + tx] = ka;
-    col_j[ty * kT + tx] = kj;
+    if (kPacked) {
+        int32_t* c32 = static_cast<int32_t*>(cb);
+        c32[ty * kT + tx] = ca;
+        c32[kGroups * kT + ty * kT + tx] = cj;
+    } else {
+        unsigned long long* c64 = static_cast<unsigned long long*>(cb);
+        c64[ty * kT + tx] = ka;
+        c64[kGroups * kT + ty * kT + tx] = kj;
+    }
 }
 
 // Combine the row-group partials of the previous tile's columns.
-template <int kRows>
-__device__ __forceinline__ void commit_columns(const unsigned long long* col_a, const unsigned long long* col_j,
-                                               int32_t K0, int32_t n, const Workspace& w) {
+template <int kRows, bool kPacked>
+__device__ __forceinline__ void commit_columns(const void* cb, int32_t K0, int32_t n, const Workspace& w,
+                                               const Packing& pk) {
+    constexpr int kGroups = Geo<kRows>::kGroups;
     const int t = threadIdx.x;
     if (t >= 2 * kT) return;
     const int q = t & 63;
-    const unsigned long long* src = (t < kT) ? col_a : col_j;
+    const int half = t < kT ? 0 : 1;  // 0: agent keys, 1: job keys
     unsigned long long m = 0ull;
+    if (kPacked) {
+        const int32_t* src = static_cast<const int32_t*>(cb) + half * kGroups * kT;
+        int32_t p = src[q];
 #pragma unroll
-    for (int g = 0; g < Geo<kRows>::kGroups; ++g) m = umax64(m, src[g * kT + q]);
+        for (int g = 1; g < kGroups; ++g) p = max(p, src[g * kT + q]);
+        m = unpack_key(p, pk);
+    } else {
+        const unsigned long long* src = static_cast<const unsigned long long*>(cb) + half * kGroups * kT;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) m = umax64(m, src[g * kT + q]);
+    }
     const int32_t k = K0 + q;
-    if (m != 0ull && k < n) atomicMax((t < kT) ? &w.key_a[k] : &w.key_j[k], m);
+    if (m != 0ull && k < n) atomicMax(half == 0 ? &w.key_a[k] : &w.key_j[k], m);
 }
 
 template <int kRows, bool kPacked>
@@ -431,6 +467,8 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
     const int32_t nb = (n + kT - 1) / kT;
     int32_t xs[4] = {0, 0, 0, 0};  // warp 0 under kTma: sigma of this lane's X rows of row block xs_j
     int32_t xs_j = -1;
+    XRows<kRows> xr;  // without kTma: this thread's X source rows for row block xr_j
+    int32_t xr_j = -1;
 
     // producer cursor: kStages - 1 tiles ahead of the consumer; the rows
     // (sigma) it will copy are loaded two tiles before they are needed
@@ -438,7 +476,12 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
     bool prod_ok = cursor_first(prod, nb, strip, bid, nblk);
     for (int s = 0; s < kStages - 1; ++s) {
         if (prod_ok) {
-            issue_tile<kRows>(w, &stages[s], prod.j, prod.k, copy_rows<kRows, kTma>(w, prod.j, prod.k));
+            if (!kTma && prod.j != xr_j) {
+                x_sources<kRows>(w, prod.j, xr);
+                xr_j = prod.j;
+            }
+            issue_tile<kRows>(w, &stages[s], prod.j, prod.k, copy_rows<kRows, kTma>(w, prod.j, prod.k),
+                              kTma ? nullptr : &xr);
             if (kTma && threadIdx.x < 32) {
                 if (prod.j != xs_j) {
                     x_rows(w, prod.j, xs);
@@ -482,13 +525,14 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
             rows_start<kRows, kPacked>(rs, stage, J0, pk);
             item_start = false;
         }
-        if (prev_k0 >= 0) {
-            const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
-            commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
-        }
+        if (prev_k0 >= 0) commit_columns<kRows, kPacked>(colbuf + ((t - 1) & 1) * 2 * kGroups * kT, prev_k0, n, w, pk);
         if (prod_ok) {
             const int32_t ps = cs == 0 ? kStages - 1 : cs - 1;  // the stage of tile t - 1, free now
-            issue_tile<kRows>(w, &stages[ps], prod.j, prod.k, rows_now);
+            if (!kTma && prod.j != xr_j) {
+                x_sources<kRows>(w, prod.j, xr);
+                xr_j = prod.j;
+            }
+            issue_tile<kRows>(w, &stages[ps], prod.j, prod.k, rows_now, kTma ? nullptr : &xr);
             if (kTma && threadIdx.x < 32) {
                 if (prod.j != xs_j) {
                     x_rows(w, prod.j, xs);
@@ -507,8 +551,8 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
         cp_async_commit();
         const int32_t K0 = cons.k * kT;
         unsigned long long* cb = colbuf + (t & 1) * 2 * kGroups * kT;
-        if ((J0 + kT > n) || (K0 + kT > n)) compute_tile<kRows, true, kPacked>(stage, rs, J0, K0, n, pk, cb, cb + kGroups * kT);
-        else compute_tile<kRows, false, kPacked>(stage, rs, J0, K0, n, pk, cb, cb + kGroups * kT);
+        if ((J0 + kT > n) || (K0 + kT > n)) compute_tile<kRows, true, kPacked>(stage, rs, J0, K0, n, pk, cb);
+        else compute_tile<kRows, false, kPacked>(stage, rs, J0, K0, n, pk, cb);
         const bool run_end = cons.k + 1 >= cons.kend;  // last tile of this row run
         if (run_end) commit_rows<kRows, kPacked>(rs, J0, n, w, pk);
         prev_k0 = K0;
@@ -522,10 +566,8 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
     }
     cp_async_wait<0>();
     __syncthreads();
-    if (prev_k0 >= 0 && w.st->status == kRunning) {
-        const unsigned long long* cb = colbuf + ((t - 1) & 1) * 2 * kGroups * kT;
-        commit_columns<kRows>(cb, cb + kGroups * kT, prev_k0, n, w);
-    }
+    if (prev_k0 >= 0 && w.st->status == kRunning)
+        commit_columns<kRows, kPacked>(colbuf + ((t - 1) & 1) * 2 * kGroups * kT, prev_k0, n, w, pk);
     __syncthreads();  // the stages and colbuf may be reused by the caller's next call
 }
 
