@@ -388,6 +388,10 @@ def run_ours(args):
     except Exception as exc:
         extra["sequential"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batched:
+        try:
+            extra["other_sizes"] = run_other_sizes(dev, measured_hbm_peak()[0])
+        except Exception as exc:
+            extra["other_sizes"] = {"error": f"{type(exc).__name__}: {exc}"}
         for key, fn in (("batched", run_batched), ("serving", run_serving)):
             try:
                 extra[key] = fn(dev)
@@ -414,6 +418,60 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- the other sizes
+def run_other_sizes(dev, peak, steps=3):
+    """Single solves of the other single-instance configurations: n = 4096
+    peer-shaped (64 MB, fits in L2) and n = 20000 (1.6 GB) peer-shaped and
+    uniform [0, 1e6).  Each result is checked to be a permutation with its
+    exact objective and no improving 2-exchange; the first full evaluation
+    is timed inside the solve."""
+    import numpy as np
+    import torch
+
+    from paper_1106_5694_gb300 import binding as B
+
+    out = []
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    for kind, n in (("peer", 4096), ("peer", 20000), ("uniform", 20000)):
+        a = make_input(kind, n, 0)
+        at = torch.from_numpy(a).to(dev)
+        del a
+        B.dgs_autotune(n, device=dev)
+        st, sig, f, stats = B.dgs_solve_ex(at, profile=1)
+        torch.cuda.synchronize(dev)
+        s64 = sig.long()
+        d = at[torch.arange(n, device=dev), s64].long()
+        ok = st == B.DGS_OK and bool(torch.equal(torch.sort(s64).values, torch.arange(n, device=dev))) and \
+            int(d.sum().item()) == f
+        best = -1
+        for r0 in range(0, n, 2048):  # no improving 2-exchange: max over G in row blocks
+            cross = at[r0:r0 + 2048][:, s64].long()            # a[i, tau_k]
+            back = at[:, s64[r0:r0 + 2048]].long().T           # a[k, tau_i] (rows i)
+            g = cross + back - d[r0:r0 + 2048, None] - d[None, :]
+            best = max(best, int(g.max().item()))
+        ok = ok and best <= 0
+        ms, ev = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(steps):
+            flush.fill_(k)
+            e0.record(stream)
+            st, sig, f2, stats = B.dgs_solve_ex(at, sigma_out=sig, profile=1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            ev.append(stats["evaluation_ms"])
+        t_ev = statistics.mean(ev)
+        out.append({"workload": f"{kind} n={n}", "ms": round(statistics.mean(ms), 3), "sweeps": stats["sweeps"],
+                    "swaps_applied": stats["swaps_applied"], "objective": f2,
+                    "evaluation_ms": round(t_ev, 4),
+                    "evaluation_frac_of_hbm": round((4 * n * n + 24 * n) / (t_ev * 1e-3) / 1e9 / peak, 4),
+                    "checked": "permutation, exact objective, no improving 2-exchange" if ok else "FAILED"})
+        del at
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------- batched and served solves

@@ -781,15 +781,8 @@ __global__ void init_batched_kernel(BatchTable t, int32_t update_policy) {
             const uint32_t v = ones ? 0x01010101u : 0u;
             *reinterpret_cast<uint4*>(p) = make_uint4(v, v, v, v);
         }
-        if (in.a_src) {  // re-pitched copy of the caller's matrix (n % 4 != 0 or misaligned)
-            int32_t* dst = const_cast<int32_t*>(w.a);
-            const int32_t n = w.n, lda = w.lda;  // n * lda < 2^31 for batched sizes
-            for (int32_t i = e.bid; i < n; i += e.nblk) {
-                const int32_t* src = in.a_src + (size_t)i * n;
-                int32_t* d = dst + (size_t)i * lda;
-                for (int32_t j = threadIdx.x; j < lda; j += blockDim.x) d[j] = j < n ? src[j] : 0;
-            }
-        }
+        // a caller's matrix that needs re-pitching (n % 4 != 0 or misaligned) is
+        // copied into the workspace by pass 1, which reads it anyway
         if (e.bid == 0 && threadIdx.x == 0) {
             DeviceState h{};
             h.status = kRunning;

@@ -20,8 +20,11 @@ namespace {
 
 constexpr int kT = 64;  // tile edge
 
+// a_src (batched instances only): the caller's matrix with row pitch n when w.a
+// is the workspace's pitched copy still to be filled; this pass reads a_src
+// and writes the copy as it goes.  Null: w.a is read.
 __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t tiles_x, int32_t tiles_total,
-                                                  int32_t bid, int32_t nblk) {
+                                                  int32_t bid, int32_t nblk, const int32_t* a_src = nullptr) {
     __shared__ int32_t s[kT][kT + 1];
     __shared__ unsigned long long colpart[4][kT];
     const int32_t n = w.n;
@@ -39,7 +42,16 @@ __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t ti
             const int c = lane16 * 4;
             const int32_t i = I0 + r, j = J0 + c;
             int4 v = make_int4(0, 0, 0, 0);
-            if (i < n && j < w.lda) v = *reinterpret_cast<const int4*>(w.a + (size_t)i * w.lda + j);
+            if (a_src == nullptr) {
+                if (i < n && j < w.lda) v = *reinterpret_cast<const int4*>(w.a + (size_t)i * w.lda + j);
+            } else if (i < n && j < w.lda) {  // re-pitch: unaligned reads, padding columns 0
+                const int32_t* src = a_src + (size_t)i * n + j;
+                v.x = j < n ? src[0] : 0;
+                v.y = j + 1 < n ? src[1] : 0;
+                v.z = j + 2 < n ? src[2] : 0;
+                v.w = j + 3 < n ? src[3] : 0;
+                *reinterpret_cast<int4*>(const_cast<int32_t*>(w.a) + (size_t)i * w.lda + j) = v;
+            }
             s[r][c + 0] = v.x; s[r][c + 1] = v.y; s[r][c + 2] = v.z; s[r][c + 3] = v.w;
             // row best over this tile's 4 columns of this thread
             unsigned long long best = 0;
@@ -428,7 +440,7 @@ __global__ void range_check_kernel(Workspace w) {
 __global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchQueues q) {
     for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t bid, int32_t nblk) {
         const int32_t tx = (in.w.n + kT - 1) / kT;
-        greedy_pass1_body(in.w, tx, tx * tx, bid, nblk);
+        greedy_pass1_body(in.w, tx, tx * tx, bid, nblk, in.a_src);
     });
 }
 
