@@ -96,6 +96,8 @@ def _load():
     lib.oracle_dgs_parallel.restype = ctypes.c_int
     lib.oracle_dgs_sequential.argtypes = [P, i32, i32, P, ctypes.c_uint64, i32, P, P, P, i32, P, P, P, P, P, P]
     lib.oracle_dgs_sequential.restype = ctypes.c_int
+    lib.oracle_dgs_rect.argtypes = [P, i32, i32, i32, i32, ctypes.c_uint64, i32, P, P, P]
+    lib.oracle_dgs_rect.restype = ctypes.c_int
     lib.oracle_hungarian.argtypes = [P, i32, P]
     lib.oracle_hungarian.restype = i64
     lib.oracle_brute_force.argtypes = [P, i32, P]
@@ -240,6 +242,19 @@ def dgs_sequential(a, init: int = INIT_GREEDY, init_tau=None, max_iters: int = 0
                     np.ones(k, np.int32), tp[:k].copy(), tf[:k].copy())
     r.trace_slot, r.trace_target, r.trace_u, r.trace_v = (x[:k].copy() for x in extra)
     return r
+
+
+def dgs_rect(a, algorithm: int = 0, init: int = INIT_GREEDY, seed: int = 0, reeval: int = REEVAL_BOX):
+    """Rectangular instance (n agents x m jobs): (status, assignment with -1
+    for agents left on a dummy job, objective, sweeps)."""
+    a = _c(a)
+    n, m = a.shape
+    out = np.empty(n, np.int32)
+    f = ctypes.c_int64()
+    st = _Stats()
+    status = _load().oracle_dgs_rect(_p(a), n, m, algorithm, init, ctypes.c_uint64(seed), reeval, _p(out),
+                                     ctypes.byref(f), ctypes.byref(st))
+    return status, out, f.value, st.sweeps
 
 
 def hungarian(a):

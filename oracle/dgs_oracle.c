@@ -495,6 +495,32 @@ out:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Rectangular instances (reading R11): the padded square instance. */
+int oracle_dgs_rect(const int32_t* a, int32_t n_agents, int32_t m_jobs, int32_t algorithm, int32_t init_mode,
+                    uint64_t seed, int32_t reeval_rule, int32_t* assign_out, int64_t* f_out, oracle_stats* stats)
+{
+    if (a == NULL || assign_out == NULL || f_out == NULL || n_agents <= 0 || m_jobs <= 0) return ORACLE_ERR_INVALID;
+    int32_t s = n_agents > m_jobs ? n_agents : m_jobs;
+    int32_t* sq = (int32_t*)calloc((size_t)s * s, sizeof(int32_t));
+    int32_t* tau = (int32_t*)malloc((size_t)s * sizeof(int32_t));
+    for (int32_t i = 0; i < n_agents; ++i)
+        memcpy(sq + (size_t)i * s, a + (size_t)i * m_jobs, (size_t)m_jobs * sizeof(int32_t));
+    int64_t f = 0;
+    int status;
+    if (algorithm == 1)
+        status = oracle_dgs_sequential(sq, s, init_mode, NULL, seed, 0, tau, &f, stats, 0, NULL, NULL,
+                                       NULL, NULL, NULL, NULL);
+    else
+        status = oracle_dgs_parallel(sq, s, init_mode, NULL, seed, 0, ORACLE_CC_SLOTS, reeval_rule, tau, &f, stats,
+                                     0, NULL, NULL, NULL);
+    for (int32_t i = 0; i < n_agents; ++i) assign_out[i] = tau[i] < m_jobs ? tau[i] : -1;
+    *f_out = f;
+    free(sq);
+    free(tau);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact optimum, Hungarian method (Kuhn 1955) in its shortest augmenting
  * path form: rows are inserted one at a time; a Dijkstra-like scan over
  * reduced costs c[i][j] - u[i] - v[j] (c = -a, minimised) finds the

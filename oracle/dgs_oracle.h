@@ -136,6 +136,18 @@ int oracle_dgs_sequential(const int32_t* a, int32_t n, int32_t init_mode,
                           int32_t trace_cap, int32_t* trace_applied, int64_t* trace_objective,
                           int32_t* trace_slot, int32_t* trace_target, int32_t* trace_u, int32_t* trace_v);
 
+/* Rectangular instances (n_agents x m_jobs, row-major, row = agent): the
+ * switching moves an agent to a free job as well as exchanging jobs.  Read
+ * (R11) as DGS on the square instance of size max(n, m) padded with
+ * zero-benefit dummy agents (n < m) or dummy jobs (n > m), dummies numbered
+ * after the real ones: an exchange between a real agent and the dummy holding
+ * a free job is exactly the move of that agent to the job (same gain).
+ * Options as oracle_dgs_parallel (algorithm 0: Algorithm 3, 1: Algorithm 1).
+ * assign_out[i] = job of agent i, or -1 when agent i holds a dummy job;
+ * *f_out = sum of the real benefits. */
+int oracle_dgs_rect(const int32_t* a, int32_t n_agents, int32_t m_jobs, int32_t algorithm, int32_t init_mode,
+                    uint64_t seed, int32_t reeval_rule, int32_t* assign_out, int64_t* f_out, oracle_stats* stats);
+
 /* Exact LSAP maximum by the Hungarian method (Kuhn 1955, in the
  * shortest-augmenting-path form with dual potentials).  O(n^3). */
 int64_t oracle_hungarian(const int32_t* a, int32_t n, int32_t* tau_out);

@@ -33,6 +33,8 @@ MUTATIONS = {
     "sequential_ties_to_agent": ("if (dbar[is] > dund[js]) {", "if (dbar[is] >= dund[js]) {"),
     "sequential_no_outer_repeat": ("        if (f == f_start) break;\n    }\n\nfinish:\n    memcpy(tau_out, tau, nb);\n    *f_out = oracle_objective(a, n, tau);\n    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;\nout:\n    if (stats) *stats = st;\n    free(sigma); free(tau); free(dbar);",
                                    "        break;\n    }\n\nfinish:\n    memcpy(tau_out, tau, nb);\n    *f_out = oracle_objective(a, n, tau);\n    if (status == ORACLE_OK && *f_out != f) status = ORACLE_ERR_INTERNAL;\nout:\n    if (stats) *stats = st;\n    free(sigma); free(tau); free(dbar);"),
+    "rect_padding_pitch": ("memcpy(sq + (size_t)i * s, a + (size_t)i * m_jobs,", "memcpy(sq + (size_t)i * m_jobs, a + (size_t)i * m_jobs,"),
+    "rect_dummy_job_kept": ("assign_out[i] = tau[i] < m_jobs ? tau[i] : -1;", "assign_out[i] = tau[i];"),
     "sequential_stale_partner": ("                u = is;\n                v = sigma[jbar[is]];", "                u = is;\n                v = jbar[is];"),
 }
 

@@ -474,3 +474,69 @@ def test_sequential_exchanges_follow_switch_definition(kind, n, seed):
         if gain > 0:
             tau[u], tau[v] = tau[v], tau[u]
     assert tau.tolist() == r.tau.tolist()
+
+
+# ------------------------------------ rectangular instances (moves to free jobs)
+def _rect_brute_force(a):
+    """Best sum over injective maps of the smaller side into the larger
+    (unmatched agents contribute 0)."""
+    import itertools
+    n, m = a.shape
+    best = None
+    if n <= m:
+        for jobs in itertools.permutations(range(m), n):
+            v = int(sum(int(a[i, j]) for i, j in enumerate(jobs)))
+            best = v if best is None else max(best, v)
+    else:
+        for agents in itertools.permutations(range(n), m):
+            v = int(sum(int(a[i, j]) for j, i in enumerate(agents)))
+            best = v if best is None else max(best, v)
+    return best
+
+
+def _rect_local_optimum(a, assign):
+    """No improving exchange between two agents and no improving move of an
+    agent to a free job (or off a job, when there are more agents than jobs,
+    where being unassigned is worth 0)."""
+    n, m = a.shape
+    a64 = a.astype(np.int64)
+    val = np.array([a64[i, assign[i]] if assign[i] >= 0 else 0 for i in range(n)])
+    for i in range(n):
+        for k in range(n):
+            if i == k:
+                continue
+            ji, jk = assign[i], assign[k]
+            gi = a64[i, jk] if jk >= 0 else 0
+            gk = a64[k, ji] if ji >= 0 else 0
+            if gi + gk - val[i] - val[k] > 0:
+                return False
+    free = set(range(m)) - {j for j in assign if j >= 0}
+    for i in range(n):
+        for j in free:
+            if a64[i, j] - val[i] > 0:
+                return False
+    return True
+
+
+@pytest.mark.parametrize("n,m,seed", [(2, 5, 0), (3, 6, 1), (4, 7, 2), (5, 8, 3), (6, 4, 4), (7, 3, 5), (1, 6, 6)])
+def test_rect_small_against_brute_force(n, m, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(-20, 50, size=(n, m), dtype=np.int32)
+    for algorithm in (0, 1):
+        for init in (oracle.INIT_GREEDY, oracle.INIT_RANDOM, oracle.INIT_IDENTITY):
+            st, assign, f, _ = oracle.dgs_rect(a, algorithm=algorithm, init=init, seed=seed)
+            assert st == oracle.OK
+            real = [j for j in assign if j >= 0]
+            assert len(set(real)) == len(real) and all(0 <= j < m for j in real)
+            assert len(real) == min(n, m) or n > m
+            assert f == int(sum(int(a[i, j]) for i, j in enumerate(assign) if j >= 0))
+            assert _rect_local_optimum(a, assign)
+            assert f <= _rect_brute_force(a)
+
+
+def test_rect_with_free_jobs_moves_an_agent():
+    """One agent, three jobs, identity start (job 0): the move to the best
+    free job is taken (a 2-exchange with the dummy agent holding it)."""
+    a = np.array([[1, 9, 4]], np.int32)
+    st, assign, f, sweeps = oracle.dgs_rect(a, init=oracle.INIT_IDENTITY)
+    assert st == oracle.OK and assign.tolist() == [1] and f == 9 and sweeps >= 1
