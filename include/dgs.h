@@ -150,6 +150,21 @@ DGS_API dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n,
                           const dgs_options* options, dgs_stats* stats,
                           dgs_stream_t stream);
 
+/* Rectangular instances: n_agents agents, m_jobs jobs, benefit n_agents x
+ * m_jobs (DEVICE, row-major, row = agent, caller-owned).  The switching also
+ * moves an agent to a free job (n < m) or off its job (n > m, where an
+ * unassigned agent is worth 0): the method runs on the square instance of
+ * size max(n, m) padded with zero-benefit dummy agents or dummy jobs,
+ * numbered after the real ones, so that such a move is a 2-exchange with a
+ * dummy (same gain).  assign_out: DEVICE, n_agents int32, the job of each
+ * agent or -1 when it is left without one.  *objective_out: the sum of the
+ * real benefits.  options as for dgs_solve_ex, except that USER starts and
+ * traces are not taken (DGS_ERR_INVALID).  Workspace: about 8 max(n, m)^2
+ * bytes (the padded matrix and its transpose).  Blocks until done. */
+DGS_API dgs_status dgs_solve_rect(const int32_t* benefit, int32_t n_agents, int32_t m_jobs, int32_t* assign_out,
+                                  int64_t* objective_out, const dgs_options* options, dgs_stats* stats,
+                                  dgs_stream_t stream);
+
 /* One fresh difference evaluation of every agent and job (Algorithm 2 for
  * all agents, JDE for all jobs; the first parallel block of Algorithm 3)
  * for the assignment sigma_in (DEVICE, agent -> job, must be a permutation).

@@ -38,7 +38,7 @@ EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host"
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
             "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning",
-            "dgs_submit_ex"]
+            "dgs_submit_ex", "dgs_solve_rect"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -171,6 +171,9 @@ def load():
     lib.dgs_server_get_info.restype = ctypes.c_int
     lib.dgs_server_destroy.argtypes = [P]
     lib.dgs_server_destroy.restype = None
+    lib.dgs_solve_rect.argtypes = [P, i32, i32, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_options),
+                                   ctypes.POINTER(dgs_stats), P]
+    lib.dgs_solve_rect.restype = ctypes.c_int
     lib.dgs_autotune.argtypes = [i32, ctypes.POINTER(dgs_tuning), P]
     lib.dgs_autotune.restype = ctypes.c_int
     lib.dgs_get_tuning.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -257,6 +260,22 @@ def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, s
     st = load().dgs_solve_ex(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
                              ctypes.byref(o), ctypes.byref(s), _stream(benefit, stream))
     return st, sigma_out, int(f.value), s.as_dict()
+
+
+def dgs_solve_rect(benefit: torch.Tensor, assign_out: torch.Tensor | None = None, stream=None, **opts):
+    """dgs_solve_rect: benefit is an n_agents x m_jobs int32 CUDA tensor;
+    returns (status, assign_out (job or -1 per agent), objective, stats)."""
+    if benefit.ndim != 2:
+        raise ValueError("benefit must be an n_agents x m_jobs matrix")
+    n, m = int(benefit.shape[0]), int(benefit.shape[1])
+    if assign_out is None:
+        assign_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
+    o = _options(**opts)
+    f = ctypes.c_int64(0)
+    s = dgs_stats()
+    st = load().dgs_solve_rect(_dev(benefit, "benefit"), n, m, _dev(assign_out, "assign_out"), ctypes.byref(f),
+                               ctypes.byref(o), ctypes.byref(s), _stream(benefit, stream))
+    return st, assign_out, int(f.value), s.as_dict()
 
 
 def dgs_solve_host(benefit: np.ndarray, stream=None, device=None, **opts):

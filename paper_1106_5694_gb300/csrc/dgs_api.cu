@@ -351,6 +351,21 @@ __global__ void arm_deadline_kernel(DeviceState* st, int64_t deadline_us) {
 
 __global__ void record_initial_objective_kernel(DeviceState* st) { st->f_initial = st->f; }
 
+// Rectangular instance -> square instance of size s (zero-benefit dummies).
+__global__ void pad_square_kernel(const int32_t* a, int32_t n, int32_t m, int32_t s, int32_t* sq) {
+    const size_t total = (size_t)s * s;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(q / s), j = (int32_t)(q - (size_t)i * s);
+        sq[q] = (i < n && j < m) ? a[(size_t)i * m + j] : 0;
+    }
+}
+
+// Jobs of the real agents; a dummy job means no job.
+__global__ void trim_assignment_kernel(const int32_t* tau, int32_t n, int32_t m, int32_t* out) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = tau[i] < m ? tau[i] : -1;
+}
+
 // Synthetic benefits for timing launch shapes: values in [0, 10016) from a
 // per-element hash (the range of peer-shaped instances, so the packed-key
 // path of the evaluation is the one timed).  Pitch lda, padding zero.
@@ -623,6 +638,33 @@ dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n, int32_t* sigma
     }
     cudaFreeAsync(buf, s);
     cudaStreamSynchronize(s);
+    return st;
+}
+
+dgs_status dgs_solve_rect(const int32_t* benefit, int32_t n_agents, int32_t m_jobs, int32_t* assign_out,
+                          int64_t* objective_out, const dgs_options* options, dgs_stats* stats, dgs_stream_t stream) {
+    if (benefit == nullptr || assign_out == nullptr || objective_out == nullptr || n_agents <= 0 || m_jobs <= 0)
+        return DGS_ERR_INVALID;
+    const int32_t sz = n_agents > m_jobs ? n_agents : m_jobs;
+    if (sz > kMaxN) return DGS_ERR_INVALID;
+    dgs_options o;
+    dgs_default_options(&o);
+    if (options) o = *options;
+    if (o.init == DGS_INIT_USER || o.trace_capacity > 0) return DGS_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceBuffer buf(s);
+    const size_t sq_bytes = align_up((size_t)sz * sz * sizeof(int32_t), 256);
+    DGS_TRY(buf.alloc(sq_bytes + (size_t)sz * sizeof(int32_t)));
+    int32_t* sq = static_cast<int32_t*>(buf.p);
+    int32_t* tau = reinterpret_cast<int32_t*>(static_cast<char*>(buf.p) + sq_bytes);
+    pad_square_kernel<<<152 * 8, 256, 0, s>>>(benefit, n_agents, m_jobs, sz, sq);
+    DGS_CUDA(cudaGetLastError(), "pad");
+    const dgs_status st = solve_impl(sq, sz, tau, objective_out, &o, stats, s);
+    if (st != DGS_OK && st != DGS_TIMEOUT) return st;
+    trim_assignment_kernel<<<(n_agents + 255) / 256, 256, 0, s>>>(tau, n_agents, m_jobs, assign_out);
+    DGS_CUDA(cudaGetLastError(), "trim");
+    DGS_CUDA(cudaStreamSynchronize(s), "trim");
+    if (stats) stats->kernel_launches += 2;
     return st;
 }
 

@@ -361,3 +361,27 @@ def test_sequential_hand_trace_and_cap_on_gpu():
         np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
         assert f == ref.objective and stats["sweeps"] == ref.sweeps
     assert B.dgs_solve_batched([_cuda(big)], algorithm=B.DGS_ALG_SEQUENTIAL)[0] == B.DGS_ERR_INVALID
+
+
+# ------------------------------- rectangular instances (moves to free jobs)
+RECT_CASES = [(1, 5, 0), (3, 7, 1), (64, 100, 2), (100, 64, 3), (130, 257, 4), (300, 129, 5), (257, 257, 6)]
+
+
+@pytest.mark.parametrize("n,m,seed", RECT_CASES)
+def test_rect_matches_oracle(n, m, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(-50, 1000, size=(n, m), dtype=np.int32)
+    for algorithm, init, reeval in ((0, oracle.INIT_GREEDY, oracle.REEVAL_BOX), (0, oracle.INIT_RANDOM, oracle.REEVAL_ALL),
+                                    (1, oracle.INIT_GREEDY, oracle.REEVAL_BOX)):
+        st_o, assign_o, f_o, sweeps_o = oracle.dgs_rect(a, algorithm=algorithm, init=init, seed=seed, reeval=reeval)
+        assert st_o == oracle.OK
+        st, assign, f, stats = B.dgs_solve_rect(_cuda(a), algorithm=algorithm, init=init, seed=seed, reeval=reeval)
+        assert st == B.DGS_OK, (B.dgs_status_string(st), B.dgs_last_cuda_error())
+        np.testing.assert_array_equal(assign.cpu().numpy(), assign_o)
+        assert f == f_o and stats["sweeps"] == sweeps_o
+
+
+def test_rect_rejects_user_start_and_bad_sizes():
+    a = _cuda(np.ones((3, 5), np.int32))
+    assert B.dgs_solve_rect(a, init=B.DGS_INIT_USER, init_sigma=_cuda(np.arange(5)))[0] == B.DGS_ERR_INVALID
+    assert B.dgs_solve_rect(torch.zeros((0, 5), dtype=torch.int32, device="cuda"))[0] == B.DGS_ERR_INVALID
