@@ -44,6 +44,14 @@ int32_t env_phase_timers() {
     }();
     return v;
 }
+int32_t env_compact_min() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_CTL_COMPACT_MIN");
+        const int32_t x = e ? std::atoi(e) : 2048;
+        return x >= 1 ? x : 2048;
+    }();
+    return v;
+}
 int32_t env_short_wraps() {
     static const int32_t v = [] {
         const char* e = std::getenv("DGS_SHORT_WRAPS");

@@ -411,6 +411,9 @@ int32_t env_controller_mode_cap();
 // tests reach their wrap-around paths.
 int32_t env_short_wraps();
 int32_t env_phase_timers();
+// DGS_CTL_COMPACT_MIN: shortest edge list the controller compacts (default
+// 2048; tests lower it so that compaction runs on small instances).
+int32_t env_compact_min();
 // DGS_EXACT_KEYS=1 disables the packed 32-bit keys of the evaluation kernel.
 int32_t env_exact_keys();
 

@@ -142,7 +142,8 @@ constexpr int kUnroll = 4;
 // list_cap: entries of each two-tier list held in shared memory.
 template <typename EdgeT>
 __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem_mode, const CtlScratch& g,
-                                                uint32_t span, uint32_t stamp_wrap, int32_t list_cap) {
+                                                uint32_t span, uint32_t stamp_wrap, int32_t list_cap,
+                                                int32_t compact_min) {
     using C = Codec<EdgeT>;
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
@@ -244,7 +245,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     // ------------------------------------------------------------- sweeps
     // Quiet sweeps turn at least one stale slot into a fresh one each, so one
     // launch runs at most 2n + 1 of them; more means an internal error.
-    const int32_t L = s_L;
+    int32_t L = s_L;
     for (int32_t quiet = 0;; ++quiet) {
         if (tid == 0) {
             // loop condition of Algorithm 3 (some slot has delta > 0), sweep
@@ -270,6 +271,39 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         DGS_CT(kPtCtlTop)
         if (s_stop) break;
         if (pt) atomicAdd(pt + kPtCtlSweeps, 1ull);
+        // An edge that dies in a quiet sweep never lives again in this launch.
+        // Once fewer than half of the L listed positions are live, compact the
+        // list in place, keeping the priority order (positions are
+        // priorities, and deterministic reservations depend only on their
+        // order), so that later sweeps scan live edges only; the reservation
+        // keys restart with the new positions.
+        if (s_live * 2 < L && L >= compact_min) {
+            int32_t base = 0;
+            for (int32_t c0 = 0; c0 < L; c0 += kCtlThreads) {
+                const int32_t p = c0 + tid;
+                const uint8_t es = p < L ? estate[p] : (uint8_t)0;
+                const bool alive = (es & kAlive) != 0;
+                const EdgeT e = alive ? E[p] : (EdgeT)0;
+                const int32_t slot = alive ? w.ctl_slot[p] : 0;
+                int32_t total;
+                const int32_t pos = base + block_scan(alive ? 1 : 0, warp_sums, &total);  // every read is done
+                if (alive) {
+                    E[pos] = e;
+                    estate[pos] = es;
+                    w.ctl_slot[pos] = slot;
+                    if (slot_s) slot_s[pos] = (uint16_t)slot;
+                }
+                base += total;
+            }
+            for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
+            __syncthreads();
+            if (tid == 0) {
+                s_L = base;
+                s_round = 0u;
+            }
+            __syncthreads();
+            L = s_L;
+        }
         if (s_stamp >= stamp_wrap) {  // claim stamps wrap: clear them once
             for (int32_t i = tid; i < n; i += kCtlThreads) claimed[i] = 0;
             __syncthreads();
@@ -525,8 +559,8 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
 template <typename EdgeT>
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
                                                                    uint32_t span, uint32_t stamp_wrap,
-                                                                   int32_t list_cap) {
-    controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap);
+                                                                   int32_t list_cap, int32_t compact_min) {
+    controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min);
 }
 
 // Before each controller launch: clear the marks of the last event, re-
@@ -911,10 +945,10 @@ __global__ void prepare_edges_batched_kernel(BatchTable t) {
 }
 
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_batched_kernel(BatchTable t, uint32_t span,
-                                                                           uint32_t stamp_wrap) {
+                                                                           uint32_t stamp_wrap, int32_t compact_min) {
     for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t, int32_t) {
         const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc, in.ctl.und};
-        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap);
+        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min);
     });
 }
 
@@ -998,8 +1032,9 @@ cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cuda
     const bool short_wrap = env_short_wraps() != 0;
     const uint32_t span = short_wrap ? 4u : kRoundSpanMax;
     const uint32_t stamp_wrap = short_wrap ? 5u : 250u;
-    if (narrow) controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap);
-    else controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap);
+    const int32_t cmin = env_compact_min();
+    if (narrow) controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin);
+    else controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin);
     return cudaGetLastError();
 }
 
@@ -1091,7 +1126,7 @@ cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const bool short_wrap = env_short_wraps() != 0;
     controller_batched_kernel<<<152, kCtlThreads, smem, s>>>(one, short_wrap ? 4u : kRoundSpanMax,
-                                                            short_wrap ? 5u : 250u);
+                                                            short_wrap ? 5u : 250u, env_compact_min());
     return cudaGetLastError();
 }
 

@@ -145,7 +145,7 @@ print(json.dumps([st, objs, [s["sweeps"] for s in stats], [g.cpu().tolist() for 
 
 
 @pytest.mark.parametrize("env", [{"DGS_UPDATE_POLICY": "1"}, {"DGS_UPDATE_POLICY": "2"}, {"DGS_CTL_MODE": "0"},
-                                 {"DGS_SHORT_WRAPS": "1"}, {"DGS_EXACT_KEYS": "1"}])
+                                 {"DGS_SHORT_WRAPS": "1"}, {"DGS_EXACT_KEYS": "1"}, {"DGS_CTL_COMPACT_MIN": "1"}])
 def test_batched_internal_paths_agree_with_oracle(env):
     import json
     cases = [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 64, 4)]

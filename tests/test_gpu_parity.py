@@ -249,13 +249,16 @@ print(json.dumps(out))
                                  {"DGS_EVAL_TMA": "1", "DGS_EVAL_STRIP": "0", "DGS_UPDATE_POLICY": "1"},
                                  {"DGS_EVAL_TMA": "1", "DGS_EVAL_STRIP": "8", "DGS_EVAL_ROWS": "4",
                                   "DGS_UPDATE_POLICY": "1"},
-                                 {"DGS_EVAL_TMA": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"}])
+                                 {"DGS_EVAL_TMA": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_CTL_COMPACT_MIN": "1"}, {"DGS_CTL_COMPACT_MIN": "1", "DGS_CTL_MODE": "0"},
+                                 {"DGS_CTL_COMPACT_MIN": "1", "DGS_SHORT_WRAPS": "1"}])
 def test_internal_paths_agree_with_oracle(env):
     """Forcing the full-evaluation or row-task update path, placing the
     controller's scratch in global memory, making its reservation keys and
-    claim stamps wrap every few rounds, disabling the evaluation kernel's
-    packed 32-bit keys, or running it with other launch shapes (rows per
-    thread, strip length), must not change any result."""
+    claim stamps wrap every few rounds, compacting its edge list at every
+    chance, disabling the evaluation kernel's packed 32-bit keys, or running
+    it with other launch shapes (rows per thread, strip length, TMA gathers),
+    must not change any result."""
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
