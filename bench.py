@@ -44,6 +44,9 @@ def parse_args():
     p.add_argument("--n", type=int, default=10000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and served measurements")
+    p.add_argument("--curve", action="store_true",
+                   help="runtime against n on GEOM instances from the random start (the paper's evaluation "
+                        "workload), GPU and oracle, instead of the benchmark line")
     return p.parse_args()
 
 
@@ -52,6 +55,8 @@ def make_input(kind: str, n: int, seed: int):
 
     if kind == "peer":
         return inputs.peer_shaped(n, seed)
+    if kind == "uniform1000":
+        return inputs.uniform(n, 0, 1000, seed)
     return inputs.uniform(n, 0, 10**6, seed)
 
 
@@ -362,6 +367,27 @@ def run_ours(args):
         f"rows{c['rows_per_thread']}_strip{c['strip']}{'_tma' if c['tma'] else ''}": round(c["ms"], 4)
         for c in tuning.get("candidates", [])}
 
+    # the row-owner (A-transpose) form of the same evaluation, on the same
+    # instance: same result, 8n^2 bytes touched against 4n^2 algorithmic
+    try:
+        ro_ms, same = [], True
+        for k in range(3):
+            flush.fill_(k)
+            st_r, sig_r, f_r, stats_r = B.dgs_solve_ex(at, profile=1, evaluation=B.DGS_EVAL_ROW_OWNER)
+            torch.cuda.synchronize(dev)
+            same = same and st_r == B.DGS_OK and f_r == f and stats_r["sweeps"] == stats["sweeps"] and \
+                bool(torch.equal(sig_r, sig))
+            ro_ms.append(stats_r["evaluation_ms"])
+        t_ro = statistics.mean(ro_ms)
+        roofline_row_owner = roofline_entry(
+            "row_owner_evaluation_kernel", "full difference evaluation by row owners (row sigma(j) of a + row j of "
+            "the maintained transpose)", 4 * n * n + 24 * n, t_ro, n, args.workload, peak, peak_src)
+        roofline_row_owner["touched_bytes_per_launch"] = 8 * n * n + 24 * n
+        roofline_row_owner["frac_touched"] = round((8 * n * n + 24 * n) / (t_ro * 1e-3) / 1e9 / peak, 4)
+        roofline_row_owner["solve_equal_to_tile_pairs"] = same
+    except Exception as exc:
+        roofline_row_owner = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tg, te, _ = oracle_sample(a, stats["sweeps"])
@@ -392,7 +418,8 @@ def run_ours(args):
             extra["other_sizes"] = run_other_sizes(dev, measured_hbm_peak()[0])
         except Exception as exc:
             extra["other_sizes"] = {"error": f"{type(exc).__name__}: {exc}"}
-        for key, fn in (("batched", run_batched), ("serving", run_serving)):
+        cpu_every = 32 if (rank == 0 and world == 1 and not args.no_cpu_baseline) else 0
+        for key, fn in (("batched", lambda d: run_batched(d, cpu_every=cpu_every)), ("serving", run_serving)):
             try:
                 extra[key] = fn(dev)
             except Exception as exc:  # reported, never hides the main measurement
@@ -404,7 +431,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": workload_config(args.workload, n, seed),
-        "roofline": roofline, "roofline_evaluation": roofline_eval, "cpu_baseline": cpu,
+        "ms_median": round(statistics.median(step_ms), 4), "ms_best": round(min(step_ms), 4),
+        "roofline": roofline, "roofline_evaluation": roofline_eval,
+        "roofline_evaluation_row_owner": roofline_row_owner, "cpu_baseline": cpu,
         "e2e": {"value": round(job_ms_per_solve(e2e, world), 3), "unit": "ms", "h2d_bytes_per_step": 4 * n * n,
                 "d2h_bytes_per_step": 4 * n},
         "clocks": clocks, "gpu_launches": int(launches),
@@ -422,12 +451,14 @@ def run_ours(args):
 
 # ------------------------------------------------------- the other sizes
 def run_other_sizes(dev, peak, steps=3):
-    """Single solves of the other single-instance configurations: n = 4096
-    peer-shaped (64 MB, fits in L2) and n = 20000 (1.6 GB) peer-shaped and
-    uniform [0, 1e6).  Each result is checked to be a permutation with its
-    exact objective and no improving 2-exchange; the first full evaluation
-    is timed inside the solve."""
-    import numpy as np
+    """Single solves of the other single-instance configurations: n = 256
+    uniform [0, 1000) (latency-bound: microseconds and launches per solve),
+    n = 4096 peer-shaped (64 MB, fits in L2), n = 10000 uniform [0, 1e6) and
+    n = 20000 (1.6 GB) peer-shaped and uniform.  Each result is checked to be a
+    permutation with its exact objective and no improving 2-exchange; the
+    first full evaluation is timed inside the solve.  Where the matrix fits in
+    L2 the evaluation is also stated against the read rate of the matrix
+    itself from L2 (dgs_read_bandwidth)."""
     import torch
 
     from paper_1106_5694_gb300 import binding as B
@@ -435,7 +466,8 @@ def run_other_sizes(dev, peak, steps=3):
     out = []
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    for kind, n in (("peer", 4096), ("peer", 20000), ("uniform", 20000)):
+    l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (126 << 20)
+    for kind, n in (("uniform1000", 256), ("peer", 4096), ("uniform", 10000), ("peer", 20000), ("uniform", 20000)):
         a = make_input(kind, n, 0)
         at = torch.from_numpy(a).to(dev)
         del a
@@ -455,7 +487,7 @@ def run_other_sizes(dev, peak, steps=3):
         ok = ok and best <= 0
         ms, ev = [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for k in range(steps):
+        for k in range(steps if n > 1000 else 20):
             flush.fill_(k)
             e0.record(stream)
             st, sig, f2, stats = B.dgs_solve_ex(at, sigma_out=sig, profile=1)
@@ -464,11 +496,20 @@ def run_other_sizes(dev, peak, steps=3):
             ms.append(e0.elapsed_time(e1))
             ev.append(stats["evaluation_ms"])
         t_ev = statistics.mean(ev)
-        out.append({"workload": f"{kind} n={n}", "ms": round(statistics.mean(ms), 3), "sweeps": stats["sweeps"],
-                    "swaps_applied": stats["swaps_applied"], "objective": f2,
-                    "evaluation_ms": round(t_ev, 4),
-                    "evaluation_frac_of_hbm": round((4 * n * n + 24 * n) / (t_ev * 1e-3) / 1e9 / peak, 4),
-                    "checked": "permutation, exact objective, no improving 2-exchange" if ok else "FAILED"})
+        alg = 4 * n * n + 24 * n
+        row = {"workload": f"{kind.replace('uniform1000', 'uniform [0,1000)')} n={n}",
+               "ms": round(statistics.mean(ms), 4), "ms_median": round(statistics.median(ms), 4),
+               "ms_best": round(min(ms), 4), "kernel_launches": stats["kernel_launches"],
+               "sweeps": stats["sweeps"], "swaps_applied": stats["swaps_applied"], "objective": f2,
+               "evaluation_ms": round(t_ev, 4),
+               "evaluation_frac_of_hbm": round(alg / (t_ev * 1e-3) / 1e9 / peak, 4),
+               "checked": "permutation, exact objective, no improving 2-exchange" if ok else "FAILED"}
+        if 4 * n * n < l2_bytes:
+            st_b, l2_gbs = B.dgs_read_bandwidth(at, repeats=20)
+            if st_b == B.DGS_OK:
+                row["l2_read_gbs_of_matrix"] = round(l2_gbs, 1)
+                row["evaluation_frac_of_l2_read"] = round(alg / (t_ev * 1e-3) / 1e9 / l2_gbs, 4)
+        out.append(row)
         del at
         torch.cuda.empty_cache()
     return out
@@ -484,7 +525,45 @@ def _pool(n_max: int, count: int, seed0: int):
     return [inputs.peer_shaped(n_max, seed0 + k) for k in range(count)]
 
 
-def run_batched(dev, count=1024, lo=64, hi=4096):
+def _oracle_solve_timed(a):
+    """Process-pool worker: one oracle solve (Algorithm 3 from the greedy
+    start) of one instance; returns (seconds, objective)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.dgs_parallel(a)
+    return time.perf_counter() - t0, int(r.objective)
+
+
+def oracle_pool_sample(get, ns, every: int, objs_gpu):
+    """The oracle over a bounded sample (every `every`-th instance) of the
+    batched set (`get(k)`: instance k as a numpy array), as a spawn process
+    pool over all host cores; the solves/s of the whole set is extrapolated
+    by sum n^2 (the oracle's work per sweep)."""
+    import numpy as np
+
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    idx = list(range(0, len(ns), every))
+    cores = os.cpu_count() or 1
+    # a worker that dies raises BrokenProcessPool here instead of stalling
+    with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_solve_timed, [np.zeros((2, 2), np.int32)] * cores))  # workers up, library loaded
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_solve_timed, [get(k) for k in idx]))
+        wall = time.perf_counter() - t0
+    n2_all = sum(int(n) * int(n) for n in ns)
+    n2_sample = sum(int(ns[k]) * int(ns[k]) for k in idx)
+    wall_all = wall * n2_all / n2_sample
+    return {"kind": "oracle", "cores": cores, "sample": f"one instance in every {every} ({len(idx)} of {len(ns)}), "
+            f"spawn process pool; whole-set time extrapolated by sum n^2", "sample_wall_s": round(wall, 2),
+            "cpu_s": round(sum(t for t, _ in res), 2), "value": round(len(ns) / wall_all, 2), "unit": "solves/s",
+            "objectives_equal_to_gpu": all(f == objs_gpu[k] for k, (_, f) in zip(idx, res))}
+
+
+def run_batched(dev, count=1024, lo=64, hi=4096, cpu_every=0):
     """1024 peer-shaped instances, n log-uniform in [64, 4096]: one
     dgs_solve_batched call vs the same instances solved one dgs_solve call at
     a time; inputs resident on the device; every result checked equal."""
@@ -528,7 +607,11 @@ def run_batched(dev, count=1024, lo=64, hi=4096):
         st1, sig1, _ = B.dgs_solve(mats[k])
         same = same and bool(torch.equal(sig1, outs[k]))
     launches = stats[0]["kernel_launches"]
+    cpu = None
+    if cpu_every > 0:
+        cpu = oracle_pool_sample(lambda k: np.ascontiguousarray(pool[k % 4][:ns[k], :ns[k]]), ns, cpu_every, objs)
     return {
+        "cpu_pool_baseline": cpu,
         "workload": f"{count} peer-shaped instances, n log-uniform in [{lo},{hi}] (seeded), one dgs_solve_batched call, "
                     "matrices resident in HBM",
         "instances": count, "sum_n2": int(sum(int(n) * int(n) for n in ns)),
@@ -662,8 +745,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------- runtime against n (Section 4)
+def run_curve(args):
+    """The paper's evaluation workload: GEOM instances (floored distances
+    between random points in [0, 1000]^2), the random start, n = 256 * 2^k.
+    Per n: GPU ms per solve (mean of 5 after warm-up, device events), the
+    oracle's single-threaded ms per solve (measured for n <= 1024, else
+    extrapolated as (1 + sweeps) x one full oracle evaluation), the sweep
+    count, and for n <= 1024 the gap to the optimum (Hungarian method)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1106_5694_gb300 import binding as B
+    from paper_1106_5694_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    B.load()
+    oracle.build()
+    rows = []
+    for n in (256, 512, 1024, 2048, 4096, 8192):
+        a = inputs.geom(n, 1000.0, n)
+        at = torch.from_numpy(a).to(dev)
+        B.dgs_autotune(n, device=dev)
+        for _ in range(3):
+            st, sig, f, stats = B.dgs_solve_ex(at, init=B.DGS_INIT_RANDOM, seed=n)
+        torch.cuda.synchronize(dev)
+        ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(5):
+            e0.record()
+            st, sig, f, stats = B.dgs_solve_ex(at, init=B.DGS_INIT_RANDOM, seed=n)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        row = {"n": n, "gpu_ms": round(statistics.mean(ms), 3), "sweeps": stats["sweeps"], "objective": f,
+               "status": B.dgs_status_string(st)}
+        if n <= 1024:
+            t0 = time.perf_counter()
+            ref = oracle.dgs_parallel(a, init=oracle.INIT_RANDOM, seed=n)
+            row["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 1)
+            row["oracle_ms_kind"] = "measured"
+            row["bit_exact"] = bool(ref.objective == f and np.array_equal(ref.tau, sig.cpu().numpy()))
+            opt = oracle.hungarian(a)[0]
+            row["gap_to_optimum_pct"] = round(100.0 * (opt - f) / opt, 4) if opt else 0.0
+        else:
+            t0 = time.perf_counter()
+            oracle.evaluate_all(a, inputs.random_permutation(n, n))
+            row["oracle_ms"] = round((1 + stats["sweeps"]) * (time.perf_counter() - t0) * 1e3, 1)
+            row["oracle_ms_kind"] = "extrapolated: (1 + sweeps) x one full oracle evaluation"
+        row["oracle_over_gpu"] = round(row["oracle_ms"] / row["gpu_ms"], 1)
+        rows.append(row)
+        del at
+        torch.cuda.empty_cache()
+    print(json.dumps({"curve": "GEOM [0,1000]^2, random start, parallel DGS; runtime per solve", "rows": rows,
+                      "oracle_cores": 1}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.curve:
+        run_curve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -91,6 +91,18 @@ typedef enum {
                               re-evaluating everything) */
 } dgs_reeval_rule;
 
+/* Which kernel runs the full difference evaluations (Algorithm 2 for every
+ * slot).  Both give identical candidates: each is the maximum of the same
+ * gains with the same tie-breaks. */
+typedef enum {
+    DGS_EVAL_TILE_PAIRS = 0,  /* unordered pairs of 64 x 64 tiles of the
+                                 sigma-permuted benefit rows: every benefit is
+                                 read once per evaluation (4 n^2 bytes) */
+    DGS_EVAL_ROW_OWNER = 1    /* one CTA per row j of the gain matrix: row
+                                 sigma(j) of the benefits plus row j of the
+                                 maintained transpose (8 n^2 bytes) */
+} dgs_evaluation_kernel;
+
 typedef struct {
     int32_t init;              /* a dgs_init_mode */
     const int32_t* init_sigma; /* DEVICE, n int32 agent -> job; read for USER */
@@ -112,6 +124,9 @@ typedef struct {
     int32_t algorithm;         /* a dgs_algorithm (default DGS_ALG_PARALLEL);
                                   dgs_solve_batched and the server take
                                   DGS_ALG_PARALLEL only */
+    int32_t evaluation;        /* a dgs_evaluation_kernel (default
+                                  DGS_EVAL_TILE_PAIRS); dgs_solve_batched and
+                                  the server take DGS_EVAL_TILE_PAIRS only */
 } dgs_options;
 
 typedef struct {
@@ -343,6 +358,21 @@ DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_t n, const 
                                        int32_t* agent_gain, int32_t* agent_job,
                                        int32_t* job_gain, int32_t* job_agent,
                                        dgs_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement.
+ *
+ * dgs_read_bandwidth: the rate, in GB/s (1e9 bytes per second), at which the
+ * GPU's SMs read `bytes` bytes at `buffer` (DEVICE, 16-byte aligned, `bytes` a
+ * multiple of 16), averaged over `repeats` back-to-back reads of the whole
+ * buffer after one untimed read; a buffer smaller than L2 is then read from
+ * L2.  The roofline of a difference evaluation whose benefit matrix fits in L2
+ * is this rate on the matrix itself.  Writes *gbs_out; nothing else is
+ * written.  Blocks until the timed reads finish.  Errors: DGS_ERR_INVALID for
+ * a null or unaligned buffer, zero or unaligned size, repeats < 1;
+ * DGS_ERR_CUDA if a launch or the timing failed. */
+DGS_API dgs_status dgs_read_bandwidth(const void* buffer, size_t bytes, int32_t repeats, double* gbs_out,
+                                      dgs_stream_t stream);
 
 /* Human-readable name of a status code (static string). */
 DGS_API const char* dgs_status_string(dgs_status status);

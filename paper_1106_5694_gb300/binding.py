@@ -33,12 +33,14 @@ DGS_REEVAL_BOX = 0
 DGS_REEVAL_ALL = 1
 DGS_ALG_PARALLEL = 0
 DGS_ALG_SEQUENTIAL = 1
+DGS_EVAL_TILE_PAIRS = 0
+DGS_EVAL_ROW_OWNER = 1
 
 EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host", "dgs_evaluate",
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
             "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning",
-            "dgs_submit_ex", "dgs_solve_rect"]
+            "dgs_submit_ex", "dgs_solve_rect", "dgs_read_bandwidth"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -58,6 +60,7 @@ class dgs_options(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("reeval_rule", ctypes.c_int32),
         ("algorithm", ctypes.c_int32),
+        ("evaluation", ctypes.c_int32),
     ]
 
 
@@ -178,6 +181,8 @@ def load():
     lib.dgs_autotune.restype = ctypes.c_int
     lib.dgs_get_tuning.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.dgs_get_tuning.restype = ctypes.c_int
+    lib.dgs_read_bandwidth.argtypes = [P, ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_double), P]
+    lib.dgs_read_bandwidth.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -214,9 +219,10 @@ def dgs_default_options() -> dgs_options:
 
 
 def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0, trace=None, profile=0, seed=0,
-             reeval=DGS_REEVAL_BOX, algorithm=DGS_ALG_PARALLEL):
+             reeval=DGS_REEVAL_BOX, algorithm=DGS_ALG_PARALLEL, evaluation=DGS_EVAL_TILE_PAIRS):
     o = dgs_default_options()
     o.algorithm = int(algorithm)
+    o.evaluation = int(evaluation)
     o.init = init
     o.seed = int(seed)
     o.reeval_rule = int(reeval)
@@ -464,3 +470,15 @@ def dgs_get_tuning(n: int):
     rows, strip, tma = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     st = load().dgs_get_tuning(int(n), ctypes.byref(rows), ctypes.byref(strip), ctypes.byref(tma))
     return st, int(rows.value), int(strip.value), int(tma.value)
+
+
+def dgs_read_bandwidth(buffer: torch.Tensor, repeats: int = 20, stream=None):
+    """dgs_read_bandwidth on a contiguous CUDA tensor (its bytes, rounded down
+    to a multiple of 16): returns (status, GB/s)."""
+    if not (isinstance(buffer, torch.Tensor) and buffer.is_cuda and buffer.is_contiguous()):
+        raise TypeError("buffer must be a contiguous CUDA tensor")
+    nbytes = buffer.numel() * buffer.element_size() // 16 * 16
+    gbs = ctypes.c_double(0.0)
+    st = load().dgs_read_bandwidth(ctypes.c_void_p(buffer.data_ptr()), nbytes, int(repeats), ctypes.byref(gbs),
+                                   _stream(buffer, stream))
+    return st, float(gbs.value)

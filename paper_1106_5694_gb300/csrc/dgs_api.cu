@@ -508,9 +508,11 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
     if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
     if (o.algorithm != DGS_ALG_PARALLEL && o.algorithm != DGS_ALG_SEQUENTIAL) return DGS_ERR_INVALID;
+    if (o.evaluation != DGS_EVAL_TILE_PAIRS && o.evaluation != DGS_EVAL_ROW_OWNER) return DGS_ERR_INVALID;
 
     Solve S(stream);
     DGS_TRY(S.setup(benefit, n, true));
+    S.w.row_owner_eval = o.evaluation == DGS_EVAL_ROW_OWNER ? 1 : 0;
     // the random start is drawn on the host and enters as the caller's start
     DeviceBuffer rnd(stream);
     if (o.init == DGS_INIT_RANDOM) {

@@ -363,7 +363,8 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
     if (options) o = *options;
     if (o.init != DGS_INIT_GREEDY && o.init != DGS_INIT_IDENTITY && o.init != DGS_INIT_RANDOM) return DGS_ERR_INVALID;
     if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
-    if (o.trace_capacity > 0 || o.algorithm != DGS_ALG_PARALLEL) return DGS_ERR_INVALID;
+    if (o.trace_capacity > 0 || o.algorithm != DGS_ALG_PARALLEL || o.evaluation != DGS_EVAL_TILE_PAIRS)
+        return DGS_ERR_INVALID;
     int32_t max_n = 0;
     for (int32_t k = 0; k < count; ++k) {
         if (!benefits[k] || !sigma_outs[k] || ns[k] <= 0 || ns[k] > DGS_BATCH_MAX_N) return DGS_ERR_INVALID;
@@ -831,7 +832,8 @@ dgs_status dgs_submit_ex(dgs_server* sv, const int32_t* benefit, int32_t n, int3
         return DGS_ERR_INVALID;
     if (o.init == DGS_INIT_USER && o.init_sigma == nullptr) return DGS_ERR_INVALID;
     if (o.reeval_rule != DGS_REEVAL_BOX && o.reeval_rule != DGS_REEVAL_ALL) return DGS_ERR_INVALID;
-    if (o.algorithm != DGS_ALG_PARALLEL || o.trace_capacity > 0) return DGS_ERR_INVALID;
+    if (o.algorithm != DGS_ALG_PARALLEL || o.trace_capacity > 0 || o.evaluation != DGS_EVAL_TILE_PAIRS)
+        return DGS_ERR_INVALID;
     const size_t bytes = request_bytes(n);
     if (bytes > sv->budget) return DGS_ERR_BUSY;
     std::lock_guard<std::mutex> lk(sv->mu);

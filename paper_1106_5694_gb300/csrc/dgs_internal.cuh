@@ -98,7 +98,7 @@ struct Workspace {
     uint32_t* g_free_a; uint32_t* g_free_j;  // free sets as bitmaps (persistent greedy)
     uint32_t* g_dirty;                       // owners to rescan this round (persistent greedy)
     int32_t exact_keys;  // 1: never use the packed 32-bit keys (test knob)
-    int32_t pad2;
+    int32_t row_owner_eval;  // 1: full evaluations by row owners (A-transpose form)
     DeviceState* st;
     unsigned long long* phase_ns;  // optional phase timers (DGS_PHASE_TIMERS=1), else null
 };
@@ -343,6 +343,7 @@ int32_t evaluation_strip();
 cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s);
 cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
+cudaError_t launch_row_owner_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
 // Algorithm 1: slots of a fresh evaluation (from the keys, which it clears),
 // and one launch of the single-CTA switching loop (need_update = 1 when the

@@ -644,38 +644,21 @@ __device__ __forceinline__ void mark_rescan_body(const Workspace& w, int32_t bid
 
 __global__ void mark_rescan_kernel(Workspace w) { mark_rescan_body(w, blockIdx.x, gridDim.x); }
 
-// Full re-evaluation of the listed rows: row j of G from row sigma(j) of a
-// and row j of at (gathered through sigma; staged in shared memory by one TMA
-// bulk copy).  Rows of changed jobs also push G[k][j] = G[j][k] into every
-// other row k (the only entries of row k that changed), through the same
-// atomic keys.
-// Row j of G recomputed in full by the CTA (row sigma(j) of a and row j of
-// at, the latter staged in shared memory by one TMA bulk copy when kStage);
-// a changed job's row also pushes G[k][j] = G[j][k] into every other row k.
-// red_a / red_j: 16 entries each.  Returns false (CTA-uniform) if the staged
-// copy did not arrive within the wait limit.
-template <bool kStage>
-__device__ __forceinline__ bool row_task_row(const Workspace& w, int32_t j, int32_t* atrow_s, uint64_t* bar,
-                                             uint32_t& phase, unsigned long long* red_a,
-                                             unsigned long long* red_j) {
+// Row j of G recomputed in full by the CTA from row sigma(j) of a (read
+// directly) and row j of at (`atrow`: global memory, or its copy staged in
+// shared memory), gathered through sigma; its two keys are raised to the row's
+// best.  With `scatter` and j a changed job, the row also pushes G[k][j] =
+// G[j][k] into every other row k (the only entries of row k that changed),
+// through the same atomic keys.  red_a / red_j: 16 entries each.  Ends with
+// a CTA barrier (red_* and the staged row may be reused).
+__device__ __forceinline__ void row_task_compute(const Workspace& w, int32_t j, const int32_t* atrow, bool scatter_ok,
+                                                 unsigned long long* red_a, unsigned long long* red_j) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t n = w.n;
     const int32_t n4 = (n + 3) / 4;
-    const int32_t* atrow = w.at + (size_t)j * w.ldt;
-    if (kStage) {
-        if (tid == 0) {
-            const uint32_t bytes = 16u * (uint32_t)n4;
-            mbar_arrive_expect_tx(bar, bytes);
-            bulk_g2s(atrow_s, atrow, bytes, bar);
-        }
-        const bool ok = mbar_wait_bounded(bar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) return false;
-        atrow = atrow_s;
-    }
     const int32_t sjj = w.sigma[j];
     const int32_t dj = w.diag[j];
-    const bool scatter = w.in_y[j];
+    const bool scatter = scatter_ok && w.in_y[j];
     const int32_t* arow = w.a + (size_t)sjj * w.lda;
     int32_t bg = 0, bc = -1, bs = 0x7fffffff;
 #pragma unroll 2
@@ -722,7 +705,29 @@ __device__ __forceinline__ bool row_task_row(const Workspace& w, int32_t j, int3
             atomicMax(&w.key_j[j], mj);
         }
     }
-    __syncthreads();  // red_* and the staged row are reused by the next row
+    __syncthreads();
+}
+
+// Full re-evaluation of one listed row (row tasks): row j of at staged in
+// shared memory by one TMA bulk copy when kStage.  Returns false (CTA-uniform)
+// if the staged copy did not arrive within the wait limit.
+template <bool kStage>
+__device__ __forceinline__ bool row_task_row(const Workspace& w, int32_t j, int32_t* atrow_s, uint64_t* bar,
+                                             uint32_t& phase, unsigned long long* red_a,
+                                             unsigned long long* red_j) {
+    const int32_t* atrow = w.at + (size_t)j * w.ldt;
+    if (kStage) {
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = 16u * (uint32_t)((w.n + 3) / 4);
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(atrow_s, atrow, bytes, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) return false;
+        atrow = atrow_s;
+    }
+    row_task_compute(w, j, atrow, true, red_a, red_j);
     return true;
 }
 
@@ -758,6 +763,67 @@ __device__ __forceinline__ void row_tasks_body(const Workspace& w, int32_t bid, 
 template <bool kStage>
 __global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
     row_tasks_body<kStage>(w, blockIdx.x, gridDim.x);
+}
+
+// The row-owner form of the full difference evaluation (Algorithm 2 for every
+// slot, the A-transpose variant): CTA b owns rows j = b, b + nblk, ... of G and
+// recomputes each from row sigma(j) of a and row j of the maintained at, with
+// the next row of at already in flight to the second shared-memory stage
+// (TMA bulk copies) while the current row is evaluated.  It touches 8n^2 bytes
+// per evaluation (the tile-pair kernel reads each benefit once, 4n^2) but needs
+// only one key update per row.  Keys are raised with atomicMax, so the result
+// is the tile-pair kernel's: the same maxima with the same tie-breaks.
+template <bool kStage>
+__global__ void __launch_bounds__(512) row_owner_evaluation_kernel(Workspace w, int32_t conditional) {
+    DeviceState* st = w.st;
+    if (st->status != kRunning) return;
+    if (conditional && !(st->need_update && use_full_update(st->rescan_count, w.n, st->update_policy))) return;
+    if (conditional && blockIdx.x == 0 && threadIdx.x == 0) st->full_evals += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ unsigned long long red_a[16], red_j[16];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int32_t n = w.n;
+    const uint32_t bytes = 16u * (uint32_t)((n + 3) / 4);
+    int32_t* const stage0 = reinterpret_cast<int32_t*>(smem_raw);  // stage b at stage0 + b * ldt
+    if (kStage && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int32_t j = blockIdx.x;
+    if (kStage && threadIdx.x == 0 && j < n) {
+        mbar_arrive_expect_tx(&bar[0], bytes);
+        bulk_g2s(stage0, w.at + (size_t)j * w.ldt, bytes, &bar[0]);
+    }
+    uint32_t phase = 0;  // bit b: parity of stage b's next completion
+    for (int32_t it = 0; j < n; ++it, j += gridDim.x) {
+        const int b = it & 1;
+        const int32_t* atrow = w.at + (size_t)j * w.ldt;
+        if (kStage) {
+            // the other stage was last read by the previous row, which ended
+            // with a CTA barrier: it is free for the next row's copy
+            const int32_t jn = j + (int32_t)gridDim.x;
+            if (threadIdx.x == 0 && jn < n) {
+                mbar_arrive_expect_tx(&bar[b ^ 1], bytes);
+                bulk_g2s(stage0 + (b ^ 1) * w.ldt, w.at + (size_t)jn * w.ldt, bytes, &bar[b ^ 1]);
+            }
+            const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+            phase ^= 1u << b;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    st->error = kErrWaitTimeout;
+                    st->status = kError;
+                    // the next row's copy may still be in flight into this CTA's
+                    // shared memory: wait for it (bounded) before leaving
+                    if (jn < n) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+                }
+                return;
+            }
+            atrow = stage0 + b * w.ldt;
+        }
+        row_task_compute(w, j, atrow, false, red_a, red_j);
+    }
 }
 
 // tau given (greedy result, identity or the caller's permutation): build
@@ -1065,6 +1131,25 @@ cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s) {
         row_tasks_kernel<true><<<grid, 512, smem, s>>>(w);
     } else {
         row_tasks_kernel<false><<<grid, 512, 0, s>>>(w);
+    }
+    return cudaGetLastError();
+}
+
+// Two stages of one row of at each: up to 27 * 1024 columns (216 KB).
+constexpr int32_t kRowOwnerStageMaxN = 27 * 1024;
+
+cudaError_t launch_row_owner_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s) {
+    if (w.n <= kRowOwnerStageMaxN) {
+        const size_t smem = 2 * 4 * (size_t)w.ldt;
+        if (smem > 48 * 1024) {
+            cudaError_t e =
+                ensure_smem_limit(reinterpret_cast<const void*>(row_owner_evaluation_kernel<true>), 12, smem);
+            if (e != cudaSuccess) return e;
+        }
+        const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+        row_owner_evaluation_kernel<true><<<152 * per_sm, 512, smem, s>>>(w, conditional);
+    } else {
+        row_owner_evaluation_kernel<false><<<152 * 2, 512, 0, s>>>(w, conditional);
     }
     return cudaGetLastError();
 }

@@ -708,6 +708,7 @@ cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional
 }
 
 cudaError_t launch_full_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s) {
+    if (w.row_owner_eval) return launch_row_owner_evaluation(w, conditional, s);
     return launch_full_evaluation_shape(w, conditional, evaluation_shape(w.n), s);
 }
 

@@ -59,3 +59,21 @@ def test_reference_arm_prints_nothing_on_other_ranks():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_oracle_pool_sample_on_host_cores():
+    """The batched CPU baseline: a spawn process pool of oracle solves over
+    a sample, extrapolated to the whole set by sum n^2."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1106_5694_gb300 import inputs
+    ns = [30, 50, 70, 90]
+    mats = [inputs.peer_shaped(n, 40 + k) for k, n in enumerate(ns)]
+    objs = [int(oracle.dgs_parallel(m).objective) for m in mats]
+    r = bench.oracle_pool_sample(lambda k: mats[k], ns, 2, objs)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["objectives_equal_to_gpu"]
+    assert r["value"] > 0 and "(2 of 4)" in r["sample"]  # instances 0 and 2
+    wrong = list(objs)
+    wrong[2] += 1
+    assert not bench.oracle_pool_sample(lambda k: mats[k], ns, 2, wrong)["objectives_equal_to_gpu"]

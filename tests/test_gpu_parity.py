@@ -229,10 +229,27 @@ from paper_1106_5694_gb300 import binding as B, inputs
 out = []
 for kind, n, seed in {cases!r}:
     a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
-    st, sig, f, stats = B.dgs_solve_ex(torch.from_numpy(a).cuda())
+    st, sig, f, stats = B.dgs_solve_ex(torch.from_numpy(a).cuda(), evaluation={evaluation!r})
     out.append([st, f, stats["sweeps"], sig.cpu().tolist()])
 print(json.dumps(out))
 """
+
+
+def _run_knob_cases(env, evaluation=0):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cases = [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 640, 4)]
+    code = _KNOB_SCRIPT.format(root=root, cases=cases, evaluation=evaluation)
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **env), capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    for (kind, n, seed), (st, f, sweeps, tau) in zip(cases, got):
+        a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
+        ref = oracle.dgs_parallel(a)
+        assert st == B.DGS_OK and f == ref.objective and sweeps == ref.sweeps
+        assert tau == ref.tau.tolist()
 
 
 @pytest.mark.parametrize("env", [{"DGS_UPDATE_POLICY": "1"}, {"DGS_UPDATE_POLICY": "2"},
@@ -259,20 +276,86 @@ def test_internal_paths_agree_with_oracle(env):
     chance, disabling the evaluation kernel's packed 32-bit keys, or running
     it with other launch shapes (rows per thread, strip length, TMA gathers),
     must not change any result."""
-    import subprocess
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    cases = [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 640, 4)]
-    code = _KNOB_SCRIPT.format(root=root, cases=cases)
-    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **env), capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 0, r.stderr
-    got = json.loads(r.stdout.strip().splitlines()[-1])
-    for (kind, n, seed), (st, f, sweeps, tau) in zip(cases, got):
-        a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
-        ref = oracle.dgs_parallel(a)
-        assert st == B.DGS_OK and f == ref.objective and sweeps == ref.sweeps
-        assert tau == ref.tau.tolist()
+    _run_knob_cases(env)
+
+
+# ------------------------- the row-owner (A-transpose) evaluation kernel
+ROW_OWNER_CASES = [(k, n, 0) for k in ("uniform", "ties", "peer", "wide") for n in (1, 2, 3, 5, 63, 65, 130, 257)] + \
+                  [("peer", 1000, 1), ("uniform", 777, 2), ("geom", 300, 3)]
+
+
+@pytest.mark.parametrize("kind,n,seed", ROW_OWNER_CASES)
+def test_row_owner_evaluation_matches_oracle(kind, n, seed):
+    """Every full evaluation by the row-owner kernel: the solve, its trace and
+    its sweep count equal the oracle's."""
+    a = _make(kind, n, seed)
+    ref = oracle.dgs_parallel(a, trace_cap=100000)
+    tr = _trace_tensors(max(ref.sweeps, 1))
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), trace=tr, evaluation=B.DGS_EVAL_ROW_OWNER)
+    assert st == B.DGS_OK, B.dgs_status_string(st)
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective and stats["sweeps"] == ref.sweeps and stats["swaps_applied"] == ref.swaps_applied
+    k = ref.sweeps
+    np.testing.assert_array_equal(tr[0][:k].cpu().numpy(), ref.trace_accepted)
+    np.testing.assert_array_equal(tr[2][:k].cpu().numpy(), ref.trace_objective)
+
+
+def test_row_owner_evaluation_other_starts_rules_and_sequential():
+    a = _make("peer", 200, 9)
+    for kw, okw in (({"init": B.DGS_INIT_RANDOM, "seed": 5}, {"init": oracle.INIT_RANDOM, "seed": 5}),
+                    ({"reeval": B.DGS_REEVAL_ALL}, {"reeval": oracle.REEVAL_ALL})):
+        ref = oracle.dgs_parallel(a, **okw)
+        st, sig, f, stats = B.dgs_solve_ex(_cuda(a), evaluation=B.DGS_EVAL_ROW_OWNER, **kw)
+        assert st == B.DGS_OK
+        np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+        assert f == ref.objective and stats["sweeps"] == ref.sweeps
+    ref = oracle.dgs_sequential(a)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), algorithm=B.DGS_ALG_SEQUENTIAL, evaluation=B.DGS_EVAL_ROW_OWNER)
+    assert st == B.DGS_OK
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective
+
+
+@pytest.mark.parametrize("env", [{"DGS_UPDATE_POLICY": "1"}, {"DGS_UPDATE_POLICY": "1", "DGS_CTL_MODE": "0"}, {}])
+def test_row_owner_evaluation_update_paths_agree_with_oracle(env):
+    """The row-owner kernel also runs the conditional full re-evaluations
+    (forced after every commit by DGS_UPDATE_POLICY=1)."""
+    _run_knob_cases(env, evaluation=B.DGS_EVAL_ROW_OWNER)
+
+
+def _best_exchange_gain_blocked(at, sig, block=2048):
+    """max over agent pairs of the 2-exchange gain (row blocks, int64)."""
+    n = at.shape[0]
+    s64 = sig.long()
+    d = at[torch.arange(n, device=at.device), s64].long()
+    best = -(1 << 62)
+    for r0 in range(0, n, block):
+        cross = at[r0:r0 + block][:, s64].long()
+        back = at[:, s64[r0:r0 + block]].long().T
+        g = cross + back - d[r0:r0 + block, None] - d[None, :]
+        best = max(best, int(g.max().item()))
+    return best
+
+
+def test_row_owner_unstaged_rows_agree_with_tile_pairs():
+    """n = 28000: a row of the transpose is too long for two shared-memory
+    stages, so the row-owner kernel gathers it from global memory.  The solve
+    equals the tile-pair solve (itself bit-exact with the oracle at every size
+    the oracle reaches) and is a 2-exchange local optimum with its exact
+    objective."""
+    n = 28000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    at = torch.randint(0, 10**6, (n, n), dtype=torch.int32, device="cuda", generator=g)
+    st1, sig1, f1, s1 = B.dgs_solve_ex(at)
+    st2, sig2, f2, s2 = B.dgs_solve_ex(at, evaluation=B.DGS_EVAL_ROW_OWNER)
+    assert st1 == B.DGS_OK and st2 == B.DGS_OK
+    assert torch.equal(sig1, sig2) and f1 == f2 and s1["sweeps"] == s2["sweeps"]
+    assert torch.equal(torch.sort(sig2.long()).values, torch.arange(n, device="cuda"))
+    assert f2 == int(at[torch.arange(n, device="cuda"), sig2.long()].long().sum().item())
+    assert _best_exchange_gain_blocked(at, sig2) <= 0
+    del at
+    torch.cuda.empty_cache()
 
 
 # ------------------- the paper's random start and the re-evaluate-all rule
@@ -324,6 +407,8 @@ def test_invalid_rule_and_start_rejected():
     a = _cuda(_make("uniform", 20, 0))
     assert B.dgs_solve_ex(a, reeval=7)[0] == B.DGS_ERR_INVALID
     assert B.dgs_solve_ex(a, init=9)[0] == B.DGS_ERR_INVALID
+    assert B.dgs_solve_ex(a, evaluation=2)[0] == B.DGS_ERR_INVALID
+    assert B.dgs_solve_batched([a], evaluation=B.DGS_EVAL_ROW_OWNER)[0] == B.DGS_ERR_INVALID
 
 
 # --------------------------------------------- Algorithm 1 (sequential DGS)
