@@ -216,7 +216,7 @@ DGS_API dgs_status dgs_greedy_init(const int32_t* benefit, int32_t n, int32_t* s
 #define DGS_TUNE_MAX_CANDIDATES 16
 typedef struct {
     int32_t n_lo, n_hi;       /* the size class the result applies to */
-    int32_t rows_per_thread;  /* chosen: 4 (1024-thread CTAs) or 8 (512) */
+    int32_t rows_per_thread;  /* chosen: 4 (1024-thread CTAs), 8 (512) or 16 (256) */
     int32_t strip;            /* chosen: column tiles per work item, 0 = one
                                  contiguous, equal range of tiles per CTA */
     double best_ms;           /* evaluation time of the chosen shape */

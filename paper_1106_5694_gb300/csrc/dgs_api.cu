@@ -747,14 +747,15 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
         if (st == DGS_OK && (e = launch_range_check(S.w, s)) != cudaSuccess) st = cuda_fail(e, "range check");
         if (st == DGS_OK && (e = launch_start_from_tau(S.w, sigma, DGS_INIT_USER, S.seen, s)) != cudaSuccess)
             st = cuda_fail(e, "start");
-        // candidate shapes: 8 rows per thread with every strip (0: contiguous
-        // balanced ranges), with and without TMA gathers; 4 rows per thread
-        // with two strips
+        // candidate shapes: 8 and 16 rows per thread with every strip (0:
+        // contiguous balanced ranges), 4 rows per thread with two strips, and
+        // the TMA-gather variants of 8 and 4 rows with two strips and one
         std::vector<EvalShape> shapes;
-        for (int32_t tma = 0; tma < 2; ++tma) {
-            for (int32_t strip : {0, 4, 8, 16, 32, 64}) shapes.push_back(EvalShape{8, strip, tma});
-            for (int32_t strip : {0, 32}) shapes.push_back(EvalShape{4, strip, tma});
-        }
+        for (int32_t strip : {0, 4, 8, 16, 32, 64}) shapes.push_back(EvalShape{8, strip, 0});
+        for (int32_t strip : {0, 8, 16, 32, 64}) shapes.push_back(EvalShape{16, strip, 0});
+        for (int32_t strip : {0, 32}) shapes.push_back(EvalShape{4, strip, 0});
+        for (int32_t strip : {0, 32}) shapes.push_back(EvalShape{8, strip, 1});
+        shapes.push_back(EvalShape{4, 0, 1});
         dgs_tuning r{};
         r.best_ms = 1e30;
         EventPair ev;

@@ -212,32 +212,64 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             s_round = 0;
             s_stamp = 0;
         }
-        // slots t = c * 1024 + tid, chunk by chunk in priority order; the
-        // slot words of several chunks are loaded before they are scanned
-        int32_t base = 0;
-        for (int32_t c0 = 0; c0 < 2 * n; c0 += 4 * kCtlThreads) {
+        // Warp wp lists the slots of its own range [lo, hi) (ranges are
+        // multiples of 32 long and ascend with wp): it counts its edges,
+        // the 32 warp counts are scanned once, and it writes its edges at
+        // its offset, so positions follow slot order (the priority order).
+        constexpr int kWarps = kCtlThreads / 32;
+        const int32_t lane = tid & 31, wp = tid >> 5;
+        const int32_t per = (2 * n + 32 * kWarps - 1) / (32 * kWarps) * 32;
+        const int32_t lo = wp * per, hi = min(2 * n, lo + per);
+        int32_t cnt = 0;
+        for (int32_t t0 = lo; t0 < hi; t0 += 4 * 32) {
             unsigned long long ew[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int32_t t = c0 + k * kCtlThreads + tid;
-                ew[k] = t < 2 * n ? w.sl_edge[t] : 0ull;
+                const int32_t t = t0 + k * 32 + lane;
+                ew[k] = t < hi ? w.sl_edge[t] : 0ull;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cnt += __popc(__ballot_sync(0xffffffffu, ew[k] != 0ull));
+        }
+        if (lane == 0) warp_sums[wp] = cnt;
+        __syncthreads();
+        if (wp == 0) {
+            const int32_t v = warp_sums[lane];
+            int32_t incl = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += o;
+            }
+            warp_sums[lane] = incl - v;
+            if (lane == 31) warp_sums[32] = incl;
+        }
+        __syncthreads();
+        int32_t pos0 = warp_sums[wp];
+        const uint32_t below = (1u << lane) - 1u;
+        for (int32_t t0 = lo; t0 < hi; t0 += 4 * 32) {
+            unsigned long long ew[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t t = t0 + k * 32 + lane;
+                ew[k] = t < hi ? w.sl_edge[t] : 0ull;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int32_t t = c0 + k * kCtlThreads + tid;
-                const int32_t has = ew[k] != 0ull;
-                int32_t total;
-                const int32_t pos = base + block_scan(has, warp_sums, &total);
+                const int32_t t = t0 + k * 32 + lane;
+                const bool has = ew[k] != 0ull;
+                const uint32_t m = __ballot_sync(0xffffffffu, has);
                 if (has) {
+                    const int32_t pos = pos0 + __popc(m & below);
                     w.ctl_slot[pos] = t;
                     if (slot_s) slot_s[pos] = (uint16_t)t;
                     E[pos] = C::make(edge_u(ew[k]), edge_v(ew[k]));
                     estate[pos] = kAlive | ((ew[k] & kApplies) ? kAppl : 0);
                 }
-                base += total;
+                pos0 += __popc(m);
             }
         }
-        if (tid == 0) { s_L = base; s_live = base; }
+        if (tid == 0) { s_L = warp_sums[32]; s_live = warp_sums[32]; }
         __syncthreads();
     }
     DGS_CT(kPtCtlEntry)
@@ -483,9 +515,18 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                 atomicAdd(&s_app, my_app);
                 atomicAdd(&s_gain, (unsigned long long)my_gain);
             }
-            for (int32_t i = tid; i < n; i += kCtlThreads) {
-                w.in_ca[i] = 0;
-                w.in_cj[i] = 0;
+            if (((reinterpret_cast<uintptr_t>(w.in_ca) | reinterpret_cast<uintptr_t>(w.in_cj)) & 15) == 0) {
+                // both arrays hold round_up(n, 128) bytes: clear them in 16-byte words
+                const int32_t n16 = (n + 15) / 16;
+                for (int32_t i = tid; i < n16; i += kCtlThreads) {
+                    reinterpret_cast<uint4*>(w.in_ca)[i] = make_uint4(0, 0, 0, 0);
+                    reinterpret_cast<uint4*>(w.in_cj)[i] = make_uint4(0, 0, 0, 0);
+                }
+            } else {
+                for (int32_t i = tid; i < n; i += kCtlThreads) {
+                    w.in_ca[i] = 0;
+                    w.in_cj[i] = 0;
+                }
             }
             __syncthreads();
             // record C: every live slot that was not accepted keeps its
@@ -493,7 +534,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             for (int32_t p = tid; p < L; p += kCtlThreads) {
                 const uint8_t es = estate[p];
                 if (!(es & kAlive) || (es & kAccBit)) continue;
-                const int32_t t = w.ctl_slot[p];
+                const int32_t t = slot_s ? (int32_t)slot_s[p] : w.ctl_slot[p];
                 if (t < n) w.in_ca[t] = 1;
                 else w.in_cj[t - n] = 1;
             }

@@ -37,7 +37,10 @@ namespace {
 
 constexpr int kT = 64;         // tile edge
 constexpr int kYP = kT + 4;    // Y row pitch (ints): 16-B aligned and int4-conflict-free
-constexpr int kStages = 5;
+// Pipeline depth: 5 stages of 34 KB (a sixth, which fits beside the column
+// buffers of 8 or 16 rows per thread, measured no faster: the kernel is
+// bound by instruction issue before it is by bytes in flight).
+constexpr int stages_for(int) { return 5; }
 
 // Thread geometry for kRows rows per thread: kThreads = 64 columns x
 // (64 / kRows) row groups; each thread copies kCopies row segments of X and
@@ -315,7 +318,19 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPa
         const int32_t* xrow = stage->x + (ty * kRows) * kT + tx;
         const int4* yrow = reinterpret_cast<const int4*>(stage->y + tx * kYP + ty * kRows);
         if (kPacked) {
-            const int32_t cka = pk.mask - k, ckj = pk.mask - sk;
+            // With h = X + Y - D[jr] (so g = h - D[k]) every key is h * 2^s
+            // plus a constant: the row-side constants fold -D[k] * 2^s in
+            // once per tile, and the column side subtracts it once after its
+            // maximum over the rows (a common shift commutes with max).  The
+            // products and sums are formed modulo 2^32; every key compared is
+            // exactly g * 2^s + offset, which fits in int32 by the packing
+            // bound, and the column-side partial maxima exceed it by at most
+            // D[k] * 2^s < 2^28.  The rows' column-side terms are reduced as a
+            // tree (depth log2 kRows instead of a kRows-long chain).
+            const uint32_t pw = (uint32_t)pk.pw;
+            const uint32_t dks = (uint32_t)dk * pw;
+            const uint32_t cka = (uint32_t)(pk.mask - k) - dks, ckj = (uint32_t)(pk.mask - sk) - dks;
+            int32_t ta[kRows], tj[kRows];
 #pragma unroll
             for (int q = 0; q < kRows / 4; ++q) {
                 const int4 y4 = yrow[q];
@@ -323,14 +338,28 @@ __device__ __forceinline__ void compute_tile(const Stage* stage, Rows<kRows, kPa
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int r = q * 4 + e;
-                    if (kRagged && J0 + ty * kRows + r >= n) continue;
-                    const int32_t g = xrow[r * kT] + yv[e] - (rs.d[r] + dk);
-                    const int32_t gs = g * pk.pw;
-                    rs.g[r] = max(rs.g[r], gs + cka);  // row jr, lowest column
-                    rs.s[r] = max(rs.s[r], gs + ckj);  // row jr, lowest partner agent
-                    ca = max(ca, gs + rs.ca[r]);       // row k, lowest column
-                    cj = max(cj, gs + rs.cj[r]);       // row k, lowest partner agent
+                    if (kRagged && J0 + ty * kRows + r >= n) {
+                        ta[r] = tj[r] = INT32_MIN;
+                        continue;
+                    }
+                    const uint32_t hs = (uint32_t)(xrow[r * kT] + yv[e] - rs.d[r]) * pw;
+                    rs.g[r] = max(rs.g[r], (int32_t)(hs + cka));  // row jr, lowest column
+                    rs.s[r] = max(rs.s[r], (int32_t)(hs + ckj));  // row jr, lowest partner agent
+                    ta[r] = (int32_t)(hs + (uint32_t)rs.ca[r]);   // row k, lowest column (+ D[k] 2^s)
+                    tj[r] = (int32_t)(hs + (uint32_t)rs.cj[r]);   // row k, lowest partner agent (+ D[k] 2^s)
                 }
+            }
+#pragma unroll
+            for (int h = kRows / 2; h >= 1; h /= 2) {
+#pragma unroll
+                for (int r = 0; r < h; ++r) {
+                    ta[r] = max(ta[r], ta[r + h]);
+                    tj[r] = max(tj[r], tj[r + h]);
+                }
+            }
+            if (!kRagged || ta[0] != INT32_MIN) {
+                ca = max(ca, (int32_t)((uint32_t)ta[0] - dks));
+                cj = max(cj, (int32_t)((uint32_t)tj[0] - dks));
             }
         } else {
             int32_t cg = 0, cc = -1, cs = 0x7fffffff;
@@ -440,7 +469,7 @@ __device__ __forceinline__ void commit_rows(const Rows<kRows, kPacked>& rs, int3
 
 template <int kRows>
 constexpr size_t eval_smem_bytes() {
-    return sizeof(Stage) * kStages + 2 * 2 * Geo<kRows>::kGroups * kT * sizeof(unsigned long long);
+    return sizeof(Stage) * stages_for(kRows) + 2 * 2 * Geo<kRows>::kGroups * kT * sizeof(unsigned long long);
 }
 
 // The tile loop of one block of one instance's evaluation.  kTma: the X
@@ -450,6 +479,7 @@ template <int kRows, bool kPacked, bool kTma>
 __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t strip, int32_t bid, int32_t nblk,
                                                 const Packing& pk, const CUtensorMap* tm) {
     constexpr int kGroups = Geo<kRows>::kGroups;
+    constexpr int kStages = stages_for(kRows);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* stages = reinterpret_cast<Stage*>(smem_raw);
     unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(Stage) * kStages);
@@ -641,9 +671,10 @@ EvalShape evaluation_shape(int32_t n) {
     EvalShape sh{8, kStrip, 0};
     const int32_t v = g_shape[size_bucket(n)].load(std::memory_order_relaxed);
     if (v != 0) sh = EvalShape{(v >> 8) & 255, v & 255, v >> 16};
-    if (env_rows == 4 || env_rows == 8) sh.rows = env_rows;
+    if (env_rows == 4 || env_rows == 8 || env_rows == 16) sh.rows = env_rows;
     if (env_strip >= 0 && env_strip <= 255) sh.strip = env_strip;
     if (env_tma == 0 || env_tma == 1) sh.tma = env_tma;
+    if (sh.rows == 16) sh.tma = 0;  // 16 rows per thread: per-thread copies only
     return sh;
 }
 
@@ -691,7 +722,7 @@ template <int kRows, bool kTma>
 static cudaError_t launch_eval(const Workspace& w, int32_t conditional, int32_t strip, const CUtensorMap& tm,
                                cudaStream_t s) {
     constexpr size_t smem = eval_smem_bytes<kRows>();
-    const int slot = kRows == 8 ? (kTma ? 11 : 0) : (kTma ? 10 : 7);  // attribute cache slots
+    const int slot = kRows == 16 ? 13 : kRows == 8 ? (kTma ? 11 : 0) : (kTma ? 10 : 7);  // attribute cache slots
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel<kRows, kTma>), slot, smem);
     if (e != cudaSuccess) return e;
     full_evaluation_kernel<kRows, kTma><<<152, Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip, tm);
@@ -701,6 +732,7 @@ static cudaError_t launch_eval(const Workspace& w, int32_t conditional, int32_t 
 cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional, EvalShape sh, cudaStream_t s) {
     alignas(64) CUtensorMap tm{};
     const bool tma = sh.tma && make_gather_map(w, &tm);
+    if (sh.rows == 16) return launch_eval<16, false>(w, conditional, sh.strip, tm, s);
     if (sh.rows == 4) return tma ? launch_eval<4, true>(w, conditional, sh.strip, tm, s)
                                  : launch_eval<4, false>(w, conditional, sh.strip, tm, s);
     return tma ? launch_eval<8, true>(w, conditional, sh.strip, tm, s)

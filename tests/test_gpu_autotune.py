@@ -24,7 +24,7 @@ def _built():
 def test_autotune_picks_a_shape_and_solves_stay_exact(n):
     st, r = B.dgs_autotune(n)
     assert st == B.DGS_OK, B.dgs_last_cuda_error()
-    assert r["rows_per_thread"] in (4, 8) and r["strip"] >= 0
+    assert r["rows_per_thread"] in (4, 8, 16) and r["strip"] >= 0
     assert r["n_lo"] <= n <= r["n_hi"]
     assert len(r["candidates"]) >= 6 and all(c["ms"] > 0 for c in r["candidates"])
     assert r["best_ms"] == min(c["ms"] for c in r["candidates"])

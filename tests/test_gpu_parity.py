@@ -267,6 +267,10 @@ def _run_knob_cases(env, evaluation=0):
                                  {"DGS_EVAL_TMA": "1", "DGS_EVAL_STRIP": "8", "DGS_EVAL_ROWS": "4",
                                   "DGS_UPDATE_POLICY": "1"},
                                  {"DGS_EVAL_TMA": "1", "DGS_EXACT_KEYS": "1", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_ROWS": "16", "DGS_EVAL_STRIP": "0", "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_ROWS": "16", "DGS_EVAL_STRIP": "3", "DGS_EXACT_KEYS": "1",
+                                  "DGS_UPDATE_POLICY": "1"},
+                                 {"DGS_EVAL_ROWS": "16", "DGS_EVAL_STRIP": "32"},
                                  {"DGS_CTL_COMPACT_MIN": "1"}, {"DGS_CTL_COMPACT_MIN": "1", "DGS_CTL_MODE": "0"},
                                  {"DGS_CTL_COMPACT_MIN": "1", "DGS_SHORT_WRAPS": "1"}])
 def test_internal_paths_agree_with_oracle(env):
