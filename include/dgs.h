@@ -374,6 +374,19 @@ DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_t n, const 
 DGS_API dgs_status dgs_read_bandwidth(const void* buffer, size_t bytes, int32_t repeats, double* gbs_out,
                                       dgs_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Device memory.
+ *
+ * The calls that allocate per call (dgs_solve*, dgs_evaluate, dgs_greedy_init,
+ * dgs_autotune, dgs_solve_batched, the server's per-request workspaces) take
+ * their device memory from the library's own stream-ordered pool on the
+ * current device, which keeps freed memory cached for the next call instead of
+ * returning it to the device (back-to-back solves then reuse their workspace
+ * instead of mapping it again).  dgs_release_cached_memory returns every
+ * cached byte of those pools to the device; memory still in use by a call in
+ * flight stays with it.  Errors: DGS_ERR_CUDA if a trim failed. */
+DGS_API dgs_status dgs_release_cached_memory(void);
+
 /* Human-readable name of a status code (static string). */
 DGS_API const char* dgs_status_string(dgs_status status);
 

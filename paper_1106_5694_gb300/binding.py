@@ -40,7 +40,8 @@ EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host"
             "dgs_evaluate_static", "dgs_greedy_init", "dgs_status_string", "dgs_last_cuda_error",
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
             "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning",
-            "dgs_submit_ex", "dgs_solve_rect", "dgs_read_bandwidth"]
+            "dgs_submit_ex", "dgs_solve_rect", "dgs_read_bandwidth",
+            "dgs_release_cached_memory"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -183,6 +184,8 @@ def load():
     lib.dgs_get_tuning.restype = ctypes.c_int
     lib.dgs_read_bandwidth.argtypes = [P, ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_double), P]
     lib.dgs_read_bandwidth.restype = ctypes.c_int
+    lib.dgs_release_cached_memory.argtypes = []
+    lib.dgs_release_cached_memory.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -482,3 +485,8 @@ def dgs_read_bandwidth(buffer: torch.Tensor, repeats: int = 20, stream=None):
     st = load().dgs_read_bandwidth(ctypes.c_void_p(buffer.data_ptr()), nbytes, int(repeats), ctypes.byref(gbs),
                                    _stream(buffer, stream))
     return st, float(gbs.value)
+
+
+def dgs_release_cached_memory() -> int:
+    """dgs_release_cached_memory: returns the status."""
+    return int(load().dgs_release_cached_memory())

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <algorithm>
 #include <vector>
 
@@ -44,6 +45,42 @@ int32_t env_phase_timers() {
     }();
     return v;
 }
+// One pool per device, created on first use.  Back-to-back solves free and
+// allocate workspaces of the same size; with the default pool (release
+// threshold 0) the memory is unmapped at every synchronisation and mapped
+// again by the next call, which cost about 0.5 ms per n = 10000 solve.
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[64] = {};
+
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        if (g_pools[dev] == nullptr) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t created = nullptr;
+            e = cudaMemPoolCreate(&created, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(created);
+                return e;
+            }
+            g_pools[dev] = created;
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 int32_t env_compact_min() {
     static const int32_t v = [] {
         const char* e = std::getenv("DGS_CTL_COMPACT_MIN");
@@ -238,14 +275,14 @@ struct Solve {
         Workspace tmp{};
         carve(sizing, tmp, plan, n, &ctl, &seen, &a_copy);
         plan.bytes = sizing.used;
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
+        cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&ar.base), plan.bytes, s);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
             snprintf(g_last_error, sizeof(g_last_error), "workspace of %zu bytes", plan.bytes);
             ar.base = nullptr;
             return DGS_ERR_OOM;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        if (e != cudaSuccess) return cuda_fail(e, "device allocation");
         ar.size = plan.bytes;
         carve(ar, w, plan, n, &ctl, &seen, &a_copy);
         w.n = n;
@@ -317,13 +354,13 @@ struct DeviceBuffer {
         if (p) cudaFreeAsync(p, s);
     }
     dgs_status alloc(size_t bytes) {
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        cudaError_t e = pool_malloc_async(&p, bytes, s);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
             p = nullptr;
             return DGS_ERR_OOM;
         }
-        return e == cudaSuccess ? DGS_OK : cuda_fail(e, "cudaMallocAsync");
+        return e == cudaSuccess ? DGS_OK : cuda_fail(e, "device allocation");
     }
 };
 
@@ -629,12 +666,12 @@ dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n, int32_t* sigma
     const size_t abytes = (size_t)n * n * sizeof(int32_t);
     const size_t obytes = align_up((size_t)n * sizeof(int32_t), 256);
     char* buf = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), abytes + obytes, s);
+    cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&buf), abytes + obytes, s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return DGS_ERR_OOM;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     int32_t* a_dev = reinterpret_cast<int32_t*>(buf + obytes);
     int32_t* out_dev = reinterpret_cast<int32_t*>(buf);
     dgs_status st = DGS_OK;
@@ -715,12 +752,12 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
     const int32_t lda = round_up32(n, 4);
     int32_t* buf = nullptr;
     const size_t abytes = (size_t)n * lda * sizeof(int32_t);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), abytes + align_up((size_t)n * 4, 256), s);
+    cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&buf), abytes + align_up((size_t)n * 4, 256), s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return DGS_ERR_OOM;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     int32_t* a = buf;
     int32_t* sigma = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(buf) + abytes);
     dgs_status st = DGS_OK;
@@ -829,3 +866,14 @@ const char* dgs_status_string(dgs_status status) {
 const char* dgs_last_cuda_error(void) { return g_last_error; }
 
 }  // extern "C"
+
+extern "C" dgs_status dgs_release_cached_memory(void) {
+    std::lock_guard<std::mutex> lock(dgs::g_pool_mutex);
+    dgs_status st = DGS_OK;
+    for (int d = 0; d < 64; ++d) {
+        if (dgs::g_pools[d] == nullptr) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(dgs::g_pools[d], 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemPoolTrimTo");
+    }
+    return st;
+}

@@ -405,7 +405,7 @@ extern "C" dgs_status dgs_solve_batched(const int32_t* const* benefits, const in
     const size_t ws_total = total;
     total += starts.size() * sizeof(int32_t);
     char* mem = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), total, s);
+    cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&mem), total, s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         cudaEventDestroy(ev);
@@ -576,7 +576,7 @@ struct dgs_server {
             }
             const int64_t t0 = now_ns();
             char* mem = nullptr;
-            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), r.bytes, up);
+            cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&mem), r.bytes, up);
             if (e == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
                 cudaGetLastError();
                 Result res{};

@@ -412,6 +412,10 @@ int32_t env_controller_mode_cap();
 // tests reach their wrap-around paths.
 int32_t env_short_wraps();
 int32_t env_phase_timers();
+// Stream-ordered allocation from the library's own memory pool on the current
+// device.  The pool keeps memory freed by cudaFreeAsync cached for the next
+// call (no release threshold); dgs_release_cached_memory returns it.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
 // DGS_CTL_COMPACT_MIN: shortest edge list the controller compacts (default
 // 2048; tests lower it so that compaction runs on small instances).
 int32_t env_compact_min();

@@ -346,16 +346,16 @@ __global__ void __launch_bounds__(kPThreads, 1) greedy_persistent_kernel(Workspa
                 if (lane == 31) s_warp[32] = wi;
             }
             __syncthreads();
-            int32_t rank = base_rank + s_warp[warp] + incl - c;
+            const int32_t rank = base_rank + s_warp[warp] + incl - c;
             total = s_warp[32];
-            while (dirty) {
-                const int k = __ffs(dirty) - 1;
-                dirty &= dirty - 1u;
-                if (rank % G == b) {
-                    const int32_t slot = atomicAdd(&s_nmine, 1);
-                    if (slot < kPMaxMine) s_mine[slot] = 32 * q + k;
-                }
-                ++rank;
+            // this word's owners take ranks rank .. rank + c - 1; the ones this
+            // CTA rescans are the set bits of index i = (b - rank) mod G,
+            // i + G, ... below c
+            for (int32_t i = ((b - rank) % G + G) % G; i < c; i += G) {
+                uint32_t d = dirty;
+                for (int32_t skip = 0; skip < i; ++skip) d &= d - 1u;  // drop the i lowest set bits
+                const int32_t slot = atomicAdd(&s_nmine, 1);
+                if (slot < kPMaxMine) s_mine[slot] = 32 * q + (__ffs(d) - 1);
             }
             base_rank += total;
             __syncthreads();

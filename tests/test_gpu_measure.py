@@ -40,3 +40,19 @@ def test_read_bandwidth_rejects_bad_arguments():
     assert lib.dgs_read_bandwidth(ctypes.c_void_p(x.data_ptr() + 4), 4096, 1, ctypes.byref(out), s) == \
         B.DGS_ERR_INVALID
     assert lib.dgs_read_bandwidth(p, 4096, 1, None, s) == B.DGS_ERR_INVALID
+
+
+def test_release_cached_memory_after_solves():
+    """Solves reuse the library pool's cached workspace; releasing it keeps
+    later solves correct."""
+    from paper_1106_5694_gb300 import inputs
+    a = torch.from_numpy(inputs.peer_shaped(700, 3)).cuda()
+    st1, sig1, f1, _ = B.dgs_solve_ex(a)
+    st2, sig2, f2, _ = B.dgs_solve_ex(a)
+    free_before = torch.cuda.mem_get_info()[0]
+    assert B.dgs_release_cached_memory() == B.DGS_OK
+    free_after = torch.cuda.mem_get_info()[0]
+    st3, sig3, f3, _ = B.dgs_solve_ex(a)
+    assert st1 == st2 == st3 == B.DGS_OK and f1 == f2 == f3
+    assert torch.equal(sig1, sig2) and torch.equal(sig1, sig3)
+    assert free_after >= free_before
