@@ -599,8 +599,22 @@ struct dgs_server {
                 if (lda != (size_t)r.n) e = cudaMemsetAsync(a_dev, 0, sizeof(int32_t) * lda * r.n, up);
                 const cudaMemcpyKind kind =
                     (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-                if (e == cudaSuccess)
-                    e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, (size_t)r.n * 4, (size_t)r.n * 4, r.n, kind, up);
+                const size_t row_bytes = (size_t)r.n * 4;
+                if (e == cudaSuccess && lda == (size_t)r.n) {
+                    e = cudaMemcpyAsync(a_dev, r.a, row_bytes * r.n, kind, up);
+                } else if (e == cudaSuccess && kind == cudaMemcpyHostToDevice) {
+                    // a pitched copy from pageable host memory is slow (the
+                    // server's uploads took 14 times longer): copy the rows
+                    // contiguously into the region of the transpose (n x ldt
+                    // >= n^2 ints, written by pass 1 only later), then
+                    // re-pitch on the device
+                    e = cudaMemcpyAsync(probe.w.at, r.a, row_bytes * r.n, kind, up);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy2DAsync(a_dev, lda * 4, probe.w.at, row_bytes, row_bytes, r.n,
+                                              cudaMemcpyDeviceToDevice, up);
+                } else if (e == cudaSuccess) {
+                    e = cudaMemcpy2DAsync(a_dev, lda * 4, r.a, row_bytes, row_bytes, r.n, kind, up);
+                }
                 // the start (USER: the caller's; RANDOM: drawn here) after the result
                 int32_t* start = start_of(mem, r.n);
                 std::vector<int32_t> perm;
