@@ -440,6 +440,7 @@ def run_ours(args):
         "solve": {"sweeps": stats["sweeps"], "events": stats["events"], "swaps_applied": stats["swaps_applied"],
                   "greedy_rounds": stats["greedy_rounds"], "greedy_rescans": stats["greedy_rescans"],
                   "objective": f, "parity": parity,
+                  "sweeps_per_s": round(stats["sweeps"] / (ms_per_step * 1e-3), 1),
                   "step_ms": [round(x, 3) for x in step_ms]},
         **extra,
     }
@@ -500,7 +501,8 @@ def run_other_sizes(dev, peak, steps=3):
         row = {"workload": f"{kind.replace('uniform1000', 'uniform [0,1000)')} n={n}",
                "ms": round(statistics.mean(ms), 4), "ms_median": round(statistics.median(ms), 4),
                "ms_best": round(min(ms), 4), "kernel_launches": stats["kernel_launches"],
-               "sweeps": stats["sweeps"], "swaps_applied": stats["swaps_applied"], "objective": f2,
+               "sweeps": stats["sweeps"], "sweeps_per_s": round(stats["sweeps"] / (statistics.mean(ms) * 1e-3), 1),
+               "swaps_applied": stats["swaps_applied"], "objective": f2,
                "evaluation_ms": round(t_ev, 4),
                "evaluation_frac_of_hbm": round(alg / (t_ev * 1e-3) / 1e9 / peak, 4),
                "checked": "permutation, exact objective, no improving 2-exchange" if ok else "FAILED"}
@@ -626,10 +628,14 @@ def run_batched(dev, count=1024, lo=64, hi=4096, cpu_every=0):
 
 def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
     """Poisson stream of peer-shaped requests, n log-uniform in [256, 16384],
-    host-memory inputs, 40 GB admission budget.  The plain comparison is a
-    FIFO single-server queue over the same arrivals whose service time is a
-    dgs_solve_host call per request (measured), latency = completion -
-    arrival."""
+    inputs in pinned host memory (as a server receives them), 40 GB
+    admission budget.  The plain comparison is a FIFO single-server queue
+    over the same arrivals whose service time is a dgs_solve_host call per
+    request on the same buffers (measured), latency = completion - arrival.
+    (From pageable memory the copies of both arms slowed down as the process
+    went on -- plain capacity fell from 380 to 190 solves/s over three
+    repetitions in one process -- which made the comparison depend on what
+    ran before it.)"""
     import threading
 
     import numpy as np
@@ -640,7 +646,9 @@ def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
 
     ns = inputs.batched_sizes(count, lo, hi, seed=11)
     pool = _pool(hi, 2, 900)
-    reqs = [np.ascontiguousarray(pool[k % 2][:n, :n]) for k, n in enumerate(ns)]
+    reqs = [torch.from_numpy(np.ascontiguousarray(pool[k % 2][:n, :n])).pin_memory().numpy()
+            for k, n in enumerate(ns)]
+    del pool
     # plain: each request alone through the host entry point
     B.dgs_solve_host(reqs[0], device=dev)
     service, plain_f = [], []
@@ -691,7 +699,7 @@ def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
 
     return {
         "workload": f"{count} peer-shaped requests, n log-uniform in [{lo},{hi}] (seeded), Poisson arrivals at "
-                    f"{rate:.1f}/s (70% of the plain solver's measured capacity), host-memory inputs, "
+                    f"{rate:.1f}/s (70% of the plain solver's measured capacity), pinned host-memory inputs, "
                     f"{budget >> 30} GB admission budget",
         "rate_per_s": round(rate, 2), "solves_per_s": round(count / span, 2),
         "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
