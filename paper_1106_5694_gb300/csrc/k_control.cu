@@ -112,7 +112,7 @@ struct TwoTier {
 // Reservation key of edge position p in DR round r: each round's keys are
 // smaller than every earlier round's, so reservations never need clearing
 // (the array is reset once per key period).
-constexpr uint32_t kPosBits = 18, kPosMask = (1u << kPosBits) - 1u, kRoundSpanMax = 1u << 14;
+constexpr uint32_t kPosBits = 18, kRoundSpanMax = 1u << 14;
 __device__ __forceinline__ uint32_t round_base(uint32_t r, uint32_t span) {
     return (span - 1u - (r & (span - 1u))) << kPosBits;
 }
@@ -134,7 +134,6 @@ struct Codec<unsigned long long> {
     static __device__ __forceinline__ int32_t v(unsigned long long e) { return (int32_t)(e >> 32); }
 };
 
-constexpr int kUnroll = 4;
 
 // Switching loop (see the file comment).
 // span: reservation-key period (power of two <= kRoundSpanMax); stamp_wrap:
@@ -149,7 +148,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     if (st->status != kRunning) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int32_t warp_sums[33];
-    __shared__ int32_t s_L, s_live, s_stop, s_acc, s_und, s_und2, s_app, s_y, s_sweeps, s_event;
+    __shared__ int32_t s_L, s_live, s_stop, s_acc, s_app, s_y, s_sweeps, s_event;
     __shared__ int32_t s_max_sweeps, s_trace_cap;
     __shared__ uint32_t s_round;
     __shared__ uint32_t s_stamp;
@@ -182,8 +181,6 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     }
     const int32_t cap = lists_s ? list_cap : 0;
     TwoTier accl{lists_s, cap, g.acc_g};
-    TwoTier und_a{lists_s ? lists_s + list_cap : nullptr, cap, g.und_g};
-    TwoTier und_b{lists_s ? lists_s + 2 * list_cap : nullptr, cap, g.und_g + 2 * n};
     unsigned long long* pt = (tid == 0) ? w.phase_ns : nullptr;
     long long tp = clock64();
 #define DGS_CT(slot)                                            \
@@ -296,7 +293,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                 stop = 1;
             }
             s_stop = stop;
-            s_acc = 0; s_und = 0; s_app = 0; s_y = 0; s_gain = 0ull; s_event = 0;
+            s_acc = 0; s_app = 0; s_y = 0; s_gain = 0ull; s_event = 0;
             s_stamp = s_stamp + 1u;
         }
         __syncthreads();
@@ -347,56 +344,53 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             __syncthreads();
         }
         const uint8_t stamp = (uint8_t)s_stamp;
-        // CC (Algorithm 4) by deterministic reservations.  Round 1 over all
-        // edges: reserve both agents; then each edge is accepted (holds both),
-        // rejected (lost an agent to an edge that holds both of its own) or
-        // undecided (later rounds, on the undecided list only).
-        const uint32_t kb = round_base(s_round, span);
-        for (int32_t p0 = tid; p0 < L; p0 += kUnroll * kCtlThreads) {
-            uint8_t es[kUnroll];
-            EdgeT e[kUnroll];
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                const int32_t p = p0 + k * kCtlThreads;
-                es[k] = p < L ? estate[p] : (uint8_t)0;
-                e[k] = (es[k] & kAlive) ? E[p] : (EdgeT)0;
-            }
-#pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
-                if (!(es[k] & kAlive)) continue;
-                const uint32_t key = kb | (uint32_t)(p0 + k * kCtlThreads);
-                const int32_t u = C::u(e[k]), v = C::v(e[k]);
-                if (key < res[u]) atomicMin(&res[u], key);
-                if (key < res[v]) atomicMin(&res[v], key);
-            }
-        }
-        __syncthreads();
-        DGS_CT(kPtCtlPass1)
+        // CC (Algorithm 4): the accepted set is the greedy one in priority
+        // order (a slot is accepted when neither agent of its exchange was
+        // claimed by an earlier accepted slot).  The list is taken in chunks
+        // of one edge per thread, in order: an edge touching an agent claimed
+        // by an earlier chunk is rejected at once; the chunk's other edges
+        // are decided among themselves by deterministic reservations (each
+        // round, the remaining candidates reserve both agents with a key that
+        // orders them by position; an edge holding both reservations is
+        // accepted and claims its agents; an edge touching a newly claimed
+        // agent is rejected; the first remaining candidate always wins, so
+        // every round accepts at least one edge).  Claims of a chunk reach
+        // the next through a barrier, so the result is the greedy one.
         {
             int32_t ev = 0;
-            for (int32_t p0 = tid; p0 < L; p0 += kUnroll * kCtlThreads) {
-                uint8_t es[kUnroll];
-                EdgeT e[kUnroll];
-                uint32_t ru[kUnroll], rv[kUnroll];
-#pragma unroll
-                for (int k = 0; k < kUnroll; ++k) {
-                    const int32_t p = p0 + k * kCtlThreads;
-                    es[k] = p < L ? estate[p] : (uint8_t)0;
-                    e[k] = (es[k] & kAlive) ? E[p] : (EdgeT)0;
+            for (int32_t c0 = 0; c0 < L; c0 += kCtlThreads) {
+                const int32_t p = c0 + tid;
+                const uint8_t es = p < L ? estate[p] : (uint8_t)0;
+                int32_t u = 0, v = 0;
+                bool cand = false;
+                if (es & kAlive) {
+                    const EdgeT e = E[p];
+                    u = C::u(e);
+                    v = C::v(e);
+                    cand = claimed[u] != stamp && claimed[v] != stamp;
                 }
-#pragma unroll
-                for (int k = 0; k < kUnroll; ++k) {
-                    ru[k] = (es[k] & kAlive) ? res[C::u(e[k])] : 0u;
-                    rv[k] = (es[k] & kAlive) ? res[C::v(e[k])] : 0u;
-                }
-#pragma unroll
-                for (int k = 0; k < kUnroll; ++k) {
-                    if (!(es[k] & kAlive)) continue;
-                    const int32_t p = p0 + k * kCtlThreads;
-                    const uint32_t key = kb | (uint32_t)p;
-                    if (ru[k] == key && rv[k] == key) {
-                        claimed[C::u(e[k])] = stamp;
-                        claimed[C::v(e[k])] = stamp;
+                for (int32_t r = 0; __syncthreads_or(cand); ++r) {
+                    if (r > kCtlThreads) {  // every round accepts the first candidate
+                        if (tid == 0) {
+                            st->error = kErrInternal;
+                            st->status = kError;
+                        }
+                        cand = false;
+                        continue;
+                    }
+                    if ((s_round & (span - 1u)) == 0u && s_round != 0u) {  // reservation keys wrap
+                        for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
+                        __syncthreads();
+                    }
+                    const uint32_t key = round_base(s_round, span) | (uint32_t)p;
+                    if (cand) {
+                        if (key < res[u]) atomicMin(&res[u], key);
+                        if (key < res[v]) atomicMin(&res[v], key);
+                    }
+                    __syncthreads();
+                    if (cand && res[u] == key && res[v] == key) {
+                        claimed[u] = stamp;
+                        claimed[v] = stamp;
                         accl.put(atomicAdd(&s_acc, 1), p);
                         if (slot_s) {  // the re-evaluation record of its slot
                             const int32_t t = slot_s[p];
@@ -404,81 +398,18 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
                         }
-                        ev |= (es[k] & kAppl) ? 1 : 0;
-                    } else {
-                        bool rej = false;
-                        if (ru[k] != key) {
-                            const EdgeT f = E[ru[k] & kPosMask];
-                            rej = res[C::u(f)] == ru[k] && res[C::v(f)] == ru[k];
-                        }
-                        if (!rej && rv[k] != key) {
-                            const EdgeT f = E[rv[k] & kPosMask];
-                            rej = res[C::u(f)] == rv[k] && res[C::v(f)] == rv[k];
-                        }
-                        if (!rej) und_a.put(atomicAdd(&s_und, 1), p);
+                        ev |= (es & kAppl) ? 1 : 0;
+                        cand = false;
                     }
+                    __syncthreads();  // this round's claims are visible
+                    if (cand && (claimed[u] == stamp || claimed[v] == stamp)) cand = false;  // rejected
+                    if (tid == 0) s_round = s_round + 1u;
                 }
             }
             if (ev) s_event = 1;
-            if (tid == 0) s_round = s_round + 1u;
+            __syncthreads();
         }
-        __syncthreads();
-        DGS_CT(kPtCtlPass2)
-        // later rounds on the undecided edges only
-        {
-            TwoTier cur = und_a, nxt = und_b;
-            for (uint32_t guard = 0; s_und > 0; ++guard) {
-                if ((s_round & (span - 1u)) == 0u) {  // reservation keys wrap
-                    for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
-                    __syncthreads();
-                }
-                const int32_t m = s_und;
-                const uint32_t kb2 = round_base(s_round, span);
-                for (int32_t q = tid; q < m; q += kCtlThreads) {
-                    const int32_t p = cur.get(q);
-                    const EdgeT e = E[p];
-                    const int32_t u = C::u(e), v = C::v(e);
-                    if (claimed[u] == stamp || claimed[v] == stamp) continue;
-                    const uint32_t key = kb2 | (uint32_t)p;
-                    atomicMin(&res[u], key);
-                    atomicMin(&res[v], key);
-                }
-                if (tid == 0) s_und2 = 0;
-                __syncthreads();
-                int32_t ev = 0;
-                for (int32_t q = tid; q < m; q += kCtlThreads) {
-                    const int32_t p = cur.get(q);
-                    const EdgeT e = E[p];
-                    const int32_t u = C::u(e), v = C::v(e);
-                    if (claimed[u] == stamp || claimed[v] == stamp) continue;  // rejected
-                    const uint32_t key = kb2 | (uint32_t)p;
-                    if (res[u] == key && res[v] == key) {
-                        claimed[u] = stamp;
-                        claimed[v] = stamp;
-                        accl.put(atomicAdd(&s_acc, 1), p);
-                        ev |= (estate[p] & kAppl) ? 1 : 0;
-                    } else {
-                        nxt.put(atomicAdd(&s_und2, 1), p);
-                    }
-                }
-                if (ev) s_event = 1;
-                __syncthreads();
-                if (tid == 0) {
-                    s_und = s_und2;
-                    s_round = s_round + 1u;
-                    if (guard > (uint32_t)(L + 2)) {  // each round accepts the first live edge
-                        st->error = kErrInternal;
-                        st->status = kError;
-                        s_und = 0;
-                    }
-                }
-                const TwoTier tmp = cur;
-                cur = nxt;
-                nxt = tmp;
-                __syncthreads();
-            }
-        }
-        DGS_CT(kPtCtlUnd)
+        DGS_CT(kPtCtlPass1)
         if (st->status != kRunning) break;
         const int32_t nacc = s_acc;
         if (s_event) {

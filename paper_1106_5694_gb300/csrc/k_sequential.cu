@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sequential_kernel(Workspace w,
     if (st->status != kRunning) return;
     extern __shared__ __align__(16) int32_t s_delta[];  // [0, n): delta-bar, [n, 2n): delta-underbar
     __shared__ unsigned long long red[32];
-    __shared__ int32_t s_stop, s_u, s_v, s_slot, s_target;
+    __shared__ int32_t s_stop, s_u, s_v, s_target;
     __shared__ long long s_gain;
     const int32_t n = w.n, tid = threadIdx.x;
     int32_t* dbar = smem_deltas ? s_delta : w.ag_gain;
@@ -104,14 +104,12 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sequential_kernel(Workspace w,
                 if (ga > gj) {
                     const int32_t i = key_index(ba);
                     dbar[i] = 0;
-                    s_slot = i;
                     s_target = w.ag_job[i];
                     s_u = i;
                     s_v = w.sigma[s_target];
                 } else {
                     const int32_t j = key_index(bj);
                     dund[j] = 0;
-                    s_slot = n + j;
                     s_target = w.jb_agent[j];
                     s_u = s_target;
                     s_v = w.sigma[j];
