@@ -695,8 +695,11 @@ __device__ __forceinline__ bool row_task_row(const Workspace& w, int32_t j, int3
             bulk_g2s(atrow_s, atrow, bytes, bar);
         }
         const bool ok = mbar_wait_bounded(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) mbar_wait_bounded(bar, phase);  // the copy may still land: wait once more
+            return false;
+        }
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) return false;
         atrow = atrow_s;
     }
     row_task_compute(w, j, atrow, true, red_a, red_j);
@@ -780,14 +783,17 @@ __global__ void __launch_bounds__(512) row_owner_evaluation_kernel(Workspace w, 
                 mbar_arrive_expect_tx(&bar[b ^ 1], bytes);
                 bulk_g2s(stage0 + (b ^ 1) * w.ldt, w.at + (size_t)jn * w.ldt, bytes, &bar[b ^ 1]);
             }
-            const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+            const uint32_t pb = (phase >> b) & 1u;
+            const bool ok = mbar_wait_bounded(&bar[b], pb);
             phase ^= 1u << b;
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) {
                     st->error = kErrWaitTimeout;
                     st->status = kError;
-                    // the next row's copy may still be in flight into this CTA's
-                    // shared memory: wait for it (bounded) before leaving
+                    // this row's copy and the next one may still be in flight
+                    // into this CTA's shared memory: wait for them (bounded)
+                    // before leaving
+                    mbar_wait_bounded(&bar[b], pb);
                     if (jn < n) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
                 }
                 return;

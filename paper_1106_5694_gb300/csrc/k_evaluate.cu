@@ -544,6 +544,11 @@ __device__ __forceinline__ void evaluation_loop(const Workspace& w, int32_t stri
                 if (threadIdx.x == 0) {
                     w.st->error = kErrWaitTimeout;
                     w.st->status = kError;
+                    // gathers may still be in flight into any stage: wait for
+                    // each stage's next completion (bounded) before leaving;
+                    // stages before cs in this cycle complete next with the
+                    // other parity
+                    for (int q = 0; q < kStages; ++q) mbar_wait_bounded(&s_bar[q], q < cs ? cph ^ 1u : cph);
                 }
                 break;
             }
