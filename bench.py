@@ -215,6 +215,21 @@ def roofline_entry(kernel, what, alg_bytes, ms, n, workload, peak, peak_src):
 
 
 # ------------------------------------------------------------------ CPU oracle
+def host_cpu() -> dict:
+    """The host's CPU model (lscpu) and core count, stated beside every CPU
+    baseline."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model or "unknown", "host_cores": os.cpu_count()}
+
+
 def oracle_sample(a, sweeps: int):
     """One greedy start + one full difference evaluation with the oracle;
     extrapolated ms per solve = t_greedy + (1 + sweeps) * t_eval."""
@@ -394,7 +409,8 @@ def run_ours(args):
         est_ms = (tg + (1 + stats["sweeps"]) * te) * 1e3
         cpu = {"value": round(est_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": (f"oracle greedy start ({tg:.1f} s) + one full difference evaluation ({te:.2f} s) on the "
-                          f"same instance; ms/solve = t_greedy + (1 + {stats['sweeps']} sweeps) x t_eval")}
+                          f"same instance; ms/solve = t_greedy + (1 + {stats['sweeps']} sweeps) x t_eval"),
+               **host_cpu()}
 
     extra = {}
     # Algorithm 1 (sequential DGS) on the same instance, for comparison
@@ -415,7 +431,8 @@ def run_ours(args):
         extra["sequential"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batched:
         try:
-            extra["other_sizes"] = run_other_sizes(dev, measured_hbm_peak()[0])
+            extra["other_sizes"] = run_other_sizes(dev, measured_hbm_peak()[0],
+                                                   cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         except Exception as exc:
             extra["other_sizes"] = {"error": f"{type(exc).__name__}: {exc}"}
         for key, fn in (("batched", run_batched), ("serving", run_serving)):
@@ -459,7 +476,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------- the other sizes
-def run_other_sizes(dev, peak, steps=3):
+def run_other_sizes(dev, peak, steps=3, cpu=False):
     """Single solves of the other single-instance configurations: n = 256
     uniform [0, 1000) (latency-bound: microseconds and launches per solve),
     n = 4096 peer-shaped (64 MB, fits in L2), n = 10000 uniform [0, 1e6) and
@@ -468,6 +485,7 @@ def run_other_sizes(dev, peak, steps=3):
     first full evaluation is timed inside the solve.  Where the matrix fits in
     L2 the evaluation is also stated against the read rate of the matrix
     itself from L2 (dgs_read_bandwidth)."""
+    import numpy as np
     import torch
 
     from paper_1106_5694_gb300 import binding as B
@@ -479,7 +497,6 @@ def run_other_sizes(dev, peak, steps=3):
     for kind, n in (("uniform1000", 256), ("peer", 4096), ("uniform", 10000), ("peer", 20000), ("uniform", 20000)):
         a = make_input(kind, n, 0)
         at = torch.from_numpy(a).to(dev)
-        del a
         B.dgs_autotune(n, device=dev)
         st, sig, f, stats = B.dgs_solve_ex(at, profile=1)
         torch.cuda.synchronize(dev)
@@ -514,6 +531,20 @@ def run_other_sizes(dev, peak, steps=3):
                "evaluation_ms": round(t_ev, 4),
                "evaluation_frac_of_hbm": round(alg / (t_ev * 1e-3) / 1e9 / peak, 4),
                "checked": "permutation, exact objective, no improving 2-exchange" if ok else "FAILED"}
+        if cpu and n <= 256:  # the oracle's full solve, one core
+            import oracle
+
+            oracle.build()
+            t0 = time.perf_counter()
+            ref = oracle.dgs_parallel(a)
+            row["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+            row["oracle_ms_kind"] = "measured full oracle solve, one core"
+            row["oracle_bit_exact"] = bool(ref.objective == f2 and np.array_equal(ref.tau, sig.cpu().numpy()))
+        elif cpu and n <= 4096:  # extrapolated like the headline's baseline
+            tg, te, _ = oracle_sample(a, stats["sweeps"])
+            row["oracle_ms"] = round((tg + (1 + stats["sweeps"]) * te) * 1e3, 1)
+            row["oracle_ms_kind"] = "t_greedy + (1 + sweeps) x one full oracle evaluation, one core"
+        del a
         if 4 * n * n < l2_bytes:
             st_b, l2_gbs = B.dgs_read_bandwidth(at, repeats=20)
             if st_b == B.DGS_OK:
@@ -570,7 +601,7 @@ def oracle_pool_sample(get, ns, every: int, objs_gpu):
     return {"kind": "oracle", "cores": cores, "sample": f"one instance in every {every} ({len(idx)} of {len(ns)}), "
             f"spawn process pool; whole-set time extrapolated by sum n^2", "sample_wall_s": round(wall, 2),
             "cpu_s": round(sum(t for t, _ in res), 2), "value": round(len(ns) / wall_all, 2), "unit": "solves/s",
-            "objectives_equal_to_gpu": all(f == objs_gpu[k] for k, (_, f) in zip(idx, res))}
+            "objectives_equal_to_gpu": all(f == objs_gpu[k] for k, (_, f) in zip(idx, res)), **host_cpu()}
 
 
 def batched_cpu_baseline(batched: dict, every: int, hi=4096) -> dict:
@@ -764,7 +795,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": workload_config(args.workload, args.n, seed),
-        "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
