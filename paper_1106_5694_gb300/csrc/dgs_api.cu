@@ -188,7 +188,6 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
     ctl->claimed = mode < 1 ? ar.take<uint8_t>(nb) : nullptr;
     ctl->estate = mode < 1 ? ar.take<uint8_t>(2 * nb) : nullptr;
     ctl->acc = ar.take<int32_t>(2 * nb);
-    ctl->und = ar.take<int32_t>(4 * nb);
     return ar.used;
 }
 
@@ -615,8 +614,8 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         unsigned long long ph[kPtCount];
         if (cudaMemcpy(ph, S.w.phase_ns, sizeof(ph), cudaMemcpyDeviceToHost) == cudaSuccess) {
             fprintf(stderr, "[dgs phases] greedy ns: match %llu bar1 %llu check %llu scan %llu bar2 %llu scanmax %llu | "
-                            "controller cycles: entry %llu top %llu pass1 %llu pass2 %llu und %llu post %llu event %llu sweeps %llu\n",
-                    ph[0], ph[1], ph[2], ph[3], ph[4], ph[5], ph[8], ph[9], ph[10], ph[11], ph[12], ph[13], ph[14], ph[15]);
+                            "controller cycles: entry %llu top %llu conflict check %llu post %llu event %llu sweeps %llu\n",
+                    ph[0], ph[1], ph[2], ph[3], ph[4], ph[5], ph[8], ph[9], ph[10], ph[13], ph[14], ph[15]);
         }
     }
     const dgs_status status = map_device_status(h);

@@ -104,14 +104,13 @@ struct Workspace {
 };
 
 // Controller scratch in global memory (the parts that do not live in shared
-// memory for this n; null otherwise) and its work lists.
+// memory for this n; null otherwise) and its accepted list.
 struct CtlGlobal {
     uint32_t* res;
     uint8_t* claimed;
     uint8_t* estate;
     void* edges;
     int32_t* acc;
-    int32_t* und;
 };
 
 // One instance of a batched or served solve, as the batched kernels see it.
@@ -119,7 +118,7 @@ struct Instance {
     Workspace w;
     CtlGlobal ctl;
     int32_t ctl_mode;          // controller scratch placement for this n
-    int32_t ctl_cap;           // entries of each controller list in shared memory
+    int32_t ctl_cap;           // entries of the controller's accepted list in shared memory
     int32_t fresh;             // 1: the next step initialises this instance
     int32_t max_sweeps;        // options of the instance
     int32_t init_mode;         // DGS_INIT_GREEDY / _IDENTITY / _USER (a random start arrives as USER)

@@ -84,7 +84,7 @@ __device__ __forceinline__ int32_t block_scan(int32_t x, int32_t* warp_sums, int
 // Controller scratch.  res: per agent, the reservation key of the current DR
 // round; claimed: per agent, the stamp of the sweep that claimed it; estate:
 // per edge position (alive / applies / fresh bits); E: per edge position, the
-// two agents of its exchange.  The undecided and accepted lists are two-tier:
+// two agents of its exchange.  The list of accepted positions is two-tier:
 // the first `cap` entries in shared memory (16-bit positions), the rest in
 // global memory.
 struct CtlScratch {
@@ -93,7 +93,6 @@ struct CtlScratch {
     uint8_t* estate;
     void* edges;
     int32_t* acc_g;  // accepted positions beyond the shared-memory part
-    int32_t* und_g;  // undecided positions beyond it (two lists of 2n)
 };
 
 enum : uint8_t { kAlive = 1, kAppl = 2, kFreshBit = 4, kAccBit = 8 };
@@ -138,7 +137,7 @@ struct Codec<unsigned long long> {
 // Switching loop (see the file comment).
 // span: reservation-key period (power of two <= kRoundSpanMax); stamp_wrap:
 // claim-stamp period (<= 255).  Both are shortened only by a test knob.
-// list_cap: entries of each two-tier list held in shared memory.
+// list_cap: entries of the accepted list held in shared memory.
 template <typename EdgeT>
 __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem_mode, const CtlScratch& g,
                                                 uint32_t span, uint32_t stamp_wrap, int32_t list_cap,
@@ -172,7 +171,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             off += sizeof(EdgeT) * 2 * (size_t)n;
         }
         lists_s = reinterpret_cast<uint16_t*>(smem_raw + off);
-        off += 2 * 3 * (size_t)list_cap;
+        off += 2 * (size_t)list_cap;
         slot_s = reinterpret_cast<uint16_t*>(smem_raw + off);
         off += 2 * 2 * (size_t)n;
         claimed = smem_raw + off;
@@ -991,7 +990,7 @@ __global__ void prepare_edges_batched_kernel(BatchTable t) {
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_batched_kernel(BatchTable t, uint32_t span,
                                                                            uint32_t stamp_wrap, int32_t compact_min) {
     for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t, int32_t) {
-        const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc, in.ctl.und};
+        const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc};
         controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min);
     });
 }
@@ -1043,29 +1042,29 @@ static size_t ctl_fixed_bytes(int32_t n, int32_t mode) {
 
 int32_t controller_smem_mode(int32_t n) {
     int32_t mode = 0;
-    if (n <= 32767 && ctl_fixed_bytes(n, 2) + 6 * 256 + 16 <= kCtlSmemLimit) mode = 2;
-    else if (n <= 32767 && ctl_fixed_bytes(n, 1) + 6 * 256 + 16 <= kCtlSmemLimit) mode = 1;
+    if (n <= 32767 && ctl_fixed_bytes(n, 2) + 2 * 256 + 16 <= kCtlSmemLimit) mode = 2;
+    else if (n <= 32767 && ctl_fixed_bytes(n, 1) + 2 * 256 + 16 <= kCtlSmemLimit) mode = 1;
     return min(mode, env_controller_mode_cap());
 }
 
 int32_t controller_list_cap(int32_t n, int32_t mode) {
     if (mode == 0) return 0;
     const size_t room = kCtlSmemLimit - ctl_fixed_bytes(n, mode) - 16;
-    const size_t cap = room / 6;  // three 16-bit lists
+    const size_t cap = room / 2;  // one 16-bit list
     return (int32_t)(cap < 2 * (size_t)n ? cap : 2 * (size_t)n);
 }
 
 size_t controller_smem_bytes(int32_t n) {
     const int32_t mode = controller_smem_mode(n);
     if (mode == 0) return 0;
-    return ctl_fixed_bytes(n, mode) + 6 * (size_t)controller_list_cap(n, mode) + 16;
+    return ctl_fixed_bytes(n, mode) + 2 * (size_t)controller_list_cap(n, mode) + 16;
 }
 
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s) {
     const int32_t mode = controller_smem_mode(w.n);
     const size_t smem = controller_smem_bytes(w.n);
     const int32_t cap = controller_list_cap(w.n, mode);
-    CtlScratch c{gs.res, gs.claimed, gs.estate, gs.edges, gs.acc, gs.und};
+    CtlScratch c{gs.res, gs.claimed, gs.estate, gs.edges, gs.acc};
     const bool narrow = w.n <= 65535;
     const void* fn = narrow ? reinterpret_cast<const void*>(controller_kernel<uint32_t>)
                             : reinterpret_cast<const void*>(controller_kernel<unsigned long long>);

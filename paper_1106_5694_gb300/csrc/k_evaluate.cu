@@ -151,7 +151,7 @@ struct CopyRows {
 template <int kRows, bool kTma = false>
 __device__ __forceinline__ CopyRows<kRows> copy_rows(const Workspace& w, int32_t J, int32_t K) {
     const int32_t rq = threadIdx.x >> 4;
-    const int32_t J0 = J * kT, K0 = K * kT, n = w.n;
+    const int32_t K0 = K * kT, n = w.n;
     CopyRows<kRows> c;
 #pragma unroll
     for (int q = 0; q < Geo<kRows>::kCopies; ++q) {
