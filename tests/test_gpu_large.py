@@ -96,3 +96,30 @@ def test_solve_at_n_40000():
     assert best <= 0
     del a
     torch.cuda.empty_cache()
+
+
+def test_solve_at_the_maximum_size():
+    """n = 2^17 (the largest n the library accepts; 68.7 GB per matrix): a
+    planted optimum (benefit 2000 on a seeded permutation, others below 100)
+    is found exactly, and nothing improves it."""
+    n = 1 << 17
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    a = torch.randint(0, 100, (n, n), dtype=torch.int32, device="cuda", generator=g)
+    perm = torch.randperm(n, device="cuda", generator=g)
+    ar = torch.arange(n, device="cuda")
+    a[ar, perm] = 2000
+    st, sig, f, stats = B.dgs_solve_ex(a)
+    assert st == B.DGS_OK, B.dgs_status_string(st) + " " + B.dgs_last_cuda_error()
+    assert torch.equal(sig.long(), perm) and f == 2000 * n
+    assert stats["sweeps"] == 0 and stats["greedy_rounds"] == 1
+    s64 = sig.long()
+    best = -1
+    for r0 in range(0, n, 1024):  # no improving 2-exchange
+        cross = a[r0:r0 + 1024][:, s64].long()
+        back = a[:, s64[r0:r0 + 1024]].long().T
+        best = max(best, int((cross + back - 2000 - 2000).max().item()))
+    assert best <= 0
+    del a, cross, back
+    torch.cuda.empty_cache()
+    assert B.dgs_release_cached_memory() == B.DGS_OK
