@@ -257,9 +257,11 @@ def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, s
     """dgs_solve_ex: returns (status, sigma_out, objective, stats dict).
 
     Keyword options: init, init_sigma (int32 CUDA tensor), seed (random
-    start), reeval (DGS_REEVAL_BOX / DGS_REEVAL_ALL), max_sweeps, deadline_us,
-    trace=(accepted int32, applied int32, objective int64) CUDA tensors of
-    equal length."""
+    start), reeval (DGS_REEVAL_BOX / DGS_REEVAL_ALL), algorithm
+    (DGS_ALG_PARALLEL / DGS_ALG_SEQUENTIAL), evaluation (DGS_EVAL_TILE_PAIRS /
+    DGS_EVAL_ROW_OWNER), max_sweeps, deadline_us, profile (1: time the first
+    evaluation and the greedy start), trace=(accepted int32, applied int32,
+    objective int64) CUDA tensors of equal length."""
     n = _n(benefit)
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
