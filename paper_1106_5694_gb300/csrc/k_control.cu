@@ -8,13 +8,15 @@
 //
 // One sweep = CC (Algorithm 4) + parallel switch + re-evaluation:
 //   * CC claims agent pairs in priority order.  Its result (the priority
-//     greedy matching of the edges) is computed exactly by deterministic
-//     reservations: every live edge writes its priority into both agents
-//     with atomicMin; an edge holding both agents is accepted; live edges
-//     touching a claimed agent are rejected (they form the set C, reading R3);
-//     repeat until no edge is live.  An accepted edge has no earlier accepted
-//     neighbour and every rejected edge has one, which is exactly the
-//     sequential outcome.
+//     greedy matching of the edges) is computed exactly, chunk by chunk of
+//     the priority order: edges touching an agent claimed by an earlier chunk
+//     are rejected at once; the chunk's other edges run deterministic
+//     reservations among themselves (each writes its priority into both
+//     agents with atomicMin; an edge holding both agents is accepted and
+//     claims them; edges touching a claimed agent are rejected; repeat).
+//     Rejected edges form the set C (reading R3).  An accepted edge has no
+//     earlier accepted neighbour and every rejected edge has one, which is
+//     exactly the sequential outcome.
 //   * Accepted exchanges are agent-disjoint, so each commits independently
 //     when its gain under the current sigma is > 0.
 //   * Slots not in C are re-evaluated (reading R4) by reading the row-best
