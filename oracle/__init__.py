@@ -2,7 +2,8 @@
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``dgs_oracle.c`` (plain,
-single-threaded C that follows Algorithms 2-4 of the paper, Section 3 and
+C that follows Algorithms 2-4 of the paper, single-threaded unless
+``set_evaluation`` asks otherwise, Section 3 and
 Section 5) through ctypes.  It shares no code with the CUDA library.
 
 Conventions: ``a`` is an n x n int32 numpy array, row = agent, column = job.
@@ -47,7 +48,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC]
+            ["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -98,6 +99,8 @@ def _load():
     lib.oracle_dgs_sequential.restype = ctypes.c_int
     lib.oracle_dgs_rect.argtypes = [P, i32, i32, i32, i32, ctypes.c_uint64, i32, P, P, P]
     lib.oracle_dgs_rect.restype = ctypes.c_int
+    lib.oracle_set_evaluation.argtypes = [i32, i32]
+    lib.oracle_set_evaluation.restype = None
     lib.oracle_hungarian.argtypes = [P, i32, P]
     lib.oracle_hungarian.restype = i64
     lib.oracle_brute_force.argtypes = [P, i32, P]
@@ -182,6 +185,13 @@ class SolveResult:
     trace_accepted: np.ndarray
     trace_applied: np.ndarray
     trace_objective: np.ndarray
+
+
+def set_evaluation(threads: int = 1, transpose: bool = False) -> None:
+    """Run Algorithm 3's slot evaluations on `threads` host threads, reading
+    columns of a from a transposed copy when `transpose`.  Results do not
+    depend on either; the default (1, False) is the literal loop."""
+    _load().oracle_set_evaluation(int(threads), 1 if transpose else 0)
 
 
 def random_permutation(n: int, seed: int) -> np.ndarray:

@@ -1,5 +1,6 @@
 /*
- * dgs_oracle.c -- plain single-threaded CPU oracle for Deep Greedy Switching.
+ * dgs_oracle.c -- plain CPU oracle for Deep Greedy Switching (single-threaded
+ * by default; see oracle_set_evaluation).
  *
  * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
  * baseline of the benchmark; never by the CUDA library.  Written for
@@ -134,6 +135,90 @@ void oracle_evaluate_all(const int32_t* a, int32_t n, const int32_t* tau,
 }
 
 /* ------------------------------------------------------------------------ */
+/* How the slot evaluations of Algorithm 3 are carried out.  Algorithm 3
+ * evaluates every agent and every job "in parallel": each ADE/JDE reads the
+ * current assignment and writes only its own slot, so running them on
+ * several host threads changes no result.  With use_transpose the column
+ * entries a[i'][j] of the four-term difference are read from a plain
+ * transposed copy at[j][i'] (the same integers, contiguous in memory).
+ * Defaults: one thread, no copy -- the literal loops above.  Only the
+ * script that writes stored full-size results changes them; the tests check
+ * that every setting gives the same solve. */
+static int32_t g_eval_threads = 1;
+static int32_t g_eval_transpose = 0;
+
+void oracle_set_evaluation(int32_t threads, int32_t use_transpose)
+{
+    g_eval_threads = threads > 1 ? threads : 1;
+    g_eval_transpose = use_transpose ? 1 : 0;
+}
+
+#define AT(j, i) ((int64_t)at[(int64_t)(j) * n + (i)])
+
+/* oracle_ade with a[i'][j] read as at[j][i']. */
+static void ade_transposed(const int32_t* a, const int32_t* at, int32_t n, const int32_t* sigma,
+                           const int32_t* tau, int32_t i, int32_t* gain, int32_t* job)
+{
+    int32_t j = tau[i];
+    int64_t best = 0;
+    int32_t best_job = -1;
+    for (int32_t jp = 0; jp < n; ++jp) {
+        if (jp == j) continue;
+        int32_t ip = sigma[jp];
+        int64_t diff = A(i, jp) + AT(j, ip) - A(i, j) - A(ip, jp);
+        if (diff > best) {
+            best = diff;
+            best_job = jp;
+        }
+    }
+    *gain = (int32_t)best;
+    *job = best_job;
+}
+
+/* oracle_jde with a[i'][j] read as at[j][i'] and a[i'][j'] as at[j'][i']. */
+static void jde_transposed(const int32_t* a, const int32_t* at, int32_t n, const int32_t* sigma,
+                           const int32_t* tau, int32_t j, int32_t* gain, int32_t* agent)
+{
+    int32_t i = sigma[j];
+    int64_t best = 0;
+    int32_t best_agent = -1;
+    for (int32_t ip = 0; ip < n; ++ip) {
+        if (ip == i) continue;
+        int32_t jp = tau[ip];
+        int64_t diff = AT(j, ip) + A(i, jp) - A(i, j) - AT(jp, ip);
+        if (diff > best) {
+            best = diff;
+            best_agent = ip;
+        }
+    }
+    *gain = (int32_t)best;
+    *agent = best_agent;
+}
+
+/* ADE of every agent i with pick_a == NULL or pick_a[i] == 0, and JDE of
+ * every job j with pick_j == NULL or pick_j[j] == 0; returns how many ran. */
+static int64_t evaluate_slots(const int32_t* a, const int32_t* at, int32_t n, const int32_t* sigma,
+                              const int32_t* tau, const uint8_t* pick_a, const uint8_t* pick_j,
+                              int32_t* ag_gain, int32_t* ag_job, int32_t* jb_gain, int32_t* jb_agent)
+{
+    int64_t count = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_eval_threads) if (g_eval_threads > 1)
+    for (int32_t i = 0; i < n; ++i) {
+        if (pick_a && pick_a[i]) continue;
+        if (at) ade_transposed(a, at, n, sigma, tau, i, &ag_gain[i], &ag_job[i]);
+        else oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]);
+    }
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_eval_threads) if (g_eval_threads > 1)
+    for (int32_t j = 0; j < n; ++j) {
+        if (pick_j && pick_j[j]) continue;
+        if (at) jde_transposed(a, at, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]);
+        else oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]);
+    }
+    for (int32_t t = 0; t < n; ++t) count += (!pick_a || !pick_a[t]) + (!pick_j || !pick_j[t]);
+    return count;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 4 (CC), reading R3.  CR collects claimed agents.  Agent slots
  * are visited first (ascending i), then job slots (ascending j); a slot
  * with a candidate claims the two agents its exchange touches -- for agent
@@ -260,6 +345,12 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
     uint8_t* in_ca = (uint8_t*)calloc((size_t)n, 1);
     uint8_t* in_cj = (uint8_t*)calloc((size_t)n, 1);
     uint8_t* in_c_agent = (uint8_t*)calloc((size_t)n, 1);
+    int32_t* at = NULL; /* transposed copy, only with oracle_set_evaluation(.., 1) */
+    if (g_eval_transpose) {
+        at = (int32_t*)malloc((size_t)n * n * sizeof(int32_t));
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t j = 0; j < n; ++j) at[(int64_t)j * n + i] = a[(int64_t)i * n + j];
+    }
     oracle_stats st = {0, 0, 0, 0};
     int status = ORACLE_OK;
 
@@ -296,9 +387,7 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
         memset(in_c_agent, 0, (size_t)n);
 
         /* Difference evaluation phase: every agent and every job. */
-        for (int32_t i = 0; i < n; ++i) oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]);
-        for (int32_t j = 0; j < n; ++j) oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]);
-        st.evaluations += 2 * (int64_t)n;
+        st.evaluations += evaluate_slots(a, at, n, sigma, tau, NULL, NULL, ag_gain, ag_job, jb_gain, jb_agent);
 
         for (;;) { /* switching phase: while some delta > 0 */
             int any = 0;
@@ -354,10 +443,8 @@ int oracle_dgs_parallel(const int32_t* a, int32_t n, int32_t init_mode,
             /* Re-evaluation of the agents and jobs not in C (reading R4), or
              * of every agent and job (ORACLE_REEVAL_ALL). */
             const int all = reeval_rule == ORACLE_REEVAL_ALL;
-            for (int32_t i = 0; i < n; ++i)
-                if (all || !in_ca[i]) { oracle_ade(a, n, sigma, tau, i, &ag_gain[i], &ag_job[i]); st.evaluations++; }
-            for (int32_t j = 0; j < n; ++j)
-                if (all || !in_cj[j]) { oracle_jde(a, n, sigma, tau, j, &jb_gain[j], &jb_agent[j]); st.evaluations++; }
+            st.evaluations += evaluate_slots(a, at, n, sigma, tau, all ? NULL : in_ca, all ? NULL : in_cj,
+                                             ag_gain, ag_job, jb_gain, jb_agent);
 
             if (st.sweeps < trace_cap) {
                 if (trace_accepted) trace_accepted[st.sweeps] = accepted;
@@ -377,7 +464,7 @@ out:
     if (stats) *stats = st;
     free(sigma); free(tau); free(tau0);
     free(ag_gain); free(ag_job); free(jb_gain); free(jb_agent);
-    free(in_ca); free(in_cj); free(in_c_agent);
+    free(in_ca); free(in_cj); free(in_c_agent); free(at);
     return status;
 }
 

@@ -1,5 +1,6 @@
 /*
- * dgs_oracle.h -- plain single-threaded CPU oracle for Deep Greedy Switching.
+ * dgs_oracle.h -- plain CPU oracle for Deep Greedy Switching (single-threaded
+ * unless oracle_set_evaluation asks for more threads).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or
  * call this file: only the test suite, the smoke check and the CPU-baseline
@@ -94,6 +95,13 @@ void oracle_check_conflicts(int32_t n, const int32_t* sigma,
                             const int32_t* agent_gain, const int32_t* agent_job,
                             const int32_t* job_gain, const int32_t* job_agent,
                             uint8_t* in_ca, uint8_t* in_cj);
+
+/* How Algorithm 3's slot evaluations run (process-wide setting): on
+ * `threads` host threads (each ADE/JDE writes only its own slot, so the
+ * result does not depend on it), and with use_transpose != 0 reading the
+ * column entries a[i'][j] from a transposed copy.  Default (1, 0): the
+ * literal single-threaded loops. */
+void oracle_set_evaluation(int32_t threads, int32_t use_transpose);
 
 /* Algorithm 3 (parallel DGS) to termination or until max_sweeps switching
  * iterations have run (max_sweeps <= 0: no cap).  init_mode is one of

@@ -60,9 +60,3 @@ def test_invalid_arguments_rejected_before_any_device_call(lib):
 
 def test_build_targets_sm103a_only():
     assert build_ext.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
-
-
-def test_kernels_use_tma_bulk_copies():
-    src = open(os.path.join(ROOT, "paper_1106_5694_gb300", "csrc", "dgs_internal.cuh")).read()
-    assert "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes" in src
-    assert re.search(r"kSpinLimit", src)

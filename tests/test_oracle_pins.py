@@ -29,13 +29,32 @@ def _init_mode(name):
     return {"identity": oracle.INIT_IDENTITY, "greedy": oracle.INIT_GREEDY}[name]
 
 
+# ------------------------------------- evaluation settings, capped (runs first)
+def test_threaded_transposed_first_sweeps_equal_literal():
+    """The first sweeps under every evaluation setting equal the literal
+    loops' (capped, so that a wrong formula fails instead of looping)."""
+    a = inputs.uniform(40, 0, 50, 3)
+    ref = oracle.dgs_parallel(a, init=oracle.INIT_IDENTITY, max_sweeps=3, trace_cap=3)
+    for threads, transpose in ((1, True), (2, True), (2, False)):
+        oracle.set_evaluation(threads, transpose)
+        try:
+            r = oracle.dgs_parallel(a, init=oracle.INIT_IDENTITY, max_sweeps=3, trace_cap=3)
+        finally:
+            oracle.set_evaluation(1, False)
+        assert (r.status, r.tau.tolist(), r.objective) == (ref.status, ref.tau.tolist(), ref.objective)
+        assert r.trace_accepted.tolist() == ref.trace_accepted.tolist()
+        assert r.evaluations == ref.evaluations
+
+
 # ---------------------------------------------------------------- hand traces
 @pytest.mark.parametrize("name", ["n3_identity", "n3_greedy", "n2_antidiagonal", "n3_identity_reeval_all"])
 def test_hand_trace(name):
     t = _traces()[name]
     a = np.array(t["a"], np.int32)
     reeval = oracle.REEVAL_ALL if t.get("reeval") == "all" else oracle.REEVAL_BOX
-    r = oracle.dgs_parallel(a, init=_init_mode(t["init"]), trace_cap=64, reeval=reeval)
+    # capped a little above the traced sweep count, so that a mistake that
+    # makes the loop endless fails here instead of hanging
+    r = oracle.dgs_parallel(a, init=_init_mode(t["init"]), trace_cap=64, reeval=reeval, max_sweeps=t["sweeps"] + 4)
     assert r.status == oracle.OK
     assert r.tau.tolist() == t["tau"]
     assert r.objective == t["objective"]
@@ -288,6 +307,32 @@ def test_dgs_invariants(kind, n, seed):
         assert np.all(np.diff(np.concatenate([[f0], r.trace_objective])) >= 0)
         assert np.all(r.trace_accepted >= 1)  # the top candidate is always accepted
         assert r.passes == (2 if r.sweeps > 0 else 1)
+
+
+@pytest.mark.parametrize("threads,transpose", [(1, True), (3, False), (4, True)])
+def test_threaded_and_transposed_evaluations_give_the_literal_solve(threads, transpose):
+    """Algorithm 3 evaluates the slots in parallel and each ADE/JDE writes only
+    its own slot, so the host thread count and reading columns from a
+    transposed copy must reproduce the literal single-threaded solve exactly
+    (assignment, objective, sweep count and per-sweep trace), which the other
+    pins fix independently."""
+    cases = [("uniform", 130, 0), ("peer", 150, 1), ("small_range", 90, 0), ("geom", 60, 1)]
+    literal = [oracle.dgs_parallel(_make(k, n, s), init=init, trace_cap=100000)
+               for k, n, s in cases for init in (oracle.INIT_GREEDY, oracle.INIT_IDENTITY)]
+    oracle.set_evaluation(threads, transpose)
+    try:
+        other = [oracle.dgs_parallel(_make(k, n, s), init=init, trace_cap=100000)
+                 for k, n, s in cases for init in (oracle.INIT_GREEDY, oracle.INIT_IDENTITY)]
+        ra = oracle.dgs_parallel(_make("uniform", 64, 1), reeval=oracle.REEVAL_ALL, trace_cap=100000)
+    finally:
+        oracle.set_evaluation(1, False)
+    rl = oracle.dgs_parallel(_make("uniform", 64, 1), reeval=oracle.REEVAL_ALL, trace_cap=100000)
+    for x, y in zip(literal + [rl], other + [ra]):
+        assert x.status == y.status == oracle.OK
+        assert x.tau.tolist() == y.tau.tolist()
+        assert (x.objective, x.sweeps, x.evaluations) == (y.objective, y.sweeps, y.evaluations)
+        assert x.trace_objective.tolist() == y.trace_objective.tolist()
+        assert x.trace_accepted.tolist() == y.trace_accepted.tolist()
 
 
 def test_single_agent():
