@@ -15,8 +15,8 @@ SRC = os.path.join(ROOT, "oracle", "dgs_oracle.c")
 MUTATIONS = {
     "ade_dropped_term": ("int64_t diff = A(i, jp) + A(ip, j) - A(i, j) - A(ip, jp);",
                          "int64_t diff = A(i, jp) + A(ip, j) - A(i, j);"),
-    "ade_ties_to_last": ("A(ip, jp);\n        if (diff > best) {\n            best = diff;\n            best_job = jp;",
-                         "A(ip, jp);\n        if (diff >= best && diff > 0) {\n            best = diff;\n            best_job = jp;"),
+    "ade_ties_to_last": ("A(ip, j) - A(i, j) - A(ip, jp);\n        if (diff > best) {\n            best = diff;\n            best_job = jp;",
+                         "A(ip, j) - A(i, j) - A(ip, jp);\n        if (diff >= best && diff > 0) {\n            best = diff;\n            best_job = jp;"),
     "jde_wrong_index": ("int64_t diff = A(ip, j) + A(i, jp) - A(i, j) - A(ip, jp);",
                         "int64_t diff = A(ip, j) + A(i, jp) - A(i, j) - A(ip, j);"),
     "cc_partner_not_through_sigma": ("int32_t ip = sigma[agent_job[i]];\n        if (cr[i] || cr[ip]) {",
