@@ -17,14 +17,31 @@
  *   - sigma_out[i] = job assigned to agent i (DEVICE pointer, n int32,
  *     caller-owned).  The paper writes this map as tau = M(sigma) and uses
  *     sigma for job -> agent; the output here is the agent -> job map.
- *   - objective_out: HOST pointer to one int64 (exact sum of benefits).
+ *   - objective_out: pointer to one int64 (exact sum of benefits), in
+ *     DEVICE memory or in HOST memory (pageable or pinned).
  *   - stream: a cudaStream_t (the library includes no CUDA header here and
- *     takes it as dgs_stream_t, the same pointer type).  Work is enqueued on
- *     it; every solve entry point BLOCKS until its result is final (it reads
- *     the device-side loop state), so outputs are valid on return.
+ *     takes it as dgs_stream_t, the same pointer type).
+ *   - dgs_solve, dgs_solve_ex and dgs_solve_rect are STREAM-ORDERED: they
+ *     enqueue the whole solve on `stream` and return without waiting for it.
+ *     The switching loop runs on the device (a CUDA graph whose conditional
+ *     loop node repeats until the loop state says the solve has ended), so no
+ *     call waits for a sweep.  The outputs -- sigma_out, *objective_out,
+ *     dgs_stats and dgs_options.status_out -- are valid once the stream has
+ *     reached the end of the solve (for example after
+ *     cudaStreamSynchronize); outputs in host memory are written then by a
+ *     host callback on the stream.  The return value reports only what is
+ *     known when the work is enqueued (invalid arguments, allocation or
+ *     launch failures); the outcome of the solve itself (DGS_OK,
+ *     DGS_TIMEOUT, DGS_ERR_RANGE, DGS_ERR_INVALID for a USER start that is
+ *     not a permutation, DGS_ERR_INTERNAL) arrives in dgs_stats.status and
+ *     *dgs_options.status_out.  After an error every sigma_out entry is -1.
+ *     Exceptions: options.profile = 1 makes the call wait for its own
+ *     timings; dgs_solve_host and the evaluation, greedy-start, autotuning
+ *     and batched calls block until their outputs are final.
  *   - The library allocates its own device workspace (about 4*n*n bytes for
  *     the transposed copy of a plus O(n)) with stream-ordered allocation and
- *     frees it before returning.  Allocation failure -> DGS_ERR_OOM.
+ *     frees it, stream-ordered, behind the solve.  Allocation failure ->
+ *     DGS_ERR_OOM.
  *   - Results are deterministic: bit-identical across runs, launch shapes
  *     and devices, and equal to the plain CPU oracle's.
  */
@@ -56,7 +73,9 @@ typedef enum {
                              assignment reached so far and its objective */
     DGS_PENDING = 6,      /* dgs_poll / dgs_server_wait: not finished yet */
     DGS_ERR_BUSY = 7,     /* dgs_submit: the request can never fit the budget */
-    DGS_ERR_INTERNAL = 8  /* a device-side consistency check failed */
+    DGS_ERR_INTERNAL = 8, /* a device-side consistency check failed */
+    DGS_CANCELLED = 9     /* dgs_poll / dgs_server_wait: the request was
+                             withdrawn by dgs_cancel before it was admitted */
 } dgs_status;
 
 typedef enum {
@@ -115,9 +134,10 @@ typedef struct {
     int32_t* trace_accepted;
     int32_t* trace_applied;
     int64_t* trace_objective;
-    /* 1: time the first full difference evaluation and the greedy start with
-     * CUDA events on the call's stream (dgs_stats.evaluation_ms, greedy_ms);
-     * 0: no timing. */
+    /* 1: time the whole solve, the first full difference evaluation and the
+     * greedy start with CUDA events on the call's stream (dgs_stats.solve_ms,
+     * evaluation_ms, greedy_ms); the call then waits for the solve.  0: no
+     * timing. */
     int32_t profile;
     uint64_t seed;             /* DGS_INIT_RANDOM: generator start */
     int32_t reeval_rule;       /* a dgs_reeval_rule (default DGS_REEVAL_BOX) */
@@ -127,13 +147,20 @@ typedef struct {
     int32_t evaluation;        /* a dgs_evaluation_kernel (default
                                   DGS_EVAL_TILE_PAIRS); dgs_solve_batched and
                                   the server take DGS_EVAL_TILE_PAIRS only */
+    /* Where the outcome of a stream-ordered solve is written when the stream
+     * reaches its end (a dgs_status as int32), DEVICE or HOST memory; NULL:
+     * not written. */
+    int32_t* status_out;
 } dgs_options;
 
 typedef struct {
     int32_t sweeps;           /* iterations of the switching loop (Alg. 3) */
     int32_t events;           /* sweeps that committed at least one exchange */
     int64_t swaps_applied;    /* committed 2-exchanges */
-    int32_t greedy_rounds;    /* locally-dominant rounds of the greedy start */
+    int32_t greedy_rounds;    /* greedy start: the most proposals one agent
+                                 made (deferred acceptance; depends on the
+                                 order in which the GPU ran them), or the
+                                 locally-dominant rounds of the fallback */
     int32_t full_evaluations; /* full difference evaluations (all slots) */
     int32_t row_updates;      /* incremental re-evaluations (row tasks) */
     int64_t rows_recomputed;  /* rows re-evaluated by those row tasks */
@@ -141,25 +168,31 @@ typedef struct {
     int64_t kernel_launches;  /* kernels this call launched */
     double evaluation_ms;     /* first full evaluation, when options.profile */
     double greedy_ms;         /* greedy start after pass 1, when options.profile */
-    int64_t greedy_rescans;   /* rows of a (or its transpose) the greedy start rescanned */
+    int64_t greedy_rescans;   /* rows of a (or its transpose) the greedy start
+                                 rescanned (depends on the order of proposals) */
+    int32_t status;           /* the solve's outcome (a dgs_status) */
+    double solve_ms;          /* everything the call enqueued, when options.profile */
 } dgs_stats;
 
 /* Fill *opt with the defaults (GREEDY start, no cap, no deadline, no trace). */
 DGS_API void dgs_default_options(dgs_options* opt);
 
 /* Solve one instance with default options (Algorithm 3 from a greedy start
- * to termination: no 2-exchange improves the result). */
+ * to termination: no 2-exchange improves the result).  Stream-ordered (see
+ * the conventions above). */
 DGS_API dgs_status dgs_solve(const int32_t* benefit, int32_t n, int32_t* sigma_out,
                      int64_t* objective_out, dgs_stream_t stream);
 
-/* Solve with options; stats may be NULL. */
+/* Solve with options; stats (HOST) may be NULL.  Stream-ordered; stats are
+ * written when the stream reaches the end of the solve. */
 DGS_API dgs_status dgs_solve_ex(const int32_t* benefit, int32_t n, int32_t* sigma_out,
                         int64_t* objective_out, const dgs_options* options,
                         dgs_stats* stats, dgs_stream_t stream);
 
 /* Same as dgs_solve_ex but every buffer is in HOST memory (pageable or
  * pinned): benefit (n*n int32), sigma_out (n int32).  The host->device copy
- * of benefit and the device->host copy of sigma_out are part of the call. */
+ * of benefit and the device->host copy of sigma_out are part of the call,
+ * which BLOCKS until the outputs are final and returns the solve's outcome. */
 DGS_API dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n,
                           int32_t* sigma_out_host, int64_t* objective_out,
                           const dgs_options* options, dgs_stats* stats,
@@ -175,7 +208,8 @@ DGS_API dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n,
  * agent or -1 when it is left without one.  *objective_out: the sum of the
  * real benefits.  options as for dgs_solve_ex, except that USER starts and
  * traces are not taken (DGS_ERR_INVALID).  Workspace: about 8 max(n, m)^2
- * bytes (the padded matrix and its transpose).  Blocks until done. */
+ * bytes (the padded matrix and its transpose).  Stream-ordered like
+ * dgs_solve_ex. */
 DGS_API dgs_status dgs_solve_rect(const int32_t* benefit, int32_t n_agents, int32_t m_jobs, int32_t* assign_out,
                                   int64_t* objective_out, const dgs_options* options, dgs_stats* stats,
                                   dgs_stream_t stream);
@@ -328,6 +362,11 @@ DGS_API dgs_status dgs_poll(dgs_server* server, uint64_t ticket, int32_t* sigma_
 DGS_API dgs_status dgs_server_wait(dgs_server* server, uint64_t ticket, int64_t timeout_us,
                                    int32_t* sigma_out_host, int64_t* objective_out, dgs_stats* stats,
                                    dgs_request_times* times);
+/* Withdraw a request that has not been admitted yet (it still waits for
+ * budget or a slot): DGS_OK, and its ticket then polls DGS_CANCELLED.  A
+ * request already admitted runs to its end: DGS_PENDING.  Unknown or
+ * finished tickets: DGS_ERR_INVALID. */
+DGS_API dgs_status dgs_cancel(dgs_server* server, uint64_t ticket);
 DGS_API dgs_status dgs_server_get_info(dgs_server* server, dgs_server_info* info);
 DGS_API void dgs_server_destroy(dgs_server* server);
 
@@ -348,11 +387,21 @@ DGS_API void dgs_server_destroy(dgs_server* server);
  *
  * Limits: 1 <= n <= DGS_STATIC_MAX_N, n a multiple of 4, benefit 16-byte
  * aligned; otherwise DGS_ERR_INVALID, with the reason in
- * dgs_last_cuda_error().  The first call on each device looks up the array's
- * device address, so make that first call before any stream capture.  All
- * calls share the one array and each call clears the parts it needs zeroed;
- * calls that overlap on the GPU (other streams or host threads) race on it and
- * must be serialised by the caller.  Blocks until the outputs are final. */
+ * dgs_last_cuda_error().  Results and status codes are those of
+ * dgs_evaluate, also on errors (after DGS_ERR_RANGE or DGS_ERR_INVALID from a
+ * repeated job in sigma_in every output slot reads gain 0, index -1).
+ *
+ * The array belongs to the library's device code, which the CUDA runtime
+ * loads on a device lazily by default: the first call on each device may be
+ * the moment the array is committed, and can then fail with DGS_ERR_CUDA for
+ * lack of device memory.  Callers that must not allocate later make one call
+ * on each device during their set-up (or set CUDA_MODULE_LOADING=EAGER, which
+ * commits it when the context is created).  All calls share the one array and
+ * each call clears the parts it needs zeroed; calls that overlap on the GPU
+ * (other streams or host threads) race on it and must be serialised by the
+ * caller.  Each call synchronises its stream before it returns (the outputs
+ * are final then), so it must not be called on a stream that is being
+ * captured into a CUDA graph. */
 #define DGS_STATIC_MAX_N 8192
 DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_t n, const int32_t* sigma_in,
                                        int32_t* agent_gain, int32_t* agent_job,

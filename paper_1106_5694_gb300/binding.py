@@ -24,6 +24,7 @@ DGS_TIMEOUT = 5
 DGS_PENDING = 6
 DGS_ERR_BUSY = 7
 DGS_ERR_INTERNAL = 8
+DGS_CANCELLED = 9
 
 DGS_INIT_GREEDY = 0
 DGS_INIT_RANDOM = 1
@@ -41,7 +42,7 @@ EXPORTED = ["dgs_default_options", "dgs_solve", "dgs_solve_ex", "dgs_solve_host"
             "dgs_solve_batched", "dgs_server_create", "dgs_server_request_bytes", "dgs_submit", "dgs_poll",
             "dgs_server_wait", "dgs_server_get_info", "dgs_server_destroy", "dgs_autotune", "dgs_get_tuning",
             "dgs_submit_ex", "dgs_solve_rect", "dgs_read_bandwidth",
-            "dgs_release_cached_memory"]
+            "dgs_release_cached_memory", "dgs_cancel"]
 DGS_STATIC_MAX_N = 8192
 DGS_BATCH_MAX_N = 32767
 DGS_SUBMIT_HOST = 1
@@ -62,6 +63,7 @@ class dgs_options(ctypes.Structure):
         ("reeval_rule", ctypes.c_int32),
         ("algorithm", ctypes.c_int32),
         ("evaluation", ctypes.c_int32),
+        ("status_out", ctypes.c_void_p),
     ]
 
 
@@ -79,6 +81,8 @@ class dgs_stats(ctypes.Structure):
         ("evaluation_ms", ctypes.c_double),
         ("greedy_ms", ctypes.c_double),
         ("greedy_rescans", ctypes.c_int64),
+        ("status", ctypes.c_int32),
+        ("solve_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -139,8 +143,8 @@ def load():
     lib.dgs_default_options.restype = None
     lib.dgs_solve.argtypes = [P, i32, P, ctypes.POINTER(i64), P]
     lib.dgs_solve.restype = ctypes.c_int
-    lib.dgs_solve_ex.argtypes = [P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_options),
-                                 ctypes.POINTER(dgs_stats), P]
+    # objective_out may be host (byref int64) or device memory (a pointer)
+    lib.dgs_solve_ex.argtypes = [P, i32, P, P, ctypes.POINTER(dgs_options), ctypes.POINTER(dgs_stats), P]
     lib.dgs_solve_ex.restype = ctypes.c_int
     lib.dgs_solve_host.argtypes = [P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_options),
                                    ctypes.POINTER(dgs_stats), P]
@@ -171,6 +175,8 @@ def load():
     lib.dgs_server_wait.argtypes = [P, ctypes.c_uint64, i64, P, ctypes.POINTER(i64), ctypes.POINTER(dgs_stats),
                                     ctypes.POINTER(dgs_request_times)]
     lib.dgs_server_wait.restype = ctypes.c_int
+    lib.dgs_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.dgs_cancel.restype = ctypes.c_int
     lib.dgs_server_get_info.argtypes = [P, ctypes.POINTER(dgs_server_info)]
     lib.dgs_server_get_info.restype = ctypes.c_int
     lib.dgs_server_destroy.argtypes = [P]
@@ -242,40 +248,83 @@ def _options(init=DGS_INIT_GREEDY, init_sigma=None, max_sweeps=0, deadline_us=0,
     return o
 
 
-def dgs_solve(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None):
-    """dgs_solve: returns (status, sigma_out, objective)."""
+def _wait(benefit, stream):
+    (stream if stream is not None else torch.cuda.current_stream(benefit.device)).synchronize()
+
+
+class Pending:
+    """A stream-ordered solve in flight (wait=False): result() waits for the
+    stream and returns what the waiting form returns."""
+
+    def __init__(self, st, benefit, stream, out, f, stats):
+        self._st, self._benefit, self._stream = st, benefit, stream
+        self._out, self._f, self._stats = out, f, stats
+
+    def result(self):
+        if self._st != DGS_OK:
+            return self._st, self._out, int(self._f.value), self._stats.as_dict()
+        _wait(self._benefit, self._stream)
+        return int(self._stats.status), self._out, int(self._f.value), self._stats.as_dict()
+
+
+def dgs_solve(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, wait=True):
+    """dgs_solve (stream-ordered): returns (status of the call, sigma_out,
+    objective).  With wait (default) the stream is synchronised first, so the
+    objective is final; the solve's own outcome (range error, ...) is not
+    reported by this entry point: after a device-side error every sigma_out
+    entry is -1, and dgs_solve_ex reports the outcome."""
     n = _n(benefit)
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
     f = ctypes.c_int64(0)
     st = load().dgs_solve(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
                           _stream(benefit, stream))
+    if wait and st == DGS_OK:
+        _wait(benefit, stream)
     return st, sigma_out, int(f.value)
 
 
-def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, **opts):
-    """dgs_solve_ex: returns (status, sigma_out, objective, stats dict).
+def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, wait=True,
+                 objective_out: torch.Tensor | None = None, status_out: torch.Tensor | None = None,
+                 stats=True, **opts):
+    """dgs_solve_ex (stream-ordered): returns (status, sigma_out, objective,
+    stats dict).  With wait (default) the stream is synchronised and status is
+    the solve's outcome (dgs_stats.status); with wait=False a Pending whose
+    result() does that.  objective_out / status_out: optional CUDA tensors
+    (int64[1] / int32[1]) the device writes instead of host memory (the
+    returned objective is then 0); stats=False passes no stats (the call then
+    needs no host callback; the returned status is the call's).
 
     Keyword options: init, init_sigma (int32 CUDA tensor), seed (random
     start), reeval (DGS_REEVAL_BOX / DGS_REEVAL_ALL), algorithm
     (DGS_ALG_PARALLEL / DGS_ALG_SEQUENTIAL), evaluation (DGS_EVAL_TILE_PAIRS /
     DGS_EVAL_ROW_OWNER), max_sweeps, deadline_us, profile (1: time the first
-    evaluation and the greedy start), trace=(accepted int32, applied int32,
-    objective int64) CUDA tensors of equal length."""
+    evaluation and the greedy start; the call then waits), trace=(accepted
+    int32, applied int32, objective int64) CUDA tensors of equal length."""
     n = _n(benefit)
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
     o = _options(**opts)
+    if status_out is not None:
+        o.status_out = ctypes.c_void_p(status_out.data_ptr())
     f = ctypes.c_int64(0)
+    fp = ctypes.c_void_p(objective_out.data_ptr()) if objective_out is not None else \
+        ctypes.c_void_p(ctypes.addressof(f))
     s = dgs_stats()
-    st = load().dgs_solve_ex(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
-                             ctypes.byref(o), ctypes.byref(s), _stream(benefit, stream))
-    return st, sigma_out, int(f.value), s.as_dict()
+    st = load().dgs_solve_ex(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), fp,
+                             ctypes.byref(o), ctypes.byref(s) if stats else None, _stream(benefit, stream))
+    if not stats:
+        if wait and st == DGS_OK:
+            _wait(benefit, stream)
+        return st, sigma_out, int(f.value), {}
+    pending = Pending(st, benefit, stream, sigma_out, f, s)
+    return pending.result() if wait else pending
 
 
 def dgs_solve_rect(benefit: torch.Tensor, assign_out: torch.Tensor | None = None, stream=None, **opts):
-    """dgs_solve_rect: benefit is an n_agents x m_jobs int32 CUDA tensor;
-    returns (status, assign_out (job or -1 per agent), objective, stats)."""
+    """dgs_solve_rect (stream-ordered; this wrapper waits): benefit is an
+    n_agents x m_jobs int32 CUDA tensor; returns (status = the solve's
+    outcome, assign_out (job or -1 per agent), objective, stats)."""
     if benefit.ndim != 2:
         raise ValueError("benefit must be an n_agents x m_jobs matrix")
     n, m = int(benefit.shape[0]), int(benefit.shape[1])
@@ -286,7 +335,7 @@ def dgs_solve_rect(benefit: torch.Tensor, assign_out: torch.Tensor | None = None
     s = dgs_stats()
     st = load().dgs_solve_rect(_dev(benefit, "benefit"), n, m, _dev(assign_out, "assign_out"), ctypes.byref(f),
                                ctypes.byref(o), ctypes.byref(s), _stream(benefit, stream))
-    return st, assign_out, int(f.value), s.as_dict()
+    return Pending(st, benefit, stream, assign_out, f, s).result()
 
 
 def dgs_solve_host(benefit: np.ndarray, stream=None, device=None, **opts):
@@ -428,6 +477,9 @@ class Server:
 
     def dgs_server_wait(self, ticket: int, timeout_us: int = -1):
         return self._take(load().dgs_server_wait, ticket, ctypes.c_int64(int(timeout_us)))
+
+    def dgs_cancel(self, ticket: int) -> int:
+        return load().dgs_cancel(self._h, int(ticket))
 
     def dgs_server_get_info(self):
         info = dgs_server_info()

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdgs.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["k_greedy.cu", "k_evaluate.cu", "k_control.cu", "dgs_api.cu", "dgs_static.cu", "dgs_batch.cu", "k_sequential.cu",
-           "dgs_measure.cu"]
+           "dgs_measure.cu", "dgs_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

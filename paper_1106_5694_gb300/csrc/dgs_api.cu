@@ -53,6 +53,12 @@ std::mutex g_pool_mutex;
 cudaMemPool_t g_pools[64] = {};
 
 cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    // DGS_FAKE_OOM_BYTES (tests): requests of at least this many bytes fail
+    // as if the device were out of memory, without touching the device
+    if (const char* fk = std::getenv("DGS_FAKE_OOM_BYTES")) {
+        const long long lim = std::atoll(fk);
+        if (lim > 0 && bytes >= (size_t)lim) return cudaErrorMemoryAllocation;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -79,6 +85,18 @@ cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
         pool = g_pools[dev];
     }
     return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+int32_t device_sms() {
+    static int32_t cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
 }
 
 int32_t env_compact_min() {
@@ -112,6 +130,19 @@ thread_local char g_last_error[512] = "";
 
 namespace dgs {
 void set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+// The status a finished solve or evaluation returns for its loop state.
+dgs_status map_device_status(const DeviceState& h) {
+    if (h.status == kDone) return DGS_OK;
+    if (h.status == kTimeout) return DGS_TIMEOUT;
+    if (h.status == kError) {
+        if (h.error == kErrRange) return DGS_ERR_RANGE;
+        if (h.error == kErrUserInit) return DGS_ERR_INVALID;
+        snprintf(g_last_error, sizeof(g_last_error), "device-side error code %d", h.error);
+        return DGS_ERR_INTERNAL;
+    }
+    return DGS_OK;
+}
 }  // namespace dgs
 
 namespace {
@@ -176,9 +207,8 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
     w.g_col = ar.take<unsigned long long>(nb);
     w.free_a = ar.take<uint8_t>(nb);
     w.free_j = ar.take<uint8_t>(nb);
-    w.g_free_a = ar.take<uint32_t>(nb / 32);
-    w.g_free_j = ar.take<uint32_t>(nb / 32);
-    w.g_dirty = ar.take<uint32_t>(2 * nb / 32);
+    w.g_hold_v = ar.take<uint32_t>(nb);
+    w.g_prop = ar.take<int32_t>(nb);
     w.phase_ns = env_phase_timers() ? ar.take<unsigned long long>(kPtCount) : nullptr;
     w.st = ar.take<DeviceState>(1);
     *seen = ar.take<uint8_t>(4 * nb);
@@ -249,6 +279,8 @@ size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in) {
 namespace {
 using namespace dgs;
 
+__global__ void write_state_kernel(DeviceState* st, DeviceState h) { *st = h; }
+
 // Everything one call needs, released in the destructor (stream-ordered).
 struct Solve {
     cudaStream_t s;
@@ -306,9 +338,6 @@ struct Solve {
         const size_t nb = align_up((size_t)n, 128);
         e = cudaMemsetAsync(w.free_a, 1, nb, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.free_j, 1, nb, s);
-        // bitmaps: bits of agents/jobs >= n are never read
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_a, 0xFF, nb / 8, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.g_free_j, 0xFF, nb / 8, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         return DGS_OK;
     }
@@ -331,8 +360,11 @@ struct Solve {
             h.trace_applied = o->trace_applied;
             h.trace_objective = o->trace_objective;
         }
-        cudaError_t e = cudaMemcpyAsync(w.st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(state)");
+        // by a kernel argument: a copy from pageable host memory would wait
+        // for the stream
+        write_state_kernel<<<1, 1, 0, s>>>(w.st, h);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "loop state");
         return DGS_OK;
     }
 
@@ -424,18 +456,6 @@ __global__ void fill_synthetic_kernel(int32_t* a, int32_t n, int32_t lda, uint64
     }
 }
 
-dgs_status map_device_status(const DeviceState& h) {
-    if (h.status == kDone) return DGS_OK;
-    if (h.status == kTimeout) return DGS_TIMEOUT;
-    if (h.status == kError) {
-        if (h.error == kErrRange) return DGS_ERR_RANGE;
-        if (h.error == kErrUserInit) return DGS_ERR_INVALID;
-        snprintf(g_last_error, sizeof(g_last_error), "device-side error code %d", h.error);
-        return DGS_ERR_INTERNAL;
-    }
-    return DGS_OK;
-}
-
 #define DGS_TRY(expr)                          \
     do {                                       \
         dgs_status _st = (expr);               \
@@ -447,83 +467,105 @@ dgs_status map_device_status(const DeviceState& h) {
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
-// Greedy rounds until every agent is matched (or an error).
+// ------------------------------------------------ device-side loop bodies
+struct LoopCtx {
+    Workspace w;
+    CtlGlobal ctl;
+};
+
+// Everything the loop bodies' launches are captured with: the workspace and
+// controller pointers and sizes, and the evaluation's launch shape for n.
+struct LoopKey {
+    unsigned char w[sizeof(Workspace)];
+    unsigned char ctl[sizeof(CtlGlobal)];
+    int32_t rows, strip, tma, pad;
+};
+
+LoopKey loop_key(const LoopCtx& c) {
+    LoopKey k;
+    memset(&k, 0, sizeof(k));
+    memcpy(k.w, &c.w, sizeof(Workspace));
+    memcpy(k.ctl, &c.ctl, sizeof(CtlGlobal));
+    const EvalShape sh = evaluation_shape(c.w.n);
+    k.rows = sh.rows;
+    k.strip = sh.strip;
+    k.tma = sh.tma;
+    return k;
+}
+
+dgs_status enqueue_loop(cudaStream_t s, LoopBody body, LoopCtx* c) {
+    const LoopKey k = loop_key(*c);
+    return enqueue_while_cached(s, body, c, &k, sizeof(k));
+}
+
+// One locally-dominant greedy round and its loop condition.
+dgs_status greedy_round_body(void* p, cudaStream_t cs, unsigned long long h) {
+    const LoopCtx* c = static_cast<const LoopCtx*>(p);
+    DGS_CUDA(launch_greedy_round(c->w, cs), "greedy round");
+    DGS_CUDA(launch_greedy_loop_cond(c->w, h, cs), "greedy loop");
+    return DGS_OK;
+}
+
+// One iteration of the switching loop of Algorithm 3: re-evaluate what the
+// last committing sweep changed (marked rows by row tasks, or all rows by a
+// full evaluation), refresh the slots not in C, then the controller's sweeps;
+// the controller decides whether the loop goes on.
+dgs_status switching_body(void* p, cudaStream_t cs, unsigned long long h) {
+    const LoopCtx* c = static_cast<const LoopCtx*>(p);
+    DGS_CUDA(launch_mark_rescan(c->w, cs), "mark");
+    DGS_CUDA(launch_full_evaluation(c->w, 1, cs), "re-evaluation");
+    DGS_CUDA(launch_row_tasks(c->w, cs), "row tasks");
+    DGS_CUDA(launch_prepare_edges(c->w, cs), "prepare");
+    DGS_CUDA(launch_controller_impl(c->w, c->ctl, cs, h), "controller");
+    return DGS_OK;
+}
+
+// Algorithm 1: the switching loop of one pass (launches until the loop ends).
+dgs_status sequential_inner_body(void* p, cudaStream_t cs, unsigned long long h) {
+    const LoopCtx* c = static_cast<const LoopCtx*>(p);
+    DGS_CUDA(launch_sequential(c->w, cs), "switching loop");
+    DGS_CUDA(launch_seq_inner_cond(c->w, h, cs), "switching loop condition");
+    return DGS_OK;
+}
+
+// Algorithm 1: one pass of the outer repeat (fresh evaluation of every slot,
+// the switching loop), repeated while a pass changes f.
+dgs_status sequential_pass_body(void* p, cudaStream_t cs, unsigned long long h) {
+    LoopCtx* c = static_cast<LoopCtx*>(p);
+    unsigned long long inner = 0;
+    DGS_TRY(create_loop_handle(cs, &inner));
+    DGS_CUDA(launch_seq_pass_begin(c->w, inner, cs), "pass");
+    // the evaluation raises the row keys from zero (slot i reads the key of
+    // row tau(i), so the keys cannot be cleared while the slots are read)
+    DGS_CUDA(cudaMemsetAsync(c->w.key_a, 0, (size_t)c->w.n * sizeof(unsigned long long), cs), "clear keys");
+    DGS_CUDA(cudaMemsetAsync(c->w.key_j, 0, (size_t)c->w.n * sizeof(unsigned long long), cs), "clear keys");
+    DGS_CUDA(launch_full_evaluation(c->w, 0, cs), "evaluation");
+    DGS_CUDA(launch_slots_from_keys(c->w, cs), "slots");
+    DGS_TRY(capture_while(cs, sequential_inner_body, c, inner));
+    DGS_CUDA(launch_seq_pass_end(c->w, h, cs), "pass condition");
+    return DGS_OK;
+}
+
+// The greedy start: pass 1, then deferred acceptance in one cooperative
+// launch; where that launch is refused, pass 1 again with the column keys and
+// the locally-dominant rounds as a device-side loop (the same assignment).
 dgs_status run_greedy(Solve& S, EventPair* timer) {
-    DGS_CUDA(launch_greedy_pass1(S.w, S.s), "greedy pass 1");
+    DGS_CUDA(launch_greedy_pass1_cols(S.w, 0, S.s), "greedy pass 1");
     S.launches += 1;
     if (timer) DGS_TRY(timer->begin(S.s));
-    const cudaError_t pe = launch_greedy_persistent(S.w, S.s);
+    const cudaError_t pe = launch_greedy_da(S.w, S.s);
     if (pe == cudaSuccess) {
-        S.launches += 1;
+        S.launches += 2;
         if (timer) DGS_TRY(timer->end(S.s));
         return DGS_OK;
     }
-    // the cooperative launch was refused: one launch per kernel per round
     cudaGetLastError();
-    const int32_t batch = 8;
-    for (int32_t launched = 0; launched <= S.w.n + batch; launched += batch) {
-        for (int32_t r = 0; r < batch; ++r) DGS_CUDA(launch_greedy_round(S.w, S.s), "greedy round");
-        S.launches += 3 * batch;
-        DeviceState h;
-        DGS_TRY(S.read_state(&h));
-        if (h.status != kRunning || h.greedy_remaining == 0) {
-            if (timer) DGS_TRY(timer->end(S.s));
-            return DGS_OK;
-        }
-    }
-    snprintf(g_last_error, sizeof(g_last_error), "greedy start did not finish");
-    return DGS_ERR_INTERNAL;
-}
-
-// Algorithm 1 after the start: passes of (fresh evaluation of every slot,
-// switching loop on one CTA) until a pass leaves f unchanged.
-dgs_status run_sequential(Solve& S, int32_t* sigma_out, int64_t* objective_out, const dgs_options& o,
-                          dgs_stats* stats, EventPair& gev) {
-    cudaStream_t stream = S.s;
-    S.launches += 2;
-    DeviceState h;
-    const int64_t max_passes = 4 * (int64_t)S.w.n + 16;
-    bool ended = false;
-    for (int64_t pass = 0; pass < max_passes && !ended; ++pass) {
-        DGS_TRY(S.read_state(&h));
-        if (h.status != kRunning) break;
-        const int64_t f_start = h.f;
-        DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
-        DGS_CUDA(launch_slots_from_keys(S.w, stream), "slots");
-        S.launches += 2;
-        for (int64_t launch = 0;; ++launch) {
-            DGS_CUDA(launch_sequential(S.w, stream), "switching loop");
-            S.launches += 1;
-            DGS_TRY(S.read_state(&h));
-            if (h.status != kRunning || !h.need_update) break;
-            if (launch > 64) {
-                snprintf(g_last_error, sizeof(g_last_error), "switching loop did not finish");
-                return DGS_ERR_INTERNAL;
-            }
-        }
-        if (h.status != kRunning || h.f == f_start) ended = true;
-    }
-    if (!ended) {
-        snprintf(g_last_error, sizeof(g_last_error), "sequential passes did not finish");
-        return DGS_ERR_INTERNAL;
-    }
-    DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
+    DGS_CUDA(launch_greedy_pass1_cols(S.w, 1, S.s), "greedy pass 1");
     S.launches += 1;
-    DGS_TRY(S.read_state(&h));
-    const dgs_status status = h.status == kRunning ? DGS_OK : map_device_status(h);
-    *objective_out = h.f;
-    if (stats) {
-        memset(stats, 0, sizeof(*stats));
-        stats->sweeps = h.sweeps;
-        stats->events = h.events;
-        stats->swaps_applied = h.swaps;
-        stats->greedy_rounds = h.greedy_rounds;
-        stats->initial_objective = h.f_initial;
-        stats->kernel_launches = S.launches;
-        stats->greedy_ms = (o.profile && o.init == DGS_INIT_GREEDY) ? gev.elapsed_ms() : 0.0;
-        stats->greedy_rescans = h.greedy_rescans;
-    }
-    return status;
+    LoopCtx c{S.w, S.ctl};
+    DGS_TRY(enqueue_loop(S.s, greedy_round_body, &c));
+    if (timer) DGS_TRY(timer->end(S.s));
+    return DGS_OK;
 }
 
 dgs_status check_common(const int32_t* benefit, int32_t n) {
@@ -531,8 +573,88 @@ dgs_status check_common(const int32_t* benefit, int32_t n) {
     return DGS_OK;
 }
 
+// The public status of a finished loop state, without touching the calling
+// thread's error text (used from stream callbacks).
+dgs_status status_of(const DeviceState& h) {
+    if (h.status == kTimeout) return DGS_TIMEOUT;
+    if (h.status != kError) return DGS_OK;
+    if (h.error == kErrRange) return DGS_ERR_RANGE;
+    if (h.error == kErrUserInit) return DGS_ERR_INVALID;
+    return DGS_ERR_INTERNAL;
+}
+
+// What a solve reports on the host once the stream reaches its end: a copy
+// of the final loop state in pinned memory is read by a host callback that
+// fills the caller's host-side outputs and returns the staging blocks.
+struct Completion {
+    DeviceState* staged = nullptr;
+    void* release = nullptr;  // pinned block of the call (the random start), or null
+    size_t release_bytes = 0;
+    dgs_stats* stats = nullptr;
+    int64_t* objective = nullptr;  // host objective (a device one is written by the finish kernel)
+    int32_t* status = nullptr;     // host options.status_out
+    dgs_status* status_api = nullptr;
+    int64_t launches = 0;          // kernels launched from the host
+    int32_t sequential = 0;
+    ~Completion() {
+        pinned_put(staged, sizeof(DeviceState));
+        pinned_put(release, release_bytes);
+    }
+};
+
+void fill_stats(const DeviceState& h, const Completion& c, dgs_stats* stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->sweeps = h.sweeps;
+    stats->events = h.events;
+    stats->swaps_applied = h.swaps;
+    stats->greedy_rounds = h.greedy_rounds;
+    stats->full_evaluations = c.sequential ? 0 : h.full_evals + 1;
+    stats->row_updates = c.sequential ? 0 : h.row_updates;
+    stats->rows_recomputed = c.sequential ? 0 : h.rows_recomputed;
+    stats->initial_objective = h.f_initial;
+    stats->kernel_launches = c.launches + h.loop_launches;
+    stats->greedy_rescans = h.greedy_rescans;
+    stats->status = status_of(h);
+}
+
+void CUDART_CB completion_callback(void* p) {
+    Completion* c = static_cast<Completion*>(p);
+    const DeviceState& h = *c->staged;
+    const dgs_status st = status_of(h);
+    if (c->objective) *c->objective = h.f;
+    if (c->status) *c->status = (int32_t)st;
+    if (c->status_api) *c->status_api = st;
+    if (c->stats) fill_stats(h, *c, c->stats);
+    delete c;
+}
+
+// The random start's permutation, staged in pinned memory for its copy to
+// the device; the block returns to the cache with the call's completion (or
+// after the stream drains, on an error path).
+struct PinnedStart {
+    cudaStream_t s;
+    void* p = nullptr;
+    size_t bytes = 0;
+    bool copied = false;
+    explicit PinnedStart(cudaStream_t st) : s(st) {}
+    ~PinnedStart() {
+        if (p == nullptr) return;
+        if (copied) cudaStreamSynchronize(s);
+        pinned_put(p, bytes);
+    }
+    void* release() {
+        void* q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+// One solve, enqueued on `stream`.  final_status (host, may be null): set to
+// the solve's status when the stream reaches its end.  extra_launches: kernels
+// the caller launches around the solve (counted in the stats).
 dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
-                      const dgs_options* opt, dgs_stats* stats, cudaStream_t stream) {
+                      const dgs_options* opt, dgs_stats* stats, cudaStream_t stream,
+                      dgs_status* final_status = nullptr, int64_t extra_launches = 0) {
     DGS_TRY(check_common(benefit, n));
     if (sigma_out == nullptr || objective_out == nullptr) return DGS_ERR_INVALID;
     dgs_options o;
@@ -546,22 +668,37 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     if (o.algorithm != DGS_ALG_PARALLEL && o.algorithm != DGS_ALG_SEQUENTIAL) return DGS_ERR_INVALID;
     if (o.evaluation != DGS_EVAL_TILE_PAIRS && o.evaluation != DGS_EVAL_ROW_OWNER) return DGS_ERR_INVALID;
 
+    // where the objective and the status go: written by the finish kernel when
+    // the device can write them, else by the completion callback
+    void* obj_dev = nullptr;
+    const bool obj_on_device = device_writable(objective_out, &obj_dev);
+    void* status_dev = nullptr;
+    const bool status_on_device = o.status_out != nullptr && device_writable(o.status_out, &status_dev);
+
+    EventPair whole;
+    if (o.profile) DGS_TRY(whole.begin(stream));
     Solve S(stream);
     DGS_TRY(S.setup(benefit, n, true));
     S.w.row_owner_eval = o.evaluation == DGS_EVAL_ROW_OWNER ? 1 : 0;
     // the random start is drawn on the host and enters as the caller's start
     DeviceBuffer rnd(stream);
+    PinnedStart pin(stream);
     if (o.init == DGS_INIT_RANDOM) {
-        std::vector<int32_t> perm(n);
-        random_start(n, o.seed, perm.data());
-        DGS_TRY(rnd.alloc((size_t)n * sizeof(int32_t)));
-        DGS_CUDA(cudaMemcpyAsync(rnd.p, perm.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, stream),
-                 "copy random start");
-        DGS_CUDA(cudaStreamSynchronize(stream), "copy random start");  // perm is released on return
+        pin.bytes = (size_t)n * sizeof(int32_t);
+        pin.p = pinned_get(pin.bytes);
+        if (pin.p == nullptr) {
+            snprintf(g_last_error, sizeof(g_last_error), "pinned staging of %zu bytes", pin.bytes);
+            return DGS_ERR_OOM;
+        }
+        random_start(n, o.seed, static_cast<int32_t*>(pin.p));
+        DGS_TRY(rnd.alloc(pin.bytes));
+        DGS_CUDA(cudaMemcpyAsync(rnd.p, pin.p, pin.bytes, cudaMemcpyHostToDevice, stream), "copy random start");
+        pin.copied = true;
         o.init = DGS_INIT_USER;
         o.init_sigma = static_cast<const int32_t*>(rnd.p);
     }
     DGS_TRY(S.init_state(o.max_sweeps, &o));
+    S.launches += 1;
     if (o.deadline_us > 0) {
         arm_deadline_kernel<<<1, 1, 0, stream>>>(S.w.st, o.deadline_us);
         DGS_CUDA(cudaGetLastError(), "arm deadline");
@@ -576,65 +713,68 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     }
     DGS_CUDA(launch_start_from_tau(S.w, o.init_sigma, o.init, S.seen, stream), "start");
     record_initial_objective_kernel<<<1, 1, 0, stream>>>(S.w.st);
-    if (o.algorithm == DGS_ALG_SEQUENTIAL) return run_sequential(S, sigma_out, objective_out, o, stats, gev);
+    S.launches += 2;
     EventPair ev;
-    if (o.profile) DGS_TRY(ev.begin(stream));
-    DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
-    if (o.profile) DGS_TRY(ev.end(stream));
-    DGS_CUDA(launch_prepare_edges(S.w, stream), "prepare");
-    DGS_CUDA(launch_controller_impl(S.w, S.ctl, stream), "controller");
-    S.launches += 5;
-    DeviceState h;
-    const int32_t batch = 4;
-    const int64_t max_iterations = 16 * (int64_t)n + 4096;
-    bool ended = false;
-    for (int64_t it = 0; it < max_iterations; it += batch) {
-        DGS_TRY(S.read_state(&h));
-        if (h.status != kRunning) {
-            ended = true;
-            break;
-        }
-        for (int32_t b = 0; b < batch; ++b) {
-            DGS_CUDA(launch_mark_rescan(S.w, stream), "mark");
-            DGS_CUDA(launch_full_evaluation(S.w, 1, stream), "re-evaluation");
-            DGS_CUDA(launch_row_tasks(S.w, stream), "row tasks");
-            DGS_CUDA(launch_prepare_edges(S.w, stream), "prepare");
-            DGS_CUDA(launch_controller_impl(S.w, S.ctl, stream), "controller");
-            S.launches += 5;
-        }
+    LoopCtx lc{S.w, S.ctl};
+    if (o.algorithm == DGS_ALG_SEQUENTIAL) {
+        DGS_TRY(enqueue_loop(stream, sequential_pass_body, &lc));
+    } else {
+        if (o.profile) DGS_TRY(ev.begin(stream));
+        DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
+        S.launches += 1;
+        if (o.profile) DGS_TRY(ev.end(stream));
+        DGS_TRY(enqueue_loop(stream, switching_body, &lc));
     }
-    if (!ended) {
-        snprintf(g_last_error, sizeof(g_last_error), "switching loop did not finish");
-        return DGS_ERR_INTERNAL;
-    }
-    DGS_CUDA(launch_finish(S.w, sigma_out, stream), "finish");
+    DGS_CUDA(launch_finish_outputs(S.w, sigma_out, obj_on_device ? static_cast<int64_t*>(obj_dev) : nullptr,
+                                   status_on_device ? static_cast<int32_t*>(status_dev) : nullptr, stream),
+             "finish");
     S.launches += 1;
-    DGS_TRY(S.read_state(&h));
-    if (S.w.phase_ns) {  // test/diagnostic output only
+    if (o.profile) DGS_TRY(whole.end(stream));  // the device work of the solve ends here
+    const bool host_outputs = stats != nullptr || !obj_on_device || (o.status_out && !status_on_device) ||
+                              final_status != nullptr || pin.p != nullptr;
+    if (host_outputs) {
+        Completion* c = new Completion();
+        c->staged = static_cast<DeviceState*>(pinned_get(sizeof(DeviceState)));
+        if (c->staged == nullptr) {
+            delete c;
+            snprintf(g_last_error, sizeof(g_last_error), "pinned staging of the loop state");
+            return DGS_ERR_OOM;
+        }
+        c->stats = stats;
+        c->objective = obj_on_device ? nullptr : objective_out;
+        c->status = (o.status_out && !status_on_device) ? o.status_out : nullptr;
+        c->status_api = final_status;
+        c->launches = S.launches + extra_launches;
+        c->sequential = o.algorithm == DGS_ALG_SEQUENTIAL ? 1 : 0;
+        cudaError_t e = cudaMemcpyAsync(c->staged, S.w.st, sizeof(DeviceState), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaLaunchHostFunc(stream, completion_callback, c);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(stream);  // the copy may be in flight
+            delete c;
+            return cuda_fail(e, "completion");
+        }
+        c->release_bytes = pin.bytes;
+        c->release = pin.release();  // returned by the callback
+    }
+    if (S.w.phase_ns) {  // test/diagnostic output only: waits for the solve
         unsigned long long ph[kPtCount];
-        if (cudaMemcpy(ph, S.w.phase_ns, sizeof(ph), cudaMemcpyDeviceToHost) == cudaSuccess) {
-            fprintf(stderr, "[dgs phases] greedy ns: match %llu bar1 %llu check %llu scan %llu bar2 %llu scanmax %llu | "
-                            "controller cycles: entry %llu top %llu conflict check %llu post %llu event %llu sweeps %llu\n",
-                    ph[0], ph[1], ph[2], ph[3], ph[4], ph[5], ph[8], ph[9], ph[10], ph[13], ph[14], ph[15]);
+        if (cudaMemcpyAsync(ph, S.w.phase_ns, sizeof(ph), cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+            cudaStreamSynchronize(stream) == cudaSuccess) {
+            fprintf(stderr, "[dgs phases] greedy: last group %llu ns, group sum %llu ns, longest chain %llu, "
+                            "most scans of a group %llu | controller cycles: entry %llu top %llu conflict check %llu "
+                            "post %llu event %llu sweeps %llu\n",
+                    ph[0], ph[1], ph[2], ph[3], ph[8], ph[9], ph[10], ph[13], ph[14], ph[15]);
         }
     }
-    const dgs_status status = map_device_status(h);
-    *objective_out = h.f;
-    if (stats) {
-        stats->sweeps = h.sweeps;
-        stats->events = h.events;
-        stats->swaps_applied = h.swaps;
-        stats->greedy_rounds = h.greedy_rounds;
-        stats->full_evaluations = h.full_evals + 1;
-        stats->row_updates = h.row_updates;
-        stats->rows_recomputed = h.rows_recomputed;
-        stats->initial_objective = h.f_initial;
-        stats->kernel_launches = S.launches;
-        stats->evaluation_ms = o.profile ? ev.elapsed_ms() : 0.0;
-        stats->greedy_ms = (o.profile && o.init == DGS_INIT_GREEDY) ? gev.elapsed_ms() : 0.0;
-        stats->greedy_rescans = h.greedy_rescans;
+    if (o.profile) {  // the event timings need the solve to have run
+        DGS_CUDA(cudaStreamSynchronize(stream), "profile");
+        if (stats) {
+            stats->solve_ms = whole.elapsed_ms();
+            stats->evaluation_ms = o.algorithm == DGS_ALG_SEQUENTIAL ? 0.0 : ev.elapsed_ms();
+            stats->greedy_ms = o.init == DGS_INIT_GREEDY ? gev.elapsed_ms() : 0.0;
+        }
     }
-    return status;
+    return DGS_OK;
 }
 
 }  // namespace
@@ -673,18 +813,18 @@ dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n, int32_t* sigma
     if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     int32_t* a_dev = reinterpret_cast<int32_t*>(buf + obytes);
     int32_t* out_dev = reinterpret_cast<int32_t*>(buf);
-    dgs_status st = DGS_OK;
+    dgs_status st = DGS_OK, outcome = DGS_OK;
     e = cudaMemcpyAsync(a_dev, benefit_host, abytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) st = cuda_fail(e, "copy benefit to device");
-    if (st == DGS_OK) st = solve_impl(a_dev, n, out_dev, objective_out, options, stats, s);
-    if (st == DGS_OK || st == DGS_TIMEOUT) {
+    if (st == DGS_OK) st = solve_impl(a_dev, n, out_dev, objective_out, options, stats, s, &outcome);
+    if (st == DGS_OK) {
         e = cudaMemcpyAsync(sigma_out_host, out_dev, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy result to host");
     }
     cudaFreeAsync(buf, s);
     cudaStreamSynchronize(s);
-    return st;
+    return st == DGS_OK ? outcome : st;
 }
 
 dgs_status dgs_solve_rect(const int32_t* benefit, int32_t n_agents, int32_t m_jobs, int32_t* assign_out,
@@ -703,15 +843,12 @@ dgs_status dgs_solve_rect(const int32_t* benefit, int32_t n_agents, int32_t m_jo
     DGS_TRY(buf.alloc(sq_bytes + (size_t)sz * sizeof(int32_t)));
     int32_t* sq = static_cast<int32_t*>(buf.p);
     int32_t* tau = reinterpret_cast<int32_t*>(static_cast<char*>(buf.p) + sq_bytes);
-    pad_square_kernel<<<152 * 8, 256, 0, s>>>(benefit, n_agents, m_jobs, sz, sq);
+    pad_square_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(benefit, n_agents, m_jobs, sz, sq);
     DGS_CUDA(cudaGetLastError(), "pad");
-    const dgs_status st = solve_impl(sq, sz, tau, objective_out, &o, stats, s);
-    if (st != DGS_OK && st != DGS_TIMEOUT) return st;
+    DGS_TRY(solve_impl(sq, sz, tau, objective_out, &o, stats, s, nullptr, 2));
     trim_assignment_kernel<<<(n_agents + 255) / 256, 256, 0, s>>>(tau, n_agents, m_jobs, assign_out);
     DGS_CUDA(cudaGetLastError(), "trim");
-    DGS_CUDA(cudaStreamSynchronize(s), "trim");
-    if (stats) stats->kernel_launches += 2;
-    return st;
+    return DGS_OK;
 }
 
 dgs_status dgs_evaluate(const int32_t* benefit, int32_t n, const int32_t* sigma_in, int32_t* agent_gain,
@@ -764,7 +901,7 @@ dgs_status dgs_autotune(int32_t n, dgs_tuning* result, dgs_stream_t stream) {
         Solve S(s);
         // a synthetic instance of this size with peer-like values, under a
         // random assignment (the evaluation's time does not depend on which)
-        fill_synthetic_kernel<<<152 * 8, 256, 0, s>>>(a, n, lda, 0x9E3779B97F4A7C15ull ^ (uint64_t)n);
+        fill_synthetic_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(a, n, lda, 0x9E3779B97F4A7C15ull ^ (uint64_t)n);
         std::vector<int32_t> perm(n);
         for (int32_t i = 0; i < n; ++i) perm[i] = i;
         uint64_t x = 0xD1B54A32D192ED03ull ^ (uint64_t)n;
@@ -858,6 +995,7 @@ const char* dgs_status_string(dgs_status status) {
         case DGS_PENDING: return "DGS_PENDING";
         case DGS_ERR_BUSY: return "DGS_ERR_BUSY";
         case DGS_ERR_INTERNAL: return "DGS_ERR_INTERNAL";
+        case DGS_CANCELLED: return "DGS_CANCELLED";
     }
     return "DGS_UNKNOWN";
 }

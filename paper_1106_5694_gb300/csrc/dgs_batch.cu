@@ -886,6 +886,27 @@ dgs_status dgs_server_wait(dgs_server* sv, uint64_t ticket, int64_t timeout_us, 
     return sv->pending.count(ticket) ? DGS_PENDING : DGS_ERR_INVALID;
 }
 
+dgs_status dgs_cancel(dgs_server* sv, uint64_t ticket) {
+    if (!sv) return DGS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto p = sv->pending.find(ticket);
+    if (p == sv->pending.end()) return DGS_ERR_INVALID;  // unknown, or already finished
+    if (p->second != 0) return DGS_PENDING;               // admitted: it runs to its end
+    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        dgs_server::Result r{};
+        r.status = DGS_CANCELLED;
+        r.times.submit_ns = it->submit_ns;
+        sv->queue.erase(it);
+        sv->pending.erase(p);
+        sv->results[ticket] = std::move(r);
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_one();  // the next request may fit now
+        return DGS_OK;
+    }
+    return DGS_PENDING;
+}
+
 dgs_status dgs_server_get_info(dgs_server* sv, dgs_server_info* info) {
     if (!sv || !info) return DGS_ERR_INVALID;
     std::lock_guard<std::mutex> lk(sv->mu);

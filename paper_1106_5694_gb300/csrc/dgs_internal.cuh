@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/dgs.h"
+
 namespace dgs {
 
 // ----------------------------------------------------------------- limits
@@ -66,6 +68,13 @@ struct DeviceState {
     int32_t* trace_accepted;
     int32_t* trace_applied;
     int64_t* trace_objective;
+    int32_t loop_iterations; // iterations of the device-side loops (bounded)
+    int32_t loop_launches;   // kernels those loops launched
+    int32_t seq_inner;       // Algorithm 1: launches of the current pass's switching loop
+    int32_t seq_passes;      // Algorithm 1: passes so far
+    int64_t f_pass;          // Algorithm 1: objective at the start of the current pass
+    int32_t da_next;         // greedy start (deferred acceptance): next agent to take
+    int32_t pad_state2;
 };
 
 // Pointers to every array of one solve (passed by value to kernels).
@@ -93,10 +102,11 @@ struct Workspace {
     int32_t* ctl_slot;  // controller: slot of each edge position (priority order)
     // greedy start
     unsigned long long* g_row;  // best free job per agent   (biased value, ~j)
-    unsigned long long* g_col;  // best free agent per job   (biased value, ~i)
+    unsigned long long* g_col;  // round form: best free agent per job (biased value, ~i);
+                                // deferred acceptance: the key (biased value, ~i) of the job's holder
     uint8_t* free_a; uint8_t* free_j;
-    uint32_t* g_free_a; uint32_t* g_free_j;  // free sets as bitmaps (persistent greedy)
-    uint32_t* g_dirty;                       // owners to rescan this round (persistent greedy)
+    uint32_t* g_hold_v;  // deferred acceptance: biased benefit of each job's holder (high word of g_col)
+    int32_t* g_prop;     // deferred acceptance: proposals made by each agent
     int32_t exact_keys;  // 1: never use the packed 32-bit keys (test knob)
     int32_t row_owner_eval;  // 1: full evaluations by row owners (A-transpose form)
     DeviceState* st;
@@ -190,17 +200,21 @@ __device__ __forceinline__ void for_each_item(const Instance* inst, const int32_
     }
 }
 
-// Blocks of the batched pass 1 and evaluation of an instance of size n (the
-// scan kernel and the host agree on them).
+// Blocks (work items) of the batched pass 1 and evaluation of an instance of
+// size n.  Only the scan kernel uses them; any count is correct (items are
+// spread over whatever grid consumes the queue), the caps only bound how
+// finely one instance is split.
+constexpr int32_t kBatchPass1MaxBlocks = 1216;
+constexpr int32_t kBatchEvalMaxBlocks = 152;
 __host__ __device__ __forceinline__ int32_t batch_blocks_pass1(int32_t n) {
     const int32_t t = (n + 63) / 64;
     const int32_t b = (t * t + 3) / 4;
-    return b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b);
+    return b < 1 ? 1 : (b > kBatchPass1MaxBlocks ? kBatchPass1MaxBlocks : b);
 }
 __host__ __device__ __forceinline__ int32_t batch_blocks_eval(int32_t n, int32_t strip) {
     const int32_t nb = (n + 63) / 64, chunks = (nb + strip - 1) / strip;
     const int32_t b = (nb * chunks + 1) / 2;
-    return b < 1 ? 1 : (b > 152 ? 152 : b);
+    return b < 1 ? 1 : (b > kBatchEvalMaxBlocks ? kBatchEvalMaxBlocks : b);
 }
 
 // Phases whose work counts the scan kernel computes.
@@ -208,7 +222,7 @@ enum : int32_t { kScanPass1 = 0, kScanGreedy = 1, kScanStart = 2, kScanSwitch = 
 
 // Phase timer slots.
 enum : int32_t {
-    kPtGreedyMatch = 0, kPtGreedyBar1, kPtGreedyCheck, kPtGreedyScan, kPtGreedyBar2, kPtGreedyScanMax,
+    kPtDaLastNs = 0, kPtDaSumNs, kPtDaChain, kPtDaGroupScans,
     kPtCtlEntry = 8, kPtCtlTop, kPtCtlPass1, kPtCtlPass2, kPtCtlUnd, kPtCtlPost, kPtCtlEvent, kPtCtlSweeps,
     kPtCount = 16
 };
@@ -313,9 +327,15 @@ __device__ __forceinline__ bool grid_barrier(DeviceState* st) {
 // Each returns the launch error (cudaSuccess on success).
 cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s);
 cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s);
-// All greedy rounds in one cooperative launch; returns cudaErrorNotSupported
-// (nothing launched) when the grid cannot be co-resident.
-cudaError_t launch_greedy_persistent(const Workspace& w, cudaStream_t s);
+// The greedy start by deferred acceptance (pass 1 must have run without
+// column keys, g_col zero); then the assignment is read off the jobs'
+// holders.  Returns an error (nothing launched) when the launch is refused
+// or DGS_GREEDY_ROUNDS=1; the caller then runs pass 1 with column keys and
+// the locally-dominant rounds (launch_greedy_round).
+cudaError_t launch_greedy_da(const Workspace& w, cudaStream_t s);
+// Pass 1 with (cols = 1) or without (cols = 0) the column keys g_col that the
+// locally-dominant rounds need.
+cudaError_t launch_greedy_pass1_cols(const Workspace& w, int32_t cols, cudaStream_t s);
 cudaError_t launch_range_check(const Workspace& w, cudaStream_t s);
 cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, int32_t mode, uint8_t* seen,
                                   cudaStream_t s);
@@ -333,7 +353,10 @@ int32_t size_bucket(int32_t n);
 cudaError_t launch_full_evaluation_shape(const Workspace& w, int32_t conditional, EvalShape shape, cudaStream_t s);
 cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja,
                                  cudaStream_t s);
-cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s);
+// handle != 0: the controller ends each launch by setting that loop
+// condition (1 while the loop state is running) and counts the iteration.
+cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s,
+                                   unsigned long long handle = 0);
 int32_t controller_list_cap(int32_t n, int32_t mode);
 int32_t controller_smem_mode(int32_t n);
 size_t controller_smem_bytes(int32_t n);
@@ -344,7 +367,19 @@ cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s);
 cudaError_t launch_row_owner_evaluation(const Workspace& w, int32_t conditional, cudaStream_t s);
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s);
-// Algorithm 1: slots of a fresh evaluation (from the keys, which it clears),
+// The outputs of a solve: sigma_out (every entry -1 after an error), and,
+// where not null, the objective and the final dgs_status code (device-
+// writable pointers).
+cudaError_t launch_finish_outputs(const Workspace& w, int32_t* sigma_out, int64_t* objective, int32_t* status,
+                                  cudaStream_t s);
+// Loop conditions of the device-side loops (see enqueue_while): the greedy
+// rounds' loop (while agents are unmatched), and Algorithm 1's switching loop
+// and passes.
+cudaError_t launch_greedy_loop_cond(const Workspace& w, unsigned long long handle, cudaStream_t s);
+cudaError_t launch_seq_pass_begin(const Workspace& w, unsigned long long inner, cudaStream_t s);
+cudaError_t launch_seq_inner_cond(const Workspace& w, unsigned long long inner, cudaStream_t s);
+cudaError_t launch_seq_pass_end(const Workspace& w, unsigned long long outer, cudaStream_t s);
+// Algorithm 1: slots of a fresh evaluation (from the keys, left as they are),
 // and one launch of the single-CTA switching loop (need_update = 1 when the
 // launch stopped at its iteration budget before the loop ended).
 cudaError_t launch_slots_from_keys(const Workspace& w, cudaStream_t s);
@@ -378,6 +413,40 @@ cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s);
 cudaError_t launch_b_finish(const BatchTable& rows, cudaStream_t s);
 cudaError_t launch_b_advance(const BatchTable& one, int32_t from_stage, cudaStream_t s);
 
+// ------------------------------------------------------ device-side loops
+// Enqueue on stream s a CUDA graph whose one node is a conditional WHILE
+// loop; `body` enqueues the loop body on the capture stream it is given and
+// passes `handle` to the kernel that decides, at the end of each iteration,
+// whether the loop goes on (cudaGraphSetConditional; the condition is 1 when
+// the body first runs).  The graph is released as soon as it is launched (an
+// executable graph in flight is freed when it completes): the call only
+// enqueues work.  `nested` bodies may themselves call capture_while on their
+// capture stream to add an inner loop; such a loop's condition is set to 1
+// at the start of the graph's launch only, so a body that runs an inner loop
+// re-arms it itself: it creates the inner handle first (create_loop_handle on
+// its capture stream), sets it from a kernel, and passes it to capture_while.
+using LoopBody = dgs_status (*)(void* ctx, cudaStream_t capture, unsigned long long handle);
+dgs_status enqueue_while(cudaStream_t s, LoopBody body, void* ctx);
+// The same, reusing an executable graph captured earlier on this device with
+// the same body and the same `key` bytes (which must cover every value the
+// body's launches are captured with); up to 16 are kept.
+dgs_status enqueue_while_cached(cudaStream_t s, LoopBody body, void* ctx, const void* key, size_t key_bytes);
+dgs_status create_loop_handle(cudaStream_t capturing, unsigned long long* handle);
+dgs_status capture_while(cudaStream_t capturing, LoopBody body, void* ctx, unsigned long long handle = 0);
+// Pinned host staging blocks from a process-wide cache (never freed while the
+// process runs; pinned_put may be called from a stream callback).
+void* pinned_get(size_t bytes);
+void pinned_put(void* p, size_t bytes);
+
+// Where a result pointer lives: device-writable (device, managed or mapped
+// pinned host memory; *alias = the address kernels use) or plain host memory
+// (written by a host callback when the stream reaches it).
+bool device_writable(const void* p, void** alias);
+
+// Streaming multiprocessors of the current device (queried once per device;
+// grids of the persistent and grid-stride kernels are multiples of it).
+int32_t device_sms();
+
 // Raise a kernel's dynamic shared memory limit once per device (slot = one
 // small integer per kernel).
 inline cudaError_t ensure_smem_limit(const void* func, int slot, size_t bytes) {
@@ -406,6 +475,10 @@ __host__ __device__ __forceinline__ bool use_full_update(int32_t rescans, int32_
 int32_t env_update_policy();
 // Store the text returned by dgs_last_cuda_error() for this thread.
 void set_last_error(const char* msg);
+// The public status of a finished call for its device loop state (kDone: OK,
+// kTimeout: DGS_TIMEOUT, kError: by the device error code; an unknown code is
+// DGS_ERR_INTERNAL with its number in dgs_last_cuda_error()).
+dgs_status map_device_status(const DeviceState& h);
 int32_t env_controller_mode_cap();
 // DGS_SHORT_WRAPS=1 shortens the controller's key and stamp periods so that
 // tests reach their wrap-around paths.

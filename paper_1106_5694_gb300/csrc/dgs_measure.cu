@@ -4,7 +4,7 @@
 // L2-resident matrix is bounded by this read rate instead).
 //
 // Every launch reads the whole buffer once with 16-byte loads, four in flight
-// per thread, 152 x 4 CTAs of 512 threads; the loaded words are folded into
+// per thread, 4 CTAs of 512 threads per SM; the loaded words are folded into
 // one value per thread that is written only if it equals a constant no
 // buffer of real data produces in practice (the store keeps the loads
 // live).  One untimed launch first brings a buffer that fits into L2; the
@@ -12,6 +12,7 @@
 #include <cstdio>
 
 #include "../../include/dgs.h"
+#include "dgs_internal.cuh"
 
 namespace {
 
@@ -51,9 +52,9 @@ extern "C" dgs_status dgs_read_bandwidth(const void* buffer, size_t bytes, int32
         return DGS_ERR_CUDA;
     }
     dgs_status st = DGS_OK;
-    read_kernel<<<152 * 4, 512, 0, s>>>(p, n16);  // brings a buffer that fits into L2
+    read_kernel<<<dgs::device_sms() * 4, 512, 0, s>>>(p, n16);  // brings a buffer that fits into L2
     cudaEventRecord(e0, s);
-    for (int32_t r = 0; r < repeats; ++r) read_kernel<<<152 * 4, 512, 0, s>>>(p, n16);
+    for (int32_t r = 0; r < repeats; ++r) read_kernel<<<dgs::device_sms() * 4, 512, 0, s>>>(p, n16);
     cudaEventRecord(e1, s);
     float ms = 0.0f;
     if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

@@ -4,18 +4,26 @@
 //
 // The array lives at file scope below.  Its name, used in host code, is only
 // a host-side stand-in for the device object: handing it to a kernel would
-// make the kernel read the wrong memory or fault.  The device address is
-// obtained once per device with cudaGetSymbolAddress (with that device
-// current) and cached; that lookup happens inside the first call on each
-// device, which should therefore come before any stream capture.
+// make the kernel read the wrong memory or fault.  Each call obtains the
+// device address with cudaGetSymbolAddress, with the call's device current,
+// and passes that address to the kernels.
 //
 // Every call reuses the same array and leaves its contents behind; the parts
-// that must start at zero (row keys, permutation check, loop state) are
-// cleared on each call.  Two calls whose work overlaps on the GPU (different
-// streams, different host threads) race on the array and must be serialised
-// by the caller.
+// that must start at zero (row keys, the assignment, the permutation check,
+// the loop state) are cleared on each call.  Two calls whose work overlaps on
+// the GPU (different streams, different host threads) race on the array and
+// must be serialised by the caller.
+//
+// The array is device memory of this library's module.  With lazy module
+// loading (the toolkit's default) the module, and with it the array, is
+// loaded and committed on a device the first time the library needs it
+// there, which may be inside the first call of this entry point: that first
+// call can therefore fail for lack of device memory, and callers that must
+// not allocate make it during their set-up (or run with
+// CUDA_MODULE_LOADING=EAGER, which commits the array when the library's
+// context is created).  The address is looked up on every call (a cheap
+// query), so it stays right after a cudaDeviceReset reloads the module.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
@@ -39,23 +47,12 @@ constexpr size_t kStaticBytes = kOffState + align256(sizeof(DeviceState));
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-std::mutex g_mutex;
-void* g_scratch_addr[64] = {};
-
-// Device address of g_static_scratch on the current device (looked up once).
+// Device address of g_static_scratch on the current device.
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -105,8 +102,11 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
     w.exact_keys = env_exact_keys();
     w.st = reinterpret_cast<DeviceState*>(base + kOffState);
 
-    // what must start at zero: row keys, the permutation check, the loop state
+    // what must start at zero: row keys, the assignment (so that the outputs
+    // of a failed call never show another call's keys), the permutation
+    // check, the loop state
     e = cudaMemsetAsync(w.key_a, 0, kOffSeen - kOffKeyA, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.tau, 0, 4 * (size_t)kStaticMaxN, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(seen, 0, 4 * (size_t)n, s);
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
@@ -125,6 +125,5 @@ extern "C" DGS_API dgs_status dgs_evaluate_static(const int32_t* benefit, int32_
         set_last_error(cudaGetErrorString(e));
         return DGS_ERR_CUDA;
     }
-    if (h.status == kError) return h.error == kErrRange ? DGS_ERR_RANGE : DGS_ERR_INVALID;
-    return DGS_OK;
+    return map_device_status(h);
 }

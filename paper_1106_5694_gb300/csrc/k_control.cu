@@ -30,6 +30,7 @@
 // controller is launched again and refreshes every slot not in C.
 #include <algorithm>
 
+#include "../../include/dgs.h"
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -529,11 +530,26 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     __syncthreads();  // shared memory is reused by the caller's next call
 }
 
+// cond != 0: the launch is the last kernel of an iteration of the device-
+// side switching loop (a conditional WHILE graph node, five kernels per
+// iteration); it sets the loop condition from the loop state.  The loop is
+// bounded: more than 16 n + 4096 iterations is an internal error.
 template <typename EdgeT>
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
                                                                    uint32_t span, uint32_t stamp_wrap,
-                                                                   int32_t list_cap, int32_t compact_min) {
+                                                                   int32_t list_cap, int32_t compact_min,
+                                                                   unsigned long long cond) {
     controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min);
+    if (cond != 0 && threadIdx.x == 0) {
+        DeviceState* st = w.st;
+        const int32_t it = ++st->loop_iterations;
+        st->loop_launches += 5;
+        if (st->status == kRunning && it > 16 * w.n + 4096) {
+            st->error = kErrInternal;
+            st->status = kError;
+        }
+        cudaGraphSetConditional(cond, st->status == kRunning ? 1u : 0u);
+    }
 }
 
 // Before each controller launch: clear the marks of the last event, re-
@@ -838,6 +854,27 @@ __global__ void finish_kernel(Workspace w, int32_t* sigma_out) {
         sigma_out[i] = w.tau[i];
 }
 
+// The dgs_status code of a finished loop state (the device side of
+// map_device_status).
+__device__ __forceinline__ int32_t device_status_code(const DeviceState* st) {
+    if (st->status == kTimeout) return DGS_TIMEOUT;
+    if (st->status != kError) return DGS_OK;
+    if (st->error == kErrRange) return DGS_ERR_RANGE;
+    if (st->error == kErrUserInit) return DGS_ERR_INVALID;
+    return DGS_ERR_INTERNAL;
+}
+
+__global__ void finish_outputs_kernel(Workspace w, int32_t* sigma_out, int64_t* objective, int32_t* status) {
+    const DeviceState* st = w.st;
+    const bool failed = st->status == kError;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x)
+        sigma_out[i] = failed ? -1 : w.tau[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (objective) *objective = st->f;
+        if (status) *status = device_status_code(st);
+    }
+}
+
 // ------------------------------------------------------- batched launches
 // Initialise the fresh instances of the table: clear their small arrays, mark
 // every agent and job free, re-pitch the caller's matrix where needed, and
@@ -1062,7 +1099,7 @@ size_t controller_smem_bytes(int32_t n) {
     return ctl_fixed_bytes(n, mode) + 2 * (size_t)controller_list_cap(n, mode) + 16;
 }
 
-cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s) {
+cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s, unsigned long long handle) {
     const int32_t mode = controller_smem_mode(w.n);
     const size_t smem = controller_smem_bytes(w.n);
     const int32_t cap = controller_list_cap(w.n, mode);
@@ -1078,21 +1115,24 @@ cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cuda
     const uint32_t span = short_wrap ? 4u : kRoundSpanMax;
     const uint32_t stamp_wrap = short_wrap ? 5u : 250u;
     const int32_t cmin = env_compact_min();
-    if (narrow) controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin);
-    else controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin);
+    if (narrow)
+        controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin, handle);
+    else
+        controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin,
+                                                                          handle);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prepare_edges(const Workspace& w, cudaStream_t s) {
     int grid = (2 * w.n + 255) / 256;
-    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid > dgs::device_sms() * 8) grid = dgs::device_sms() * 8;
     prepare_edges_kernel<<<grid, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s) {
     int grid = (w.n + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > dgs::device_sms() * 4) grid = dgs::device_sms() * 4;
     mark_rescan_kernel<<<grid, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
@@ -1100,7 +1140,7 @@ cudaError_t launch_mark_rescan(const Workspace& w, cudaStream_t s) {
 constexpr int32_t kRowStageMaxN = 54 * 1024;
 
 cudaError_t launch_row_tasks(const Workspace& w, cudaStream_t s) {
-    const int grid = 152 * 2;
+    const int grid = dgs::device_sms() * 2;
     if (w.n <= kRowStageMaxN) {
         const size_t smem = 4 * (size_t)w.ldt;
         if (smem > 48 * 1024) {
@@ -1126,9 +1166,9 @@ cudaError_t launch_row_owner_evaluation(const Workspace& w, int32_t conditional,
             if (e != cudaSuccess) return e;
         }
         const int per_sm = smem <= 110 * 1024 ? 2 : 1;
-        row_owner_evaluation_kernel<true><<<152 * per_sm, 512, smem, s>>>(w, conditional);
+        row_owner_evaluation_kernel<true><<<dgs::device_sms() * per_sm, 512, smem, s>>>(w, conditional);
     } else {
-        row_owner_evaluation_kernel<false><<<152 * 2, 512, 0, s>>>(w, conditional);
+        row_owner_evaluation_kernel<false><<<dgs::device_sms() * 2, 512, 0, s>>>(w, conditional);
     }
     return cudaGetLastError();
 }
@@ -1136,7 +1176,7 @@ cudaError_t launch_row_owner_evaluation(const Workspace& w, int32_t conditional,
 cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, int32_t mode, uint8_t* seen,
                                   cudaStream_t s) {
     int grid = (w.n + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > dgs::device_sms() * 4) grid = dgs::device_sms() * 4;
     start_from_tau_kernel<<<grid, 256, 0, s>>>(w, user_tau, mode, seen);
     return cudaGetLastError();
 }
@@ -1146,17 +1186,17 @@ cudaError_t launch_start_from_tau(const Workspace& w, const int32_t* user_tau, i
 // block); one: one entry per instance.
 
 cudaError_t launch_b_init(const BatchTable& rows, cudaStream_t s) {
-    init_batched_kernel<<<152 * 8, 256, 0, s>>>(rows, env_update_policy());
+    init_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows, env_update_policy());
     return cudaGetLastError();
 }
 
 cudaError_t launch_b_start(const BatchTable& rows, cudaStream_t s) {
-    start_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    start_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s) {
-    mark_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    mark_rescan_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
@@ -1168,7 +1208,7 @@ cudaError_t launch_b_row_tasks(const BatchQueues& q, int32_t max_n, cudaStream_t
         if (e != cudaSuccess) return e;
     }
     const int per_sm = (int)std::min<size_t>(4, (227 * 1024) / (smem + 1024));  // 512 threads, 2048 per SM
-    row_tasks_batched_kernel<<<152 * (per_sm < 1 ? 1 : per_sm), 512, smem, s>>>(q);
+    row_tasks_batched_kernel<<<dgs::device_sms() * (per_sm < 1 ? 1 : per_sm), 512, smem, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -1178,7 +1218,7 @@ cudaError_t launch_b_scan(const BatchQueues& q, int32_t phase, int32_t strip, cu
 }
 
 cudaError_t launch_b_prepare_edges(const BatchTable& rows, cudaStream_t s) {
-    prepare_edges_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    prepare_edges_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
@@ -1189,13 +1229,13 @@ cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s) {
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(controller_batched_kernel), 5, smem);
     if (e != cudaSuccess) return e;
     const bool short_wrap = env_short_wraps() != 0;
-    controller_batched_kernel<<<152, kCtlThreads, smem, s>>>(one, short_wrap ? 4u : kRoundSpanMax,
+    controller_batched_kernel<<<dgs::device_sms(), kCtlThreads, smem, s>>>(one, short_wrap ? 4u : kRoundSpanMax,
                                                             short_wrap ? 5u : 250u, env_compact_min());
     return cudaGetLastError();
 }
 
 cudaError_t launch_b_finish(const BatchTable& rows, cudaStream_t s) {
-    finish_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    finish_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
@@ -1204,9 +1244,17 @@ cudaError_t launch_b_advance(const BatchTable& one, int32_t from_stage, cudaStre
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish_outputs(const Workspace& w, int32_t* sigma_out, int64_t* objective, int32_t* status,
+                                  cudaStream_t s) {
+    int grid = (w.n + 255) / 256;
+    if (grid > dgs::device_sms() * 4) grid = dgs::device_sms() * 4;
+    finish_outputs_kernel<<<grid, 256, 0, s>>>(w, sigma_out, objective, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish(const Workspace& w, int32_t* sigma_out, cudaStream_t s) {
     int grid = (w.n + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > dgs::device_sms() * 4) grid = dgs::device_sms() * 4;
     finish_kernel<<<grid, 256, 0, s>>>(w, sigma_out);
     return cudaGetLastError();
 }

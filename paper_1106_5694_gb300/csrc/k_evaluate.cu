@@ -638,9 +638,18 @@ __global__ void __launch_bounds__(Geo<kRows>::kThreads, 1) full_evaluation_batch
     });
 }
 
-// agent slot i <- key_a[tau(i)], job slot j <- key_j[j]  (public evaluation API)
+// agent slot i <- key_a[tau(i)], job slot j <- key_j[j]  (public evaluation
+// API); after a range or start error every slot reads "no candidate"
 __global__ void keys_to_slots_kernel(Workspace w, int32_t* ag, int32_t* aj, int32_t* jg, int32_t* ja) {
+    const bool failed = w.st->status == kError;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < w.n; t += gridDim.x * blockDim.x) {
+        if (failed) {
+            ag[t] = 0;
+            aj[t] = -1;
+            jg[t] = 0;
+            ja[t] = -1;
+            continue;
+        }
         const unsigned long long ka = w.key_a[w.tau[t]];
         ag[t] = ka ? key_gain(ka) : 0;
         aj[t] = ka ? key_index(ka) : -1;
@@ -730,7 +739,7 @@ static cudaError_t launch_eval(const Workspace& w, int32_t conditional, int32_t 
     const int slot = kRows == 16 ? 13 : kRows == 8 ? (kTma ? 11 : 0) : (kTma ? 10 : 7);  // attribute cache slots
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_kernel<kRows, kTma>), slot, smem);
     if (e != cudaSuccess) return e;
-    full_evaluation_kernel<kRows, kTma><<<152, Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip, tm);
+    full_evaluation_kernel<kRows, kTma><<<dgs::device_sms(), Geo<kRows>::kThreads, smem, s>>>(w, conditional, strip, tm);
     return cudaGetLastError();
 }
 
@@ -758,7 +767,7 @@ cudaError_t launch_b_evaluation(const BatchQueues& q, int32_t strip, cudaStream_
     constexpr size_t smem = eval_smem_bytes<8>();
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(full_evaluation_batched_kernel<8>), 4, smem);
     if (e != cudaSuccess) return e;
-    full_evaluation_batched_kernel<8><<<152, Geo<8>::kThreads, smem, s>>>(q, strip);
+    full_evaluation_batched_kernel<8><<<dgs::device_sms(), Geo<8>::kThreads, smem, s>>>(q, strip);
     return cudaGetLastError();
 }
 

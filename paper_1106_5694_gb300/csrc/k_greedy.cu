@@ -13,6 +13,8 @@
 // transposed copy at (used later for column scans), checks |a| < 2^29 and
 // computes every agent's and job's best pair.  Later rounds rescan only the
 // agents (rows of a) and jobs (rows of at) whose best partner was taken.
+#include <cstdlib>
+
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -24,7 +26,8 @@ constexpr int kT = 64;  // tile edge
 // is the workspace's pitched copy still to be filled; this pass reads a_src
 // and writes the copy as it goes.  Null: w.a is read.
 __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t tiles_x, int32_t tiles_total,
-                                                  int32_t bid, int32_t nblk, const int32_t* a_src = nullptr) {
+                                                  int32_t bid, int32_t nblk, const int32_t* a_src = nullptr,
+                                                  bool cols = true) {
     __shared__ int32_t s[kT][kT + 1];
     __shared__ unsigned long long colpart[4][kT];
     const int32_t n = w.n;
@@ -71,7 +74,7 @@ __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t ti
         }
         __syncthreads();
         // column best: thread (group g = t/64, column c = t%64) scans 16 rows
-        {
+        if (cols) {
             const int c = t & 63, g = t >> 6;
             const int32_t j = J0 + c;
             unsigned long long best = 0;
@@ -97,7 +100,7 @@ __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t ti
             }
         }
         __syncthreads();
-        if (t < kT) {
+        if (cols && t < kT) {
             const int32_t j = J0 + t;
             unsigned long long best = umax64(umax64(colpart[0][t], colpart[1][t]), umax64(colpart[2][t], colpart[3][t]));
             if (j < n && best != 0) atomicMax(&w.g_col[j], best);
@@ -113,8 +116,9 @@ __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t ti
     }
 }
 
-__global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t tiles_x, int32_t tiles_total) {
-    greedy_pass1_body(w, tiles_x, tiles_total, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t tiles_x, int32_t tiles_total,
+                                                           int32_t cols) {
+    greedy_pass1_body(w, tiles_x, tiles_total, blockIdx.x, gridDim.x, nullptr, cols != 0);
 }
 
 // Match every mutually-best (agent, job) pair.
@@ -186,229 +190,243 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
     }
 }
 
-// All rounds in one cooperative launch, one grid barrier per round.  Every
-// CTA keeps its own copy of the free-agent and free-job sets as bitmaps in
-// shared memory and computes the round's matches redundantly from the keys
-// (all CTAs reach the same result), then the full list of owners to rescan;
-// CTA b rescans the entries of rank b, b + G, ... of that list, so the work
-// is balanced without further synchronisation.  Round r equals round r of
-// the launch-per-round path.
-constexpr int kPThreads = 1024;
-constexpr int kPGroups = 8;          // rescans run in groups of 128 threads
-constexpr int kPMaxBitWords = 2048;  // n <= 65536 (larger n: one launch per round)
-constexpr int kPMaxMine = 512;       // rescans per CTA per round held in shared memory
+// Deferred acceptance (Gale and Shapley 1962, agents proposing).  Every
+// agent ranks the jobs by (benefit desc, job asc) and every job ranks the
+// agents by (benefit desc, agent asc); both rankings are induced by the one
+// strict total order on pairs (benefit desc, agent asc, job asc), so the
+// stable matching is unique and equals the global greedy assignment: the
+// greedy matching is stable, and in any other perfect matching the first
+// pair, in that order, where the two differ is a greedy pair, which blocks
+// the other matching.  Deferred acceptance in any order of proposals reaches
+// it.
+//
+// Form: g_col[j] holds the key (biased benefit, ~agent) of the job's holder
+// and only grows (64-bit atomicMax).  A free agent proposes to its best job
+// among those whose holder it beats; a proposal that raises the key
+// displaces the holder.  The first proposal of every agent is its best job
+// overall, found by pass 1 (g_row); later ones rescan the agent's row of a
+// against g_hold_v (the holders' benefits, a lower bound of the high word of
+// g_col: a stale value only admits a job whose atomicMax then fails).  A
+// failed proposal rescans.  A group of threads takes the next agent from a
+// global counter and follows the chain of displacements: the agent it
+// displaced proposes next, by the same group, until a proposal lands on a
+// job nobody held.  Every free agent is thus in exactly one group's hands,
+// no group waits for another, and the launch ends when the counter is
+// exhausted and every chain has ended.
+constexpr int kDaThreads = 1024;
+constexpr uint64_t kDaTimeoutNs = 16000000000ull;  // bound on one group's work (internal error beyond)
 
-__device__ __forceinline__ bool bit_get(const uint32_t* bm, int32_t i) { return (bm[i >> 5] >> (i & 31)) & 1u; }
+template <int kGroup>
+__device__ __forceinline__ void group_bar(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kGroup) : "memory");
+}
 
-// Flags and keys written by other CTAs during the launch are read with
-// __ldcg (from L2): L1 is not coherent across SMs.
-__global__ void __launch_bounds__(kPThreads, 1) greedy_persistent_kernel(Workspace w) {
+// One proposal of agent i (and its rescans after failed ones), by the whole
+// group.  first: i has not proposed yet (its best job overall, from pass 1).
+// Returns the displaced agent, -1 when the job was free, -2 on an error.
+template <int kGroup>
+__device__ __forceinline__ int32_t da_propose(const Workspace& w, int32_t i, bool first, int grp, int gt,
+                                              unsigned long long* s_red, int32_t* s_out, int32_t& scans) {
+    constexpr int kWarps = kGroup / 32;
     DeviceState* st = w.st;
-    if (st->status != kRunning) return;
-    __shared__ uint32_t s_free_a[kPMaxBitWords], s_free_j[kPMaxBitWords], s_dirty[2 * kPMaxBitWords];
-    __shared__ int32_t s_mine[kPMaxMine];
-    __shared__ int32_t s_nmine, s_rem, s_warp[33];
-    __shared__ unsigned long long s_red[kPThreads / 32];
-    const int32_t n = w.n, G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-    const int32_t words = (n + 31) >> 5;
-    for (int32_t q = tid; q < words; q += kPThreads) {
-        const int32_t hi = min(32, n - 32 * q);
-        const uint32_t m = hi == 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
-        s_free_a[q] = m;
-        s_free_j[q] = m;
-    }
-    // the global copies start full (set by the host); every CTA reads them
-    // only after the first barrier
-    __syncthreads();
-    unsigned long long* pt = w.phase_ns;
-    const bool timing = pt != nullptr && tid == 0;
-    uint64_t tp = timing ? globaltimer_ns() : 0, scan_total = 0;
-#define DGS_PT(slot)                                   \
-    if (timing && b == 0) {                            \
-        const uint64_t now = globaltimer_ns();         \
-        atomicAdd(pt + (slot), now - tp);              \
-        tp = now;                                      \
-    } else if (timing) {                               \
-        tp = globaltimer_ns();                         \
-    }
-    int32_t rounds = 0;
-    for (int32_t round = 0; round <= n; ++round) {
-        // ---- every CTA copied last round's dirty bitmap before the round's
-        // final barrier: clear it (the new flags are set after the next one)
-        for (int32_t q = b * kPThreads + tid; q < (2 * n + 31) >> 5; q += G * kPThreads) w.g_dirty[q] = 0u;
-        // ---- match every mutually-best pair: each CTA its slice of agents,
-        // recorded in the global free bitmaps; then every CTA copies them
-        for (int32_t i0 = b * kPThreads + tid; i0 < n; i0 += 4 * G * kPThreads) {
-            int32_t jj[4];
+    const int32_t n = w.n;
+    const int glane = gt & 31, gwarp = gt >> 5;
+    const int32_t* row = w.a + (size_t)i * w.lda;
+    const uint32_t me_lo = ~(uint32_t)i;
+    for (int32_t attempt = 0;; ++attempt) {
+        unsigned long long best = 0;
+        if (attempt == 0 && first) {
+            if (gt == 0) best = w.g_row[i];
+        } else {
+            // the best job whose holder this agent beats: a job whose
+            // holder's benefit is below the agent's qualifies at once; at
+            // equal benefit the lower agent wins, which needs the holder's
+            // key (checked afterwards, for the best such job only)
+            ++scans;
+            constexpr int kB = 4;  // 16-byte loads of the row (and of the holders) in flight per thread
+            unsigned long long tie = 0;
+            for (int32_t c0 = gt * 4; c0 < n; c0 += 4 * kGroup * kB) {
+                int4 v[kB];
+                uint4 h[kB];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t i = i0 + k * G * kPThreads;
-                jj[k] = (i < n && bit_get(s_free_a, i)) ? key_index(__ldcg(w.g_row + i)) : -1;
-            }
-            int32_t back[4];
+                for (int b = 0; b < kB; ++b) {
+                    const int32_t c = c0 + b * 4 * kGroup;
+                    if (c < n) {
+                        v[b] = __ldcs(reinterpret_cast<const int4*>(row + c));
+                        h[b] = __ldcg(reinterpret_cast<const uint4*>(w.g_hold_v + c));
+                    }
+                }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) back[k] = (jj[k] >= 0 && jj[k] < n) ? key_index(__ldcg(w.g_col + jj[k])) : -2;
+                for (int b = 0; b < kB; ++b) {
+                    const int32_t c = c0 + b * 4 * kGroup;
+                    if (c >= n) continue;
+                    const int32_t vals[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
+                    const uint32_t hs[4] = {h[b].x, h[b].y, h[b].z, h[b].w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t i = i0 + k * G * kPThreads, j = jj[k];
-                if (back[k] != i) continue;
-                atomicAnd(w.g_free_a + (i >> 5), ~(1u << (i & 31)));
-                atomicAnd(w.g_free_j + (j >> 5), ~(1u << (j & 31)));
-                w.tau[i] = j;
-                w.sigma[j] = i;
-            }
-        }
-        if (!grid_barrier(st)) {
-            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
-            return;
-        }
-        for (int32_t q = tid; q < words; q += kPThreads) {
-            s_free_a[q] = __ldcg(w.g_free_a + q);
-            s_free_j[q] = __ldcg(w.g_free_j + q);
-        }
-        __syncthreads();
-        ++rounds;
-        // ---- remaining free agents, and the owners to rescan (rows: free
-        // agents whose best job was taken; columns: the converse)
-        if (tid == 0) { s_rem = 0; s_nmine = 0; }
-        __syncthreads();
-        {
-            int32_t rem = 0;
-            for (int32_t q = tid; q < words; q += kPThreads) {
-                const int32_t hi = min(32, n - 32 * q);  // bits of agents >= n are not counted
-                rem += __popc(s_free_a[q] & (hi == 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)));
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) rem += __shfl_xor_sync(0xffffffffu, rem, off);
-            if ((tid & 31) == 0 && rem) atomicAdd(&s_rem, rem);
-        }
-        __syncthreads();
-        if (b == 0 && tid == 0) st->greedy_remaining = s_rem;
-        DGS_PT(kPtGreedyMatch)
-        if (s_rem == 0 || *(volatile int32_t*)&st->status != kRunning) break;
-        // owners are numbered 0..2n-1 (rows, then columns): each CTA flags
-        // the dirty owners of its slice in the global bitmap (cleared by the
-        // previous round), then every CTA copies the bitmap and ranks it
-        const int32_t owner_words = (2 * n + 31) >> 5;
-        for (int32_t o0 = b * kPThreads + tid; o0 < 2 * n; o0 += 4 * G * kPThreads) {
-            int32_t best[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t o = o0 + k * G * kPThreads;
-                best[k] = -3;
-                if (o < 2 * n) {
-                    const bool is_row = o < n;
-                    const int32_t x = is_row ? o : o - n;
-                    if (bit_get(is_row ? s_free_a : s_free_j, x))
-                        best[k] = key_index(__ldcg(is_row ? w.g_row + x : w.g_col + x));
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t x = (uint32_t)(vals[e] + kBenefitLimit);
+                        const unsigned long long key =
+                            ((unsigned long long)x << 32) | (unsigned long long)(~(uint32_t)(c + e));
+                        if (c + e < n && x > hs[e]) best = umax64(best, key);
+                        else if (c + e < n && x == hs[e]) tie = umax64(tie, key);
+                    }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (best[k] == -3) continue;
-                const int32_t o = o0 + k * G * kPThreads;
-                const bool is_row = o < n;
-                const bool taken = best[k] < 0 || best[k] >= n || !bit_get(is_row ? s_free_j : s_free_a, best[k]);
-                if (taken) atomicOr(w.g_dirty + (o >> 5), 1u << (o & 31));
-            }
-        }
-        if (!grid_barrier(st)) {
-            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
-            return;
-        }
-        for (int32_t q = tid; q < owner_words; q += kPThreads) s_dirty[q] = __ldcg(w.g_dirty + q);
-        __syncthreads();
-        int32_t base_rank = 0;
-        for (int32_t w0 = 0; w0 < owner_words; w0 += kPThreads) {
-            const int32_t q = w0 + tid;
-            uint32_t dirty = q < owner_words ? s_dirty[q] : 0u;
-            const int32_t c = __popc(dirty);
-            int32_t total;
-            // exclusive block scan of c
-            int32_t incl = c;
-            const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int32_t o = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += o;
-            }
-            if (lane == 31) s_warp[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                const int32_t v = s_warp[lane];
-                int32_t wi = v;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int32_t o = __shfl_up_sync(0xffffffffu, wi, off);
-                    if (lane >= off) wi += o;
+            // the best tie that would win, if this agent beats its holder;
+            // else the next one below it (a rare second pass over this
+            // thread's part of the row)
+            while (tie > best) {
+                const int32_t j = key_index(tie);
+                const unsigned long long mine = (tie & 0xFFFFFFFF00000000ull) | me_lo;
+                if (mine > __ldcg(w.g_col + j)) {
+                    best = tie;
+                    break;
                 }
-                s_warp[lane] = wi - v;
-                if (lane == 31) s_warp[32] = wi;
-            }
-            __syncthreads();
-            const int32_t rank = base_rank + s_warp[warp] + incl - c;
-            total = s_warp[32];
-            // this word's owners take ranks rank .. rank + c - 1; the ones this
-            // CTA rescans are the set bits of index i = (b - rank) mod G,
-            // i + G, ... below c
-            for (int32_t i = ((b - rank) % G + G) % G; i < c; i += G) {
-                uint32_t d = dirty;
-                for (int32_t skip = 0; skip < i; ++skip) d &= d - 1u;  // drop the i lowest set bits
-                const int32_t slot = atomicAdd(&s_nmine, 1);
-                if (slot < kPMaxMine) s_mine[slot] = 32 * q + (__ffs(d) - 1);
-            }
-            base_rank += total;
-            __syncthreads();
-        }
-        if (s_nmine > kPMaxMine) {  // cannot happen for n <= 131072 with G >= 152
-            if (tid == 0) { st->error = kErrInternal; st->status = kError; }
-            break;
-        }
-        DGS_PT(kPtGreedyCheck)
-        if (tid == 0 && s_nmine) atomicAdd((unsigned long long*)&st->greedy_rescans, (unsigned long long)s_nmine);
-        // ---- rescan this CTA's owners: eight 128-thread groups
-        const int32_t cnt = s_nmine;
-        const int grp = tid >> 7, gt = tid & 127, glane = tid & 31, gwarp = (tid >> 5) & 3;
-        for (int32_t t = grp; t < cnt; t += kPGroups) {
-            const int32_t o2 = s_mine[t];
-            const bool is_row = o2 < n;
-            const int32_t o = is_row ? o2 : o2 - n;
-            const int32_t* row = is_row ? w.a + (size_t)o * w.lda : w.at + (size_t)o * w.ldt;
-            const uint32_t* pfree = is_row ? s_free_j : s_free_a;
-            unsigned long long best = 0;
-#pragma unroll 8
-            for (int32_t c = gt * 4; c < n; c += 4 * 128) {
-                const int4 v = *reinterpret_cast<const int4*>(row + c);
-                const uint32_t fr = (pfree[c >> 5] >> (c & 31)) & 0xFu;
-                const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+                const unsigned long long below = tie;
+                tie = 0;
+                for (int32_t c = gt * 4; c < n; c += 4 * kGroup) {
+                    const int4 v = *reinterpret_cast<const int4*>(row + c);
+                    const uint4 h = __ldcg(reinterpret_cast<const uint4*>(w.g_hold_v + c));
+                    const int32_t vals[4] = {v.x, v.y, v.z, v.w};
+                    const uint32_t hs[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (c + e < n && ((fr >> e) & 1u)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t x = (uint32_t)(vals[e] + kBenefitLimit);
+                        const unsigned long long key =
+                            ((unsigned long long)x << 32) | (unsigned long long)(~(uint32_t)(c + e));
+                        if (c + e < n && x > hs[e]) best = umax64(best, key);
+                        else if (c + e < n && x == hs[e] && key < below) tie = umax64(tie, key);
+                    }
+                }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
-            if (glane == 0) s_red[grp * 4 + gwarp] = best;
-            asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
-            if (gt == 0) {
-                const unsigned long long m = umax64(umax64(s_red[grp * 4], s_red[grp * 4 + 1]),
-                                                    umax64(s_red[grp * 4 + 2], s_red[grp * 4 + 3]));
-                (is_row ? w.g_row : w.g_col)[o] = m;
+            if (glane == 0) s_red[grp * kWarps + gwarp] = best;
+            group_bar<kGroup>(grp);
+            if (gt == 0)
+                for (int q = 0; q < kWarps; ++q) best = umax64(best, s_red[grp * kWarps + q]);
+        }
+        if (gt == 0) {
+            int32_t out = -1;
+            const int32_t j = key_index(best);
+            // some job always accepts a free agent, and a failed proposal
+            // rules its job out, so an agent needs at most n + 1 attempts
+            if (best == 0 || j < 0 || j >= n || attempt > n + 1) {
+                st->error = kErrInternal;
+                st->status = kError;
+                out = -2;
+            } else {
+                w.g_prop[i] += 1;
+                const uint32_t x = (uint32_t)(best >> 32);
+                const unsigned long long mine = ((unsigned long long)x << 32) | me_lo;
+                const unsigned long long old = atomicMax(w.g_col + j, mine);
+                if (old < mine) {
+                    atomicMax(w.g_hold_v + j, x);
+                    out = old == 0 ? -1 : key_index(old);
+                } else {
+                    atomicMax(w.g_hold_v + j, (uint32_t)(old >> 32));
+                    out = -3;  // the job was taken meanwhile: rescan
+                }
             }
-            asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
+            *s_out = out;
         }
-        __syncthreads();
-        if (timing) scan_total += globaltimer_ns() - tp;
-        DGS_PT(kPtGreedyScan)
-        if (!grid_barrier(st)) {
-            if (tid == 0) { st->error = kErrWaitTimeout; st->status = kError; }
-            return;
-        }
-        DGS_PT(kPtGreedyBar2)
+        group_bar<kGroup>(grp);
+        const int32_t out = *s_out;
+        group_bar<kGroup>(grp);
+        if (out != -3) return out;
     }
-    if (timing) atomicMax(pt + kPtGreedyScanMax, (unsigned long long)scan_total);
-#undef DGS_PT
-    if (b == 0 && tid == 0) st->greedy_rounds = rounds;
-    // the free flags of the round-based path are not used after this kernel
+}
+
+template <int kGroup>
+__global__ void __launch_bounds__(kDaThreads, 1) greedy_da_kernel(Workspace w) {
+    constexpr int kGroups = kDaThreads / kGroup;
+    DeviceState* st = w.st;
+    __shared__ unsigned long long s_red[kDaThreads / 32];
+    __shared__ int32_t s_out[kGroups];
+    __shared__ int32_t s_status;
+    if (threadIdx.x == 0) s_status = *(volatile int32_t*)&st->status;
+    __syncthreads();
+    if (s_status != kRunning) return;
+    const int32_t n = w.n;
+    const int tid = threadIdx.x, grp = tid / kGroup, gt = tid % kGroup;
+    int32_t scans = 0, longest = 0;
+    const uint64_t t_start = globaltimer_ns();
+    for (;;) {
+        if (gt == 0) s_out[grp] = atomicAdd(&st->da_next, 1);
+        group_bar<kGroup>(grp);
+        int32_t a = s_out[grp];
+        group_bar<kGroup>(grp);
+        if (a >= n) break;
+        bool first = true;
+        int32_t d, steps = 0;
+        // the chain of displacements that starts with agent a
+        while ((d = da_propose<kGroup>(w, a, first, grp, gt, s_red, &s_out[grp], scans)) >= 0) {
+            a = d;
+            first = false;
+            ++steps;
+            longest = max(longest, steps);
+            if (gt == 0 && globaltimer_ns() - t_start > kDaTimeoutNs) {
+                st->error = kErrWaitTimeout;
+                st->status = kError;
+                s_out[grp] = 1;
+            } else if (gt == 0) {
+                s_out[grp] = 0;
+            }
+            group_bar<kGroup>(grp);
+            const bool late = s_out[grp] != 0;
+            group_bar<kGroup>(grp);
+            if (late) {
+                d = -2;
+                break;
+            }
+        }
+        if (d == -2) break;
+    }
+    if (gt == 0 && scans) atomicAdd((unsigned long long*)&st->greedy_rescans, (unsigned long long)scans);
+    if (gt == 0 && w.phase_ns) {  // diagnostics (DGS_PHASE_TIMERS=1)
+        const uint64_t t = globaltimer_ns() - t_start;
+        atomicMax(w.phase_ns + kPtDaLastNs, (unsigned long long)t);
+        atomicAdd(w.phase_ns + kPtDaSumNs, (unsigned long long)t);
+        atomicMax(w.phase_ns + kPtDaChain, (unsigned long long)longest);
+        atomicMax(w.phase_ns + kPtDaGroupScans, (unsigned long long)scans);
+    }
+}
+
+// Loop condition of the locally-dominant rounds run as a device-side loop
+// (three kernels and this one per iteration): go on while agents are
+// unmatched; more than n + 8 rounds is an internal error.
+__global__ void greedy_loop_cond_kernel(Workspace w, unsigned long long cond) {
+    DeviceState* st = w.st;
+    const int32_t it = ++st->loop_iterations;
+    st->loop_launches += 4;
+    if (st->status == kRunning && st->greedy_remaining > 0 && it > w.n + 8) {
+        st->error = kErrInternal;
+        st->status = kError;
+    }
+    cudaGraphSetConditional(cond, (st->status == kRunning && st->greedy_remaining > 0) ? 1u : 0u);
+}
+
+// The assignment from the jobs' holders; greedy_rounds = the most proposals
+// any one agent made.
+__global__ void greedy_da_finish_kernel(Workspace w) {
+    DeviceState* st = w.st;
+    if (st->status != kRunning) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->greedy_remaining = 0;
+    int32_t most = 0;
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < w.n; j += gridDim.x * blockDim.x) {
+        const int32_t i = key_index(w.g_col[j]);
+        if (i < 0 || i >= w.n) {
+            st->error = kErrInternal;
+            st->status = kError;
+            continue;
+        }
+        w.sigma[j] = i;
+        w.tau[i] = j;
+        most = max(most, w.g_prop[i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, off));
+    if ((threadIdx.x & 31) == 0 && most) atomicMax(&st->greedy_rounds, most);
 }
 
 // |a| < 2^29 check alone (for entry points that do not run pass 1).
@@ -510,22 +528,29 @@ __global__ void __launch_bounds__(256) greedy_rescan_batched_kernel(BatchQueues 
 }  // namespace
 
 cudaError_t launch_range_check(const Workspace& w, cudaStream_t s) {
-    range_check_kernel<<<152 * 4, 256, 0, s>>>(w);
+    range_check_kernel<<<dgs::device_sms() * 4, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s) {
+cudaError_t launch_greedy_pass1_cols(const Workspace& w, int32_t cols, cudaStream_t s) {
     const int32_t tx = (w.n + kT - 1) / kT;
     const int32_t total = tx * tx;
-    const int32_t grid = total < 152 * 8 ? total : 152 * 8;
-    greedy_pass1_kernel<<<grid, 256, 0, s>>>(w, tx, total);
+    const int32_t grid = total < dgs::device_sms() * 8 ? total : dgs::device_sms() * 8;
+    greedy_pass1_kernel<<<grid, 256, 0, s>>>(w, tx, total, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s) { return launch_greedy_pass1_cols(w, 1, s); }
+
+cudaError_t launch_greedy_loop_cond(const Workspace& w, unsigned long long handle, cudaStream_t s) {
+    greedy_loop_cond_kernel<<<1, 1, 0, s>>>(w, handle);
     return cudaGetLastError();
 }
 
 cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
     const int32_t nb = (w.n + 255) / 256;
-    greedy_match_kernel<<<nb < 152 * 4 ? nb : 152 * 4, 256, 0, s>>>(w);
-    const int32_t g = w.n < 152 * 8 ? w.n : 152 * 8;  // one owner per CTA at a time
+    greedy_match_kernel<<<nb < dgs::device_sms() * 4 ? nb : dgs::device_sms() * 4, 256, 0, s>>>(w);
+    const int32_t g = w.n < dgs::device_sms() * 8 ? w.n : dgs::device_sms() * 8;  // one owner per CTA at a time
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.a, w.lda, w.g_row, w.free_a, w.free_j, 1);
     greedy_rescan_kernel<<<g, 256, 0, s>>>(w, w.at, w.ldt, w.g_col, w.free_j, w.free_a, 0);
     return cudaGetLastError();
@@ -534,7 +559,7 @@ cudaError_t launch_greedy_round(const Workspace& w, cudaStream_t s) {
 // Pass 1 of the instances queued by the kScanPass1 scan (blocks over the
 // 64x64 tiles of a).
 cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s) {
-    greedy_pass1_batched_kernel<<<152 * 8, 256, 0, s>>>(q);
+    greedy_pass1_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -542,29 +567,48 @@ cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s) {
 // entries over agents and jobs), list the owners to rescan, queue them
 // (scan), rescan each with one CTA.
 cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchQueues& q, cudaStream_t s) {
-    greedy_match_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
-    greedy_dirty_batched_kernel<<<152 * 8, 256, 0, s>>>(rows);
+    greedy_match_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
+    greedy_dirty_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     cudaError_t e = launch_b_scan(q, kScanGreedy, 0, s);
     if (e != cudaSuccess) return e;
-    greedy_rescan_batched_kernel<<<152 * 8, 256, 0, s>>>(q);
+    greedy_rescan_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(q);
     return cudaGetLastError();
 }
 
-cudaError_t launch_greedy_persistent(const Workspace& w, cudaStream_t s) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, greedy_persistent_kernel, kPThreads, 0);
-    if (e != cudaSuccess) return e;
-    int grid = sms * (per_sm < 1 ? per_sm : 1);
-    if (w.g_free_a == nullptr || w.g_free_j == nullptr || w.g_dirty == nullptr) return cudaErrorNotSupported;
-    if (grid < 1) return cudaErrorNotSupported;
-    if (w.n > 32 * kPMaxBitWords || (int64_t)2 * w.n > (int64_t)kPMaxMine * grid) return cudaErrorNotSupported;
+// Threads per proposal of the deferred acceptance (DGS_DA_GROUP = 128, 256
+// or 512; results do not depend on it).
+int32_t da_group_env() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_DA_GROUP");
+        const int32_t x = e ? std::atoi(e) : 256;
+        return (x == 128 || x == 512) ? x : 256;
+    }();
+    return v;
+}
+
+// DGS_GREEDY_ROUNDS=1: the locally-dominant rounds instead of deferred
+// acceptance (tests; the same assignment).
+int32_t greedy_rounds_env() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_GREEDY_ROUNDS");
+        return (e && std::atoi(e) == 1) ? 1 : 0;
+    }();
+    return v;
+}
+
+cudaError_t launch_greedy_da(const Workspace& w, cudaStream_t s) {
+    if (greedy_rounds_env() || w.g_hold_v == nullptr || w.g_prop == nullptr) return cudaErrorNotSupported;
+    const int32_t g = da_group_env();
+    const void* kernel = g == 128 ? reinterpret_cast<const void*>(greedy_da_kernel<128>)
+                       : g == 512 ? reinterpret_cast<const void*>(greedy_da_kernel<512>)
+                                  : reinterpret_cast<const void*>(greedy_da_kernel<256>);
     Workspace arg = w;
     void* args[] = {&arg};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(greedy_persistent_kernel), dim3(grid),
-                                       dim3(kPThreads), args, 0, s);
+    cudaError_t e = cudaLaunchKernel(kernel, dim3(dgs::device_sms()), dim3(kDaThreads), args, 0, s);
+    if (e != cudaSuccess) return e;
+    const int32_t nb = (w.n + 255) / 256;
+    greedy_da_finish_kernel<<<nb < dgs::device_sms() * 4 ? nb : dgs::device_sms() * 4, 256, 0, s>>>(w);
+    return cudaGetLastError();
 }
 
 }  // namespace dgs

@@ -14,8 +14,8 @@
 //     lowest partner agent sigma(k)).
 // The slot deltas live in shared memory (n <= kSeqSmemMaxN) or in the
 // workspace's slot arrays.  The outer repeat (a fresh evaluation of every
-// slot, then the loop again until a pass leaves f unchanged) is driven by
-// the host.
+// slot, then the loop again until a pass leaves f unchanged) runs as a
+// device-side loop of passes.
 #include "dgs_internal.cuh"
 
 namespace dgs {
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) sequential_kernel(Workspace w,
         __syncthreads();
     }
     // the loop ended (or this launch reached its iteration budget: need_update
-    // tells the host to launch again)
+    // makes the loop condition launch it again)
     if (tid == 0) st->need_update = s_stop ? 0 : 1;
     if (smem_deltas) {
         __syncthreads();
@@ -189,16 +189,60 @@ __global__ void slots_from_keys_kernel(Workspace w) {
         const unsigned long long kj = w.key_j[t];
         w.jb_gain[t] = kj ? key_gain(kj) : 0;
         w.jb_agent[t] = kj ? key_index(kj) : -1;
-        w.key_a[t] = 0ull;  // cleared for the next pass's evaluation
-        w.key_j[t] = 0ull;
     }
+}
+
+// Device-side passes of Algorithm 1 (conditional WHILE graph nodes): each
+// pass begins by recording f and re-arming the switching loop, the loop runs
+// while a launch stops at its iteration budget (need_update), and the passes
+// go on while a pass changed f (the outer repeat).  Bounds: 4 n + 16 passes,
+// 64 launches of the switching loop per pass (internal error beyond).
+__global__ void seq_pass_begin_kernel(Workspace w, unsigned long long inner) {
+    DeviceState* st = w.st;
+    st->f_pass = st->f;
+    st->seq_inner = 0;
+    st->loop_launches += 3;  // this kernel, the evaluation, the slots
+    if (st->status == kRunning && ++st->seq_passes > 4 * w.n + 16) {
+        st->error = kErrInternal;
+        st->status = kError;
+    }
+    cudaGraphSetConditional(inner, st->status == kRunning ? 1u : 0u);
+}
+
+__global__ void seq_inner_cond_kernel(Workspace w, unsigned long long inner) {
+    DeviceState* st = w.st;
+    st->loop_launches += 2;  // the switching loop and this kernel
+    if (st->status == kRunning && st->need_update && ++st->seq_inner > 64) {
+        st->error = kErrInternal;
+        st->status = kError;
+    }
+    cudaGraphSetConditional(inner, (st->status == kRunning && st->need_update) ? 1u : 0u);
+}
+
+__global__ void seq_pass_end_kernel(Workspace w, unsigned long long outer) {
+    DeviceState* st = w.st;
+    st->loop_launches += 1;
+    cudaGraphSetConditional(outer, (st->status == kRunning && st->f != st->f_pass) ? 1u : 0u);
 }
 
 }  // namespace
 
+cudaError_t launch_seq_pass_begin(const Workspace& w, unsigned long long inner, cudaStream_t s) {
+    seq_pass_begin_kernel<<<1, 1, 0, s>>>(w, inner);
+    return cudaGetLastError();
+}
+cudaError_t launch_seq_inner_cond(const Workspace& w, unsigned long long inner, cudaStream_t s) {
+    seq_inner_cond_kernel<<<1, 1, 0, s>>>(w, inner);
+    return cudaGetLastError();
+}
+cudaError_t launch_seq_pass_end(const Workspace& w, unsigned long long outer, cudaStream_t s) {
+    seq_pass_end_kernel<<<1, 1, 0, s>>>(w, outer);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_slots_from_keys(const Workspace& w, cudaStream_t s) {
     int grid = (w.n + 255) / 256;
-    if (grid > 152 * 4) grid = 152 * 4;
+    if (grid > dgs::device_sms() * 4) grid = dgs::device_sms() * 4;
     slots_from_keys_kernel<<<grid, 256, 0, s>>>(w);
     return cudaGetLastError();
 }

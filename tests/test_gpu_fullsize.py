@@ -1,6 +1,10 @@
-"""Full-size parity: the GPU solve of the workloads bench.py times equals the
-oracle's complete result stored in tests/golden/bench_golden.json (written by
-tests/golden/make_bench_golden.py, which calls only the oracle)."""
+"""Full-size parity: the GPU solve of every single-instance workload of the
+benchmark (peer-shaped and uniform [0, 1e6), n = 4096, 10000, 20000) equals
+the oracle's complete result stored in tests/golden/bench_golden.json
+(written by tests/golden/make_bench_golden.py, which calls only the oracle):
+the greedy start, the final assignment, its objective, the sweep count and
+the number of committed exchanges, and, where the record holds one, the
+per-sweep trace of a capped prefix of the switching loop."""
 import hashlib
 import json
 import os
@@ -25,17 +29,39 @@ def _workloads():
         return json.load(f)["workloads"]
 
 
+def _make_input(w):
+    if w["generator"] == "uniform":
+        return inputs.uniform(w["n"], w["lo"], w["hi"], w["seed"])
+    return getattr(inputs, w["generator"])(w["n"], w["seed"])
+
+
 @pytest.mark.parametrize("w", _workloads(), ids=lambda w: w["name"])
 def test_fullsize_solve_equals_stored_oracle_result(w):
     from paper_1106_5694_gb300 import build_ext
     build_ext.build()
-    a = getattr(inputs, w["generator"])(w["n"], w["seed"])
+    a = _make_input(w)
     if _sha(a) != w["a_sha256"]:
         pytest.fail("generated input differs from the one the oracle solved (platform-dependent generator?)")
     at = torch.from_numpy(a).cuda()
+    del a
     st, g = B.dgs_greedy_init(at)
     assert st == B.DGS_OK
     assert _sha(g.cpu().numpy().astype(np.int32)) == w["greedy_tau_sha256"]
+    p = w.get("prefix_result")
+    if p is not None:
+        cap = int(w["prefix"])
+        ta = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        tp = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        tf = torch.zeros(cap, dtype=torch.int64, device="cuda")
+        st, sig, f, stats = B.dgs_solve_ex(at, max_sweeps=cap, trace=(ta, tp, tf))
+        assert st == p["status"]
+        assert stats["sweeps"] == p["sweeps"] and f == p["objective"]
+        assert ta.cpu().tolist() == p["trace_accepted"]
+        assert tp.cpu().tolist() == p["trace_applied"]
+        assert tf.cpu().tolist() == p["trace_objective"]
+        assert _sha(sig.cpu().numpy().astype(np.int32)) == p["tau_sha256"]
+    if "objective" not in w:  # a record with the prefix only
+        return
     st, sig, f, stats = B.dgs_solve_ex(at)
     assert st == B.DGS_OK
     assert f == w["objective"]

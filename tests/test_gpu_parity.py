@@ -150,11 +150,17 @@ def test_errors():
     a = _make("uniform", 20, 0)
     bad = a.copy()
     bad[3, 4] = 1 << 29
-    st, _, _ = B.dgs_solve(_cuda(bad))
-    assert st == B.DGS_ERR_RANGE
+    # stream-ordered: the call is accepted, the outcome arrives with the stream
+    st, sig, _ = B.dgs_solve(_cuda(bad))
+    assert st == B.DGS_OK and bool((sig == -1).all())
+    assert B.dgs_solve_ex(_cuda(bad))[0] == B.DGS_ERR_RANGE
     neg = a.copy()
     neg[0, 0] = -(1 << 29)
-    assert B.dgs_solve(_cuda(neg))[0] == B.DGS_ERR_RANGE
+    assert B.dgs_solve_ex(_cuda(neg))[0] == B.DGS_ERR_RANGE
+    # the outcome also lands in a device word (options.status_out)
+    word = torch.full((1,), -5, dtype=torch.int32, device="cuda")
+    st, sig, _, stats = B.dgs_solve_ex(_cuda(neg), status_out=word)
+    assert st == stats["status"] == B.DGS_ERR_RANGE and int(word.item()) == B.DGS_ERR_RANGE
     dup = np.arange(20, dtype=np.int32)
     dup[5] = 6
     st, _, _, _ = B.dgs_solve_ex(_cuda(a), init=B.DGS_INIT_USER, init_sigma=_cuda(dup))

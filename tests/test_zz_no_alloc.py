@@ -74,3 +74,24 @@ def test_static_evaluation_rejects_unsupported_sizes():
     st, *got = B.dgs_evaluate_static(a2, tau2)
     assert st == B.DGS_OK
     assert all(torch.equal(g, r) for g, r in zip(got, B.dgs_evaluate(a2, tau2)[1:]))
+
+
+def test_static_evaluation_after_a_failed_call_shows_no_stale_results():
+    """A call rejected on the device (a job repeated in sigma_in) leaves every
+    output slot at "no candidate", as dgs_evaluate does, although the shared
+    array still holds the keys of the call before it; the next valid call is
+    unaffected."""
+    a, tau = _instance("peer", 512, 4)
+    st, *good = B.dgs_evaluate_static(a, tau)
+    assert st == B.DGS_OK
+    bad = tau.clone()
+    bad[1] = bad[0]
+    st_s, *got = B.dgs_evaluate_static(a, bad)
+    st_r, *ref = B.dgs_evaluate(a, bad)
+    assert st_s == st_r == B.DGS_ERR_INVALID
+    for g, r in zip(got, ref):
+        assert torch.equal(g, r)
+    assert all(bool((g == 0).all()) for g in got[0::2]) and all(bool((g == -1).all()) for g in got[1::2])
+    st, *again = B.dgs_evaluate_static(a, tau)
+    assert st == B.DGS_OK
+    assert all(torch.equal(g, r) for g, r in zip(again, good))
