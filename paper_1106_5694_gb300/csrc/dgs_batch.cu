@@ -11,7 +11,8 @@
 // of launches:
 //
 //   init (fresh slots) -> pass 1 -> advance(new)
-//   -> greedy rounds x kGreedyPerStep -> advance(greedy)
+//   -> greedy start (deferred acceptance of every new instance's agents in
+//      one launch) -> advance(greedy)
 //   -> start, first full evaluation -> advance(start)
 //   -> switching iterations x kSwitchPerStep -> finish -> advance(switch)
 //   -> copy of every slot's loop state to pinned host memory
@@ -38,7 +39,6 @@
 namespace dgs {
 namespace {
 
-constexpr int32_t kGreedyPerStep = 16;  // greedy rounds per step
 constexpr int32_t kSwitchPerStep = 8;   // switching iterations per step
 
 // Static work tables (the per-instance work of these launches is known from
@@ -256,7 +256,7 @@ class Engine {
         B_LAUNCH(launch_b_scan(q, kScanPass1, strip, s), 1, "scan");
         B_LAUNCH(launch_b_pass1(q, s), 1, "pass 1");
         B_LAUNCH(launch_b_advance(one, kStageNew, s), 1, "advance");
-        for (int32_t r = 0; r < kGreedyPerStep; ++r) B_LAUNCH(launch_b_greedy_round(rows, q, s), 4, "greedy round");
+        B_LAUNCH(launch_b_greedy(rows, q, s), 3, "greedy start");
         B_LAUNCH(launch_b_advance(one, kStageGreedy, s), 1, "advance");
         B_LAUNCH(launch_b_start(rows, s), 1, "start");
         B_LAUNCH(launch_b_scan(q, kScanStart, strip, s), 1, "scan");
@@ -335,11 +335,11 @@ class Engine {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Upper bound on the steps of one instance: every step runs kGreedyPerStep
-// greedy rounds (at most n in all) and kSwitchPerStep switching iterations
-// (at most 16 n + 4096 in all, the bound of the single solve).
+// Upper bound on the steps of one instance: the greedy start ends within its
+// first step, then every step runs kSwitchPerStep switching iterations (at
+// most 16 n + 4096 in all, the bound of the single solve).
 int64_t max_steps_for(int32_t n) {
-    return 4 + ceil_div(n + 1, kGreedyPerStep) + ceil_div(16ll * n + 4096, kSwitchPerStep);
+    return 5 + ceil_div(16ll * n + 4096, kSwitchPerStep);
 }
 
 int64_t now_ns() {

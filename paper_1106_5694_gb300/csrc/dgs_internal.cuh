@@ -218,7 +218,7 @@ __host__ __device__ __forceinline__ int32_t batch_blocks_eval(int32_t n, int32_t
 }
 
 // Phases whose work counts the scan kernel computes.
-enum : int32_t { kScanPass1 = 0, kScanGreedy = 1, kScanStart = 2, kScanSwitch = 3 };
+enum : int32_t { kScanPass1 = 0, kScanGreedyDA = 1, kScanStart = 2, kScanSwitch = 3 };
 
 // Phase timer slots.
 enum : int32_t {
@@ -403,7 +403,7 @@ struct BatchQueues {
 cudaError_t launch_b_scan(const BatchQueues& q, int32_t phase, int32_t strip, cudaStream_t s);
 cudaError_t launch_b_init(const BatchTable& rows, cudaStream_t s);
 cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s);
-cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchQueues& q, cudaStream_t s);
+cudaError_t launch_b_greedy(const BatchTable& rows, const BatchQueues& q, cudaStream_t s);
 cudaError_t launch_b_start(const BatchTable& rows, cudaStream_t s);
 cudaError_t launch_b_evaluation(const BatchQueues& q, int32_t strip, cudaStream_t s);
 cudaError_t launch_b_mark_rescan(const BatchTable& rows, cudaStream_t s);

@@ -955,8 +955,8 @@ __global__ void __launch_bounds__(512) row_tasks_batched_kernel(BatchQueues q) {
 // + 1 entries each), with the counters a single solve updates at the same
 // point.  One CTA of 1024 threads.
 //   kScanPass1:  q0 = pass-1 blocks of instances in kStageNew
-//   kScanGreedy: q0 = owners listed for rescan (greedy stage; the round is
-//                counted when the match matched pairs)
+//   kScanGreedyDA: q0 = agents of the instances in kStageGreedy (every q1
+//                entry is 0: q1[0] is the deferred acceptance's shared counter)
 //   kScanStart:  q0 = evaluation blocks of instances in kStageStart
 //   kScanSwitch: q0 = evaluation blocks of the updates that re-evaluate every
 //                row, q1 = rows of the updates that use row tasks
@@ -975,18 +975,8 @@ __global__ void __launch_bounds__(1024) scan_batched_kernel(BatchQueues q, int32
                 const bool running = st->status == kRunning;
                 if (phase == kScanPass1) {
                     if (stage == kStageNew) x0 = batch_blocks_pass1(n);
-                } else if (phase == kScanGreedy) {
-                    if (stage == kStageGreedy) {
-                        if (st->greedy_matched) {
-                            st->greedy_rounds += 1;
-                            st->greedy_matched = 0;
-                        }
-                        if (running && st->greedy_remaining > 0) {
-                            x0 = st->rescan_count;
-                            st->greedy_rescans += x0;
-                        }
-                        st->rescan_count = 0;
-                    }
+                } else if (phase == kScanGreedyDA) {
+                    if (stage == kStageGreedy && running && st->greedy_remaining > 0) x0 = n;
                 } else if (phase == kScanStart) {
                     if (stage == kStageStart && running) x0 = batch_blocks_eval(n, strip);
                 } else if (phase == kScanSwitch) {

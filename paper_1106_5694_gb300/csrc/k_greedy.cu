@@ -458,70 +458,80 @@ __global__ void range_check_kernel(Workspace w) {
 __global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchQueues q) {
     for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t bid, int32_t nblk) {
         const int32_t tx = (in.w.n + kT - 1) / kT;
-        greedy_pass1_body(in.w, tx, tx * tx, bid, nblk, in.a_src);
+        greedy_pass1_body(in.w, tx, tx * tx, bid, nblk, in.a_src, false);
     });
 }
 
-__global__ void __launch_bounds__(256) greedy_match_batched_kernel(BatchTable t) {
-    for_each_entry(t, kStageGreedy, [&](const Instance& in, int32_t bid, int32_t nblk) {
-        greedy_match_body(in.w, bid, nblk);
-    });
+// Deferred acceptance of every instance in kStageGreedy in one launch: the
+// agents of all those instances form one index space (prefix offsets q0 of
+// the kScanGreedyDA scan, which also zeroes q1[0], the shared counter); a
+// group takes the next agent of that space and follows its chain of
+// displacements inside its instance, exactly as greedy_da_kernel does for a
+// single solve.
+template <int kGroup>
+__global__ void __launch_bounds__(kDaThreads, 1) greedy_da_batched_kernel(BatchQueues q) {
+    constexpr int kGroups = kDaThreads / kGroup;
+    __shared__ unsigned long long s_red[kDaThreads / 32];
+    __shared__ int32_t s_out[kGroups];
+    const int32_t total = q.q0[q.cap];
+    if (total <= 0) return;
+    const int tid = threadIdx.x, grp = tid / kGroup, gt = tid % kGroup;
+    int32_t scans = 0, k_last = -1;
+    for (;;) {
+        if (gt == 0) s_out[grp] = atomicAdd(q.q1, 1);
+        group_bar<kGroup>(grp);
+        const int32_t g = s_out[grp];
+        group_bar<kGroup>(grp);
+        if (g >= total) break;
+        int32_t lo = 0, hi = q.cap;  // q0[lo] <= g < q0[hi]
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (q.q0[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const Instance& in = q.inst[lo];
+        if (k_last != lo && k_last >= 0 && gt == 0 && scans)  // rescans are counted per instance
+            atomicAdd((unsigned long long*)&q.inst[k_last].w.st->greedy_rescans, (unsigned long long)scans);
+        if (k_last != lo) scans = 0;
+        k_last = lo;
+        int32_t a = g - q.q0[lo];
+        bool first = true;
+        int32_t d;
+        while ((d = da_propose<kGroup>(in.w, a, first, grp, gt, s_red, &s_out[grp], scans)) >= 0) {
+            a = d;
+            first = false;
+        }
+    }
+    if (k_last >= 0 && gt == 0 && scans)
+        atomicAdd((unsigned long long*)&q.inst[k_last].w.st->greedy_rescans, (unsigned long long)scans);
 }
 
-// After a match: list the owners to rescan (owners 0..n-1 are agents, rows of
-// a; n..2n-1 are jobs, rows of at): free owners whose best partner was just
-// taken.  The list lives in ctl_slot (unused until the switching loop) and
-// its length in rescan_count (the scan kernel reads and clears it).
-__global__ void __launch_bounds__(256) greedy_dirty_batched_kernel(BatchTable t) {
+// The assignment of every instance in kStageGreedy from its jobs' holders
+// (greedy_da_finish_kernel per instance).
+__global__ void greedy_da_finish_batched_kernel(BatchTable t) {
     for_each_entry(t, kStageGreedy, [&](const Instance& in, int32_t bid, int32_t nblk) {
         const Workspace& w = in.w;
         DeviceState* st = w.st;
-        if (st->status != kRunning || st->greedy_remaining == 0) return;
-        const int32_t n = w.n;
-        for (int32_t o = bid * blockDim.x + threadIdx.x; o < 2 * n; o += nblk * blockDim.x) {
-            const bool is_row = o < n;
-            const int32_t x = is_row ? o : o - n;
-            if (!(is_row ? w.free_a[x] : w.free_j[x])) continue;
-            const int32_t b = key_index(is_row ? w.g_row[x] : w.g_col[x]);
-            if (b >= 0 && b < n && (is_row ? w.free_j[b] : w.free_a[b])) continue;
-            w.ctl_slot[atomicAdd(&st->rescan_count, 1)] = o;
-        }
-    });
-}
-
-// One listed owner per item: its best free partner over its whole row, with
-// the CTA (the same scan as greedy_rescan_kernel).
-__global__ void __launch_bounds__(256) greedy_rescan_batched_kernel(BatchQueues q) {
-    __shared__ unsigned long long red[8];
-    for_each_item(q.inst, q.q0, q.cap, [&](const Instance& in, int32_t t, int32_t) {
-        const Workspace& w = in.w;
-        const int32_t n = w.n;
-        const int32_t o2 = w.ctl_slot[t];
-        const bool is_row = o2 < n;
-        const int32_t o = is_row ? o2 : o2 - n;
-        const int32_t* row = is_row ? w.a + (size_t)o * w.lda : w.at + (size_t)o * w.ldt;
-        const uint8_t* partner_free = is_row ? w.free_j : w.free_a;
-        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        unsigned long long best = 0;
-#pragma unroll 4
-        for (int32_t c = tid * 4; c < n; c += 1024) {
-            const int4 v = *reinterpret_cast<const int4*>(row + c);
-            const uint32_t fr = *reinterpret_cast<const uint32_t*>(partner_free + c);
-            const int32_t vals[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (c + e < n && ((fr >> (8 * e)) & 0xffu)) best = umax64(best, pack_benefit(vals[e], (uint32_t)(c + e)));
+        // every queued agent of the instance was placed by the launch before
+        // (the instance's blocks must not test greedy_remaining, which block
+        // 0 clears here for the advance kernel)
+        if (st->status != kRunning) return;
+        if (bid == 0 && threadIdx.x == 0) st->greedy_remaining = 0;
+        int32_t most = 0;
+        for (int32_t j = bid * blockDim.x + threadIdx.x; j < w.n; j += nblk * blockDim.x) {
+            const int32_t i = key_index(w.g_col[j]);
+            if (i < 0 || i >= w.n) {
+                st->error = kErrInternal;
+                st->status = kError;
+                continue;
+            }
+            w.sigma[j] = i;
+            w.tau[i] = j;
+            most = max(most, w.g_prop[i]);
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
-        if (lane == 0) red[warp] = best;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long m = 0;
-            for (int k = 0; k < 8; ++k) m = umax64(m, red[k]);
-            (is_row ? w.g_row : w.g_col)[o] = m;
-        }
-        __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, off));
+        if ((threadIdx.x & 31) == 0 && most) atomicMax(&st->greedy_rounds, most);
     });
 }
 
@@ -563,15 +573,16 @@ cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One locally-dominant round of the instances in kStageGreedy: match (rows:
-// entries over agents and jobs), list the owners to rescan, queue them
-// (scan), rescan each with one CTA.
-cudaError_t launch_b_greedy_round(const BatchTable& rows, const BatchQueues& q, cudaStream_t s) {
-    greedy_match_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
-    greedy_dirty_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
-    cudaError_t e = launch_b_scan(q, kScanGreedy, 0, s);
+// The greedy start of every instance in kStageGreedy (deferred acceptance:
+// queue the agents, one launch, then the assignments; the advance kernel
+// moves the instances on once greedy_remaining is 0).
+cudaError_t launch_b_greedy(const BatchTable& rows, const BatchQueues& q, cudaStream_t s) {
+    cudaError_t e = launch_b_scan(q, kScanGreedyDA, 0, s);
     if (e != cudaSuccess) return e;
-    greedy_rescan_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(q);
+    greedy_da_batched_kernel<256><<<dgs::device_sms(), kDaThreads, 0, s>>>(q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    greedy_da_finish_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
