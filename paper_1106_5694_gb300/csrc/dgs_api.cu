@@ -199,6 +199,7 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
     w.y_list = ar.take<int32_t>(nb);
     w.rescan_list = ar.take<int32_t>(nb);
     w.sl_edge = ar.take<unsigned long long>(2 * nb);
+    w.sl_chunk = ar.take<int32_t>(2 * nb / 32);
     w.sl_rkey = ar.take<unsigned long long>(2 * nb);
     w.sl_ru = ar.take<int32_t>(2 * nb);
     w.sl_rv = ar.take<int32_t>(2 * nb);
@@ -207,8 +208,7 @@ size_t carve(Arena& ar, Workspace& w, const Plan& p, int32_t n, CtlGlobal* ctl, 
     w.g_col = ar.take<unsigned long long>(nb);
     w.free_a = ar.take<uint8_t>(nb);
     w.free_j = ar.take<uint8_t>(nb);
-    w.g_hold_v = ar.take<uint32_t>(nb);
-    w.g_prop = ar.take<int32_t>(nb);
+    w.g_list = ar.take<unsigned long long>(4 * nb);
     w.phase_ns = env_phase_timers() ? ar.take<unsigned long long>(kPtCount) : nullptr;
     w.st = ar.take<DeviceState>(1);
     *seen = ar.take<uint8_t>(4 * nb);

@@ -96,6 +96,7 @@ struct Workspace {
     // per slot (agent slots 0..n-1, job slots n..2n-1): its edge word (0 when
     // it has no candidate) and its re-evaluated candidate (key, exchange agents)
     unsigned long long* sl_edge;
+    int32_t* sl_chunk;  // edges among slots 32c .. 32c + 31 (written with sl_edge)
     unsigned long long* sl_rkey;
     int32_t* sl_ru;
     int32_t* sl_rv;
@@ -105,8 +106,7 @@ struct Workspace {
     unsigned long long* g_col;  // round form: best free agent per job (biased value, ~i);
                                 // deferred acceptance: the key (biased value, ~i) of the job's holder
     uint8_t* free_a; uint8_t* free_j;
-    uint32_t* g_hold_v;  // deferred acceptance: biased benefit of each job's holder (high word of g_col)
-    int32_t* g_prop;     // deferred acceptance: proposals made by each agent
+    unsigned long long* g_list;  // deferred acceptance: per agent, 4 slots: the 2nd-4th jobs of its last scan
     int32_t exact_keys;  // 1: never use the packed 32-bit keys (test knob)
     int32_t row_owner_eval;  // 1: full evaluations by row owners (A-transpose form)
     DeviceState* st;

@@ -212,24 +212,20 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             s_stamp = 0;
         }
         // Warp wp lists the slots of its own range [lo, hi) (ranges are
-        // multiples of 32 long and ascend with wp): it counts its edges,
-        // the 32 warp counts are scanned once, and it writes its edges at
-        // its offset, so positions follow slot order (the priority order).
+        // multiples of 32 long and ascend with wp): it sums the edge counts
+        // of its 32-slot chunks (written by the grid beside the edge words),
+        // the 32 warp counts are scanned once, and it writes the edges of
+        // its chunks that have any at its offset, so positions follow slot
+        // order (the priority order).
         constexpr int kWarps = kCtlThreads / 32;
         const int32_t lane = tid & 31, wp = tid >> 5;
         const int32_t per = (2 * n + 32 * kWarps - 1) / (32 * kWarps) * 32;
-        const int32_t lo = wp * per, hi = min(2 * n, lo + per);
+        const int32_t lo = min(2 * n, wp * per), hi = min(2 * n, lo + per);
+        const int32_t c_lo = lo >> 5, c_hi = lo < hi ? (hi + 31) >> 5 : c_lo;  // lo is a multiple of 32
         int32_t cnt = 0;
-        for (int32_t t0 = lo; t0 < hi; t0 += 4 * 32) {
-            unsigned long long ew[4];
+        for (int32_t c = c_lo + lane; c < c_hi; c += 32) cnt += w.sl_chunk[c];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t t = t0 + k * 32 + lane;
-                ew[k] = t < hi ? w.sl_edge[t] : 0ull;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cnt += __popc(__ballot_sync(0xffffffffu, ew[k] != 0ull));
-        }
+        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
         if (lane == 0) warp_sums[wp] = cnt;
         __syncthreads();
         if (wp == 0) {
@@ -246,26 +242,35 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         __syncthreads();
         int32_t pos0 = warp_sums[wp];
         const uint32_t below = (1u << lane) - 1u;
-        for (int32_t t0 = lo; t0 < hi; t0 += 4 * 32) {
-            unsigned long long ew[4];
+        for (int32_t cb = c_lo; cb < c_hi; cb += 32) {
+            uint32_t nz = __ballot_sync(0xffffffffu, cb + lane < c_hi && w.sl_chunk[cb + lane] > 0);
+            while (nz) {  // four chunks with edges at a time, their loads in flight together
+                int32_t ck[4];
+                unsigned long long ew[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t t = t0 + k * 32 + lane;
-                ew[k] = t < hi ? w.sl_edge[t] : 0ull;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t t = t0 + k * 32 + lane;
-                const bool has = ew[k] != 0ull;
-                const uint32_t m = __ballot_sync(0xffffffffu, has);
-                if (has) {
-                    const int32_t pos = pos0 + __popc(m & below);
-                    w.ctl_slot[pos] = t;
-                    if (slot_s) slot_s[pos] = (uint16_t)t;
-                    E[pos] = C::make(edge_u(ew[k]), edge_v(ew[k]));
-                    estate[pos] = kAlive | ((ew[k] & kApplies) ? kAppl : 0);
+                for (int k = 0; k < 4; ++k) {
+                    ck[k] = nz ? cb + __ffs(nz) - 1 : -1;
+                    nz &= nz - 1u;
                 }
-                pos0 += __popc(m);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t t = ck[k] * 32 + lane;
+                    ew[k] = (ck[k] >= 0 && t < hi) ? w.sl_edge[t] : 0ull;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t t = ck[k] * 32 + lane;
+                    const bool has = ew[k] != 0ull;
+                    const uint32_t m = __ballot_sync(0xffffffffu, has);
+                    if (has) {
+                        const int32_t pos = pos0 + __popc(m & below);
+                        w.ctl_slot[pos] = t;
+                        if (slot_s) slot_s[pos] = (uint16_t)t;
+                        E[pos] = C::make(edge_u(ew[k]), edge_v(ew[k]));
+                        estate[pos] = kAlive | ((ew[k] & kApplies) ? kAppl : 0);
+                    }
+                    pos0 += __popc(m);
+                }
             }
         }
         if (tid == 0) { s_L = warp_sums[32]; s_live = warp_sums[32]; }
@@ -607,6 +612,11 @@ __device__ __forceinline__ void prepare_edges_body(const Workspace& w, int32_t b
             e = edge_word(u, v) | (exchange_gain(w, u, v) > 0 ? kApplies : 0ull);
         }
         w.sl_edge[t] = e;
+        // the warp's 32 consecutive slots form one chunk: its edge count
+        // lets the controller skip chunks without edges
+        const uint32_t am = __activemask();
+        const uint32_t bm = __ballot_sync(am, e != 0ull);
+        if ((int)(threadIdx.x & 31) == __ffs(am) - 1) w.sl_chunk[t >> 5] = __popc(bm);
     }
 }
 

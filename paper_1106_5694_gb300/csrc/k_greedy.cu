@@ -201,59 +201,130 @@ __global__ void __launch_bounds__(256) greedy_rescan_kernel(Workspace w, const i
 // it.
 //
 // Form: g_col[j] holds the key (biased benefit, ~agent) of the job's holder
-// and only grows (64-bit atomicMax).  A free agent proposes to its best job
-// among those whose holder it beats; a proposal that raises the key
-// displaces the holder.  The first proposal of every agent is its best job
-// overall, found by pass 1 (g_row); later ones rescan the agent's row of a
-// against g_hold_v (the holders' benefits, a lower bound of the high word of
-// g_col: a stale value only admits a job whose atomicMax then fails).  A
-// failed proposal rescans.  A group of threads takes the next agent from a
-// global counter and follows the chain of displacements: the agent it
-// displaced proposes next, by the same group, until a proposal lands on a
-// job nobody held.  Every free agent is thus in exactly one group's hands,
-// no group waits for another, and the launch ends when the counter is
-// exhausted and every chain has ended.
+// and only grows (64-bit atomicMax).  Agent i beats the holder of job j iff
+// its own key (a[i][j] biased, ~i) is larger.  A free agent proposes to its
+// best job among those whose holder it beats; a proposal that raises the
+// key displaces the holder.  The first proposal of every agent is its best
+// job overall, found by pass 1 (g_row).  A later proposal takes the first
+// job of the agent's list that it still beats; the list (g_list, three
+// keys) holds the second to fourth jobs of the agent's last scan.  Holders'
+// keys only grow, so every job ranked above a list entry and left out of
+// the list was already lost at the scan and is lost still: the first list
+// entry the agent beats is its best job.  With no such entry the agent
+// rescans its row of a against the holders' keys (a stale key is lower and
+// only admits a job whose atomicMax then fails) and keeps the top four.  A
+// failed proposal tries the list, else rescans.  A group of threads takes
+// the next agent from a global counter and follows the chain of
+// displacements: the agent it displaced proposes next, by the same group,
+// until a proposal lands on a job nobody held.  Every free agent is thus in
+// exactly one group's hands, no group waits for another, and the launch
+// ends when the counter is exhausted and every chain has ended.
 constexpr int kDaThreads = 1024;
 constexpr uint64_t kDaTimeoutNs = 16000000000ull;  // bound on one group's work (internal error beyond)
+constexpr int kDaList = 3;                         // list entries per agent (g_list has 4 slots)
 
 template <int kGroup>
 __device__ __forceinline__ void group_bar(int grp) {
-    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kGroup) : "memory");
+    if (kGroup == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kGroup) : "memory");
 }
 
-// One proposal of agent i (and its rescans after failed ones), by the whole
+// 64-bit atomic max with acquire-release order at GPU scope: the proposal
+// publishes the proposer's list, and the displacer then reads the displaced
+// agent's list.
+__device__ __forceinline__ unsigned long long atomic_max_acq_rel(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.max.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+// Insert key k into the descending t[0..3] (keys are distinct: the low word
+// is the job).
+__device__ __forceinline__ void top4_insert(unsigned long long (&t)[4], unsigned long long k) {
+    if (k <= t[3]) return;
+    t[3] = k;
+    if (t[3] > t[2]) { const unsigned long long x = t[2]; t[2] = t[3]; t[3] = x; }
+    if (t[2] > t[1]) { const unsigned long long x = t[1]; t[1] = t[2]; t[2] = x; }
+    if (t[1] > t[0]) { const unsigned long long x = t[0]; t[0] = t[1]; t[1] = x; }
+}
+
+// The four largest keys of the warp, in every lane's out[0..3].
+__device__ __forceinline__ void warp_top4(unsigned long long (&t)[4], unsigned long long (&out)[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        unsigned long long m = t[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = umax64(m, __shfl_xor_sync(0xffffffffu, m, off));
+        out[r] = m;
+        if (m != 0 && t[0] == m) {  // the owner drops it
+            t[0] = t[1];
+            t[1] = t[2];
+            t[2] = t[3];
+            t[3] = 0;
+        }
+    }
+}
+
+// One proposal of agent i (and its retries after failed ones), by the whole
 // group.  first: i has not proposed yet (its best job overall, from pass 1).
-// Returns the displaced agent, -1 when the job was free, -2 on an error.
+// s_red: 4 keys per warp of the block; s_top: 4 keys per group.  Returns the
+// displaced agent, -1 when the job was free, -2 on an error.
 template <int kGroup>
 __device__ __forceinline__ int32_t da_propose(const Workspace& w, int32_t i, bool first, int grp, int gt,
-                                              unsigned long long* s_red, int32_t* s_out, int32_t& scans) {
+                                              unsigned long long* s_red, unsigned long long* s_top,
+                                              int32_t* s_out, int32_t& scans) {
     constexpr int kWarps = kGroup / 32;
+    constexpr unsigned long long kHi = 0xFFFFFFFF00000000ull;
     DeviceState* st = w.st;
     const int32_t n = w.n;
     const int glane = gt & 31, gwarp = gt >> 5;
     const int32_t* row = w.a + (size_t)i * w.lda;
     const uint32_t me_lo = ~(uint32_t)i;
+    unsigned long long* list = w.g_list + 4 * (size_t)i;
     for (int32_t attempt = 0;; ++attempt) {
         unsigned long long best = 0;
-        if (attempt == 0 && first) {
-            if (gt == 0) best = w.g_row[i];
-        } else {
-            // the best job whose holder this agent beats: a job whose
-            // holder's benefit is below the agent's qualifies at once; at
-            // equal benefit the lower agent wins, which needs the holder's
-            // key (checked afterwards, for the best such job only)
+        if (gt == 0) {
+            int32_t need_scan = 0;
+            if (attempt == 0 && first) {
+                best = w.g_row[i];
+            } else {  // the first list entry whose holder this agent beats
+                unsigned long long l[kDaList], h[kDaList];
+#pragma unroll
+                for (int m = 0; m < kDaList; ++m) l[m] = list[m];
+#pragma unroll
+                for (int m = 0; m < kDaList; ++m) h[m] = l[m] ? __ldcg(w.g_col + key_index(l[m])) : ~0ull;
+                int32_t used = kDaList;
+#pragma unroll
+                for (int m = kDaList - 1; m >= 0; --m)
+                    if (l[m] != 0 && ((l[m] & kHi) | me_lo) > h[m]) {
+                        best = l[m];
+                        used = m + 1;
+                    }
+                if (best == 0) need_scan = 1;
+#pragma unroll
+                for (int m = 0; m < kDaList; ++m)
+                    if (m < used) list[m] = 0ull;  // consumed
+            }
+            *s_out = need_scan;
+        }
+        group_bar<kGroup>(grp);
+        const bool need_scan = *s_out != 0;
+        group_bar<kGroup>(grp);
+        if (need_scan) {
+            // the four best jobs whose holders this agent beats
             ++scans;
-            constexpr int kB = 4;  // 16-byte loads of the row (and of the holders) in flight per thread
-            unsigned long long tie = 0;
+            unsigned long long t[4] = {0ull, 0ull, 0ull, 0ull};
+            constexpr int kB = 2;  // 16-byte loads of the row (and 32 bytes of holder keys each) in flight
             for (int32_t c0 = gt * 4; c0 < n; c0 += 4 * kGroup * kB) {
                 int4 v[kB];
-                uint4 h[kB];
+                ulonglong2 h[kB][2];
 #pragma unroll
                 for (int b = 0; b < kB; ++b) {
                     const int32_t c = c0 + b * 4 * kGroup;
                     if (c < n) {
                         v[b] = __ldcs(reinterpret_cast<const int4*>(row + c));
-                        h[b] = __ldcg(reinterpret_cast<const uint4*>(w.g_hold_v + c));
+                        h[b][0] = __ldcg(reinterpret_cast<const ulonglong2*>(w.g_col + c));
+                        h[b][1] = __ldcg(reinterpret_cast<const ulonglong2*>(w.g_col + c + 2));
                     }
                 }
 #pragma unroll
@@ -261,71 +332,64 @@ __device__ __forceinline__ int32_t da_propose(const Workspace& w, int32_t i, boo
                     const int32_t c = c0 + b * 4 * kGroup;
                     if (c >= n) continue;
                     const int32_t vals[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
-                    const uint32_t hs[4] = {h[b].x, h[b].y, h[b].z, h[b].w};
+                    const unsigned long long hs[4] = {h[b][0].x, h[b][0].y, h[b][1].x, h[b][1].y};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const uint32_t x = (uint32_t)(vals[e] + kBenefitLimit);
-                        const unsigned long long key =
-                            ((unsigned long long)x << 32) | (unsigned long long)(~(uint32_t)(c + e));
-                        if (c + e < n && x > hs[e]) best = umax64(best, key);
-                        else if (c + e < n && x == hs[e]) tie = umax64(tie, key);
+                        const unsigned long long x = (uint32_t)(vals[e] + kBenefitLimit);
+                        if (c + e < n && ((x << 32) | me_lo) > hs[e])
+                            top4_insert(t, (x << 32) | (unsigned long long)(~(uint32_t)(c + e)));
                     }
                 }
             }
-            // the best tie that would win, if this agent beats its holder;
-            // else the next one below it (a rare second pass over this
-            // thread's part of the row)
-            while (tie > best) {
-                const int32_t j = key_index(tie);
-                const unsigned long long mine = (tie & 0xFFFFFFFF00000000ull) | me_lo;
-                if (mine > __ldcg(w.g_col + j)) {
-                    best = tie;
-                    break;
-                }
-                const unsigned long long below = tie;
-                tie = 0;
-                for (int32_t c = gt * 4; c < n; c += 4 * kGroup) {
-                    const int4 v = *reinterpret_cast<const int4*>(row + c);
-                    const uint4 h = __ldcg(reinterpret_cast<const uint4*>(w.g_hold_v + c));
-                    const int32_t vals[4] = {v.x, v.y, v.z, v.w};
-                    const uint32_t hs[4] = {h.x, h.y, h.z, h.w};
+            unsigned long long wt[4];
+            warp_top4(t, wt);
+            if (kWarps == 1) {
+                if (gt == 0) {
+                    best = wt[0];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t x = (uint32_t)(vals[e] + kBenefitLimit);
-                        const unsigned long long key =
-                            ((unsigned long long)x << 32) | (unsigned long long)(~(uint32_t)(c + e));
-                        if (c + e < n && x > hs[e]) best = umax64(best, key);
-                        else if (c + e < n && x == hs[e] && key < below) tie = umax64(tie, key);
-                    }
+                    for (int m = 0; m < kDaList; ++m) list[m] = wt[1 + m];
                 }
+            } else {
+            if (glane == 0) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) s_red[(grp * kWarps + gwarp) * 4 + r] = wt[r];
             }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, off));
-            if (glane == 0) s_red[grp * kWarps + gwarp] = best;
             group_bar<kGroup>(grp);
-            if (gt == 0)
-                for (int q = 0; q < kWarps; ++q) best = umax64(best, s_red[grp * kWarps + q]);
+            if (gwarp == 0) {  // the group's first warp merges its warps' candidates
+                unsigned long long c4[4] = {0ull, 0ull, 0ull, 0ull};
+                for (int q = glane; q < kWarps * 4; q += 32) top4_insert(c4, s_red[grp * kWarps * 4 + q]);
+                unsigned long long gt4[4];
+                warp_top4(c4, gt4);
+                if (glane == 0) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) s_top[grp * 4 + r] = gt4[r];
+                }
+            }
+            group_bar<kGroup>(grp);
+            if (gt == 0) {
+                best = s_top[grp * 4];
+#pragma unroll
+                for (int m = 0; m < kDaList; ++m) list[m] = s_top[grp * 4 + 1 + m];
+            }
+            }
         }
         if (gt == 0) {
             int32_t out = -1;
             const int32_t j = key_index(best);
-            // some job always accepts a free agent, and a failed proposal
-            // rules its job out, so an agent needs at most n + 1 attempts
-            if (best == 0 || j < 0 || j >= n || attempt > n + 1) {
+            // some job always accepts a free agent, and every failed proposal
+            // or rejected list entry rules a job out, so an agent needs at
+            // most 2 n + 2 attempts
+            if (best == 0 || j < 0 || j >= n || attempt > 2 * n + 2) {
                 st->error = kErrInternal;
                 st->status = kError;
                 out = -2;
             } else {
-                w.g_prop[i] += 1;
-                const uint32_t x = (uint32_t)(best >> 32);
-                const unsigned long long mine = ((unsigned long long)x << 32) | me_lo;
-                const unsigned long long old = atomicMax(w.g_col + j, mine);
+                const unsigned long long mine = (best & kHi) | me_lo;
+                const unsigned long long old = atomic_max_acq_rel(w.g_col + j, mine);
                 if (old < mine) {
-                    atomicMax(w.g_hold_v + j, x);
                     out = old == 0 ? -1 : key_index(old);
                 } else {
-                    atomicMax(w.g_hold_v + j, (uint32_t)(old >> 32));
-                    out = -3;  // the job was taken meanwhile: rescan
+                    out = -3;  // the job was taken meanwhile: the list, else a rescan
                 }
             }
             *s_out = out;
@@ -341,7 +405,8 @@ template <int kGroup>
 __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_kernel(Workspace w) {
     constexpr int kGroups = kDaThreads / kGroup;
     DeviceState* st = w.st;
-    __shared__ unsigned long long s_red[kDaThreads / 32];
+    __shared__ unsigned long long s_red[kDaThreads / 32 * 4];
+    __shared__ unsigned long long s_top[kGroups * 4];
     __shared__ int32_t s_out[kGroups];
     __shared__ int32_t s_status;
     if (threadIdx.x == 0) s_status = *(volatile int32_t*)&st->status;
@@ -350,6 +415,7 @@ __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_kernel(Workspace w) {
     const int32_t n = w.n;
     const int tid = threadIdx.x, grp = tid / kGroup, gt = tid % kGroup;
     int32_t scans = 0, longest = 0;
+    bool worked = false;
     const uint64_t t_start = globaltimer_ns();
     for (;;) {
         if (gt == 0) s_out[grp] = atomicAdd(&st->da_next, 1);
@@ -359,8 +425,9 @@ __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_kernel(Workspace w) {
         if (a >= n) break;
         bool first = true;
         int32_t d, steps = 0;
+        worked = true;
         // the chain of displacements that starts with agent a
-        while ((d = da_propose<kGroup>(w, a, first, grp, gt, s_red, &s_out[grp], scans)) >= 0) {
+        while ((d = da_propose<kGroup>(w, a, first, grp, gt, s_red, s_top, &s_out[grp], scans)) >= 0) {
             a = d;
             first = false;
             ++steps;
@@ -383,6 +450,7 @@ __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_kernel(Workspace w) {
         if (d == -2) break;
     }
     if (gt == 0 && scans) atomicAdd((unsigned long long*)&st->greedy_rescans, (unsigned long long)scans);
+    if (gt == 0 && worked) atomicMax(&st->greedy_rounds, longest + 1);  // proposals along the longest chain
     if (gt == 0 && w.phase_ns) {  // diagnostics (DGS_PHASE_TIMERS=1)
         const uint64_t t = globaltimer_ns() - t_start;
         atomicMax(w.phase_ns + kPtDaLastNs, (unsigned long long)t);
@@ -406,13 +474,11 @@ __global__ void greedy_loop_cond_kernel(Workspace w, unsigned long long cond) {
     cudaGraphSetConditional(cond, (st->status == kRunning && st->greedy_remaining > 0) ? 1u : 0u);
 }
 
-// The assignment from the jobs' holders; greedy_rounds = the most proposals
-// any one agent made.
+// The assignment from the jobs' holders.
 __global__ void greedy_da_finish_kernel(Workspace w) {
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->greedy_remaining = 0;
-    int32_t most = 0;
     for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < w.n; j += gridDim.x * blockDim.x) {
         const int32_t i = key_index(w.g_col[j]);
         if (i < 0 || i >= w.n) {
@@ -422,11 +488,7 @@ __global__ void greedy_da_finish_kernel(Workspace w) {
         }
         w.sigma[j] = i;
         w.tau[i] = j;
-        most = max(most, w.g_prop[i]);
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, off));
-    if ((threadIdx.x & 31) == 0 && most) atomicMax(&st->greedy_rounds, most);
 }
 
 // |a| < 2^29 check alone (for entry points that do not run pass 1).
@@ -471,7 +533,8 @@ __global__ void __launch_bounds__(256) greedy_pass1_batched_kernel(BatchQueues q
 template <int kGroup>
 __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_batched_kernel(BatchQueues q) {
     constexpr int kGroups = kDaThreads / kGroup;
-    __shared__ unsigned long long s_red[kDaThreads / 32];
+    __shared__ unsigned long long s_red[kDaThreads / 32 * 4];
+    __shared__ unsigned long long s_top[kGroups * 4];
     __shared__ int32_t s_out[kGroups];
     const int32_t total = q.q0[q.cap];
     if (total <= 0) return;
@@ -496,11 +559,13 @@ __global__ void __launch_bounds__(kDaThreads, 1) greedy_da_batched_kernel(BatchQ
         k_last = lo;
         int32_t a = g - q.q0[lo];
         bool first = true;
-        int32_t d;
-        while ((d = da_propose<kGroup>(in.w, a, first, grp, gt, s_red, &s_out[grp], scans)) >= 0) {
+        int32_t d, steps = 1;
+        while ((d = da_propose<kGroup>(in.w, a, first, grp, gt, s_red, s_top, &s_out[grp], scans)) >= 0) {
             a = d;
             first = false;
+            ++steps;
         }
+        if (gt == 0 && d == -1) atomicMax(&in.w.st->greedy_rounds, steps);
     }
     if (k_last >= 0 && gt == 0 && scans)
         atomicAdd((unsigned long long*)&q.inst[k_last].w.st->greedy_rescans, (unsigned long long)scans);
@@ -517,7 +582,6 @@ __global__ void greedy_da_finish_batched_kernel(BatchTable t) {
         // 0 clears here for the advance kernel)
         if (st->status != kRunning) return;
         if (bid == 0 && threadIdx.x == 0) st->greedy_remaining = 0;
-        int32_t most = 0;
         for (int32_t j = bid * blockDim.x + threadIdx.x; j < w.n; j += nblk * blockDim.x) {
             const int32_t i = key_index(w.g_col[j]);
             if (i < 0 || i >= w.n) {
@@ -527,11 +591,7 @@ __global__ void greedy_da_finish_batched_kernel(BatchTable t) {
             }
             w.sigma[j] = i;
             w.tau[i] = j;
-            most = max(most, w.g_prop[i]);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, off));
-        if ((threadIdx.x & 31) == 0 && most) atomicMax(&st->greedy_rounds, most);
     });
 }
 
@@ -573,29 +633,44 @@ cudaError_t launch_b_pass1(const BatchQueues& q, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Threads per proposal of the deferred acceptance (DGS_DA_GROUP = 32, 128,
+// 256 or 512; results do not depend on it).  Groups of more than one warp
+// synchronise on named barriers 1..15, one per group of the block.
+int32_t da_group_env() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_DA_GROUP");
+        const int32_t x = e ? std::atoi(e) : 256;
+        return (x == 32 || x == 128 || x == 512) ? x : 256;
+    }();
+    return v;
+}
+
+template <template <int> class K>
+const void* da_kernel_for(int32_t g) {
+    return g == 32 ? reinterpret_cast<const void*>(K<32>::fn)
+         : g == 128 ? reinterpret_cast<const void*>(K<128>::fn)
+         : g == 512 ? reinterpret_cast<const void*>(K<512>::fn)
+                    : reinterpret_cast<const void*>(K<256>::fn);
+}
+template <int G> struct SingleDa { static constexpr auto fn = greedy_da_kernel<G>; };
+template <int G> struct BatchedDa { static constexpr auto fn = greedy_da_batched_kernel<G>; };
+
 // The greedy start of every instance in kStageGreedy (deferred acceptance:
 // queue the agents, one launch, then the assignments; the advance kernel
 // moves the instances on once greedy_remaining is 0).
 cudaError_t launch_b_greedy(const BatchTable& rows, const BatchQueues& q, cudaStream_t s) {
     cudaError_t e = launch_b_scan(q, kScanGreedyDA, 0, s);
     if (e != cudaSuccess) return e;
-    greedy_da_batched_kernel<256><<<dgs::device_sms(), kDaThreads, 0, s>>>(q);
-    e = cudaGetLastError();
+    BatchQueues arg = q;
+    void* args[] = {&arg};
+    e = cudaLaunchKernel(da_kernel_for<BatchedDa>(da_group_env()), dim3(dgs::device_sms()), dim3(kDaThreads), args,
+                         0, s);
     if (e != cudaSuccess) return e;
     greedy_da_finish_batched_kernel<<<dgs::device_sms() * 8, 256, 0, s>>>(rows);
     return cudaGetLastError();
 }
 
-// Threads per proposal of the deferred acceptance (DGS_DA_GROUP = 128, 256
-// or 512; results do not depend on it).
-int32_t da_group_env() {
-    static const int32_t v = [] {
-        const char* e = std::getenv("DGS_DA_GROUP");
-        const int32_t x = e ? std::atoi(e) : 256;
-        return (x == 128 || x == 512) ? x : 256;
-    }();
-    return v;
-}
+
 
 // DGS_GREEDY_ROUNDS=1: the locally-dominant rounds instead of deferred
 // acceptance (tests; the same assignment).
@@ -608,11 +683,8 @@ int32_t greedy_rounds_env() {
 }
 
 cudaError_t launch_greedy_da(const Workspace& w, cudaStream_t s) {
-    if (greedy_rounds_env() || w.g_hold_v == nullptr || w.g_prop == nullptr) return cudaErrorNotSupported;
-    const int32_t g = da_group_env();
-    const void* kernel = g == 128 ? reinterpret_cast<const void*>(greedy_da_kernel<128>)
-                       : g == 512 ? reinterpret_cast<const void*>(greedy_da_kernel<512>)
-                                  : reinterpret_cast<const void*>(greedy_da_kernel<256>);
+    if (greedy_rounds_env() || w.g_list == nullptr) return cudaErrorNotSupported;
+    const void* kernel = da_kernel_for<SingleDa>(da_group_env());
     Workspace arg = w;
     void* args[] = {&arg};
     cudaError_t e = cudaLaunchKernel(kernel, dim3(dgs::device_sms()), dim3(kDaThreads), args, 0, s);
