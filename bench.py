@@ -708,17 +708,18 @@ def run_batched(dev, count=1024, lo=64, hi=4096):
     }
 
 
-def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
-    """Poisson stream of peer-shaped requests, n log-uniform in [256, 16384],
+def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1.2), seeds=(13, 14), distinct=64):
+    """Poisson streams of peer-shaped requests, n log-uniform in [256, 16384],
     inputs in pinned host memory (as a server receives them), 40 GB
-    admission budget.  The plain comparison is a FIFO single-server queue
-    over the same arrivals whose service time is a dgs_solve_host call per
-    request on the same buffers (measured), latency = completion - arrival.
-    (From pageable memory the copies of both arms slowed down as the process
-    went on -- plain capacity fell from 380 to 190 solves/s over three
-    repetitions in one process -- which made the comparison depend on what
-    ran before it.)"""
+    admission budget, `count` requests per run cycling over `distinct`
+    seeded request buffers.  Per arrival rate (a fraction of the plain
+    solver's measured capacity) and arrival seed, two live runs over the same
+    arrivals: the server (dgs_submit / dgs_server_wait) and the plain
+    solver, one worker thread taking requests first come first served and
+    solving each alone through dgs_solve_host.  Latency = completion -
+    arrival."""
     import threading
+    from collections import deque
 
     import numpy as np
     import torch
@@ -726,71 +727,103 @@ def run_serving(dev, count=64, lo=256, hi=16384, budget=40 << 30):
     from paper_1106_5694_gb300 import binding as B
     from paper_1106_5694_gb300 import inputs
 
-    ns = inputs.batched_sizes(count, lo, hi, seed=11)
+    ns = inputs.batched_sizes(distinct, lo, hi, seed=11)
     pool = _pool(hi, 2, 900)
-    reqs = [torch.from_numpy(np.ascontiguousarray(pool[k % 2][:n, :n])).pin_memory().numpy()
+    bufs = [torch.from_numpy(np.ascontiguousarray(pool[k % 2][:n, :n])).pin_memory().numpy()
             for k, n in enumerate(ns)]
     del pool
-    # plain: each request alone through the host entry point
-    B.dgs_solve_host(reqs[0], device=dev)
-    service, plain_f = [], []
-    for a in reqs:
+    req_n = [int(ns[k % distinct]) for k in range(count)]
+    B.dgs_solve_host(bufs[0], device=dev)
+    svc, ref_f = [], []
+    for a in bufs:  # service time of each distinct request alone
         t0 = time.perf_counter()
         st, _, f, _ = B.dgs_solve_host(a, device=dev)
-        service.append(time.perf_counter() - t0)
-        plain_f.append(f)
-    capacity = count / sum(service)
-    rate = 0.7 * capacity
-    arrivals = inputs.poisson_arrivals(count, rate, seed=13)
-    done, lat_plain = 0.0, []
-    for t_a, s_i in zip(arrivals, service):
-        done = max(done, t_a) + s_i
-        lat_plain.append(done - t_a)
-    plain_span = done - arrivals[0]
-    # served
+        svc.append(time.perf_counter() - t0)
+        ref_f.append(f)
+    capacity = count / sum(svc[k % distinct] for k in range(count))
     torch.cuda.set_device(dev)
-    srv = B.Server(budget_bytes=budget)
-    w = srv.dgs_submit(reqs[0][:256, :256].copy())[1]  # warm-up (graph capture)
-    srv.dgs_server_wait(w)
-    tickets = [None] * count
-    t_start = time.perf_counter()
-
-    def submitter():
-        for k, (t_a, a) in enumerate(zip(arrivals, reqs)):
-            delay = t_start + t_a - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets[k] = srv.dgs_submit(a)[1]
-
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    lat, ok, first_submit, last_done = [], True, None, 0
-    for k, t in enumerate(tickets):
-        st, _, f, _, tm = srv.dgs_server_wait(t, timeout_us=600_000_000)
-        ok = ok and st == B.DGS_OK and f == plain_f[k]
-        lat.append((tm["done_ns"] - tm["submit_ns"]) / 1e9)
-        first_submit = tm["submit_ns"] if first_submit is None else min(first_submit, tm["submit_ns"])
-        last_done = max(last_done, tm["done_ns"])
-    info = srv.dgs_server_get_info()[1]
-    srv.dgs_server_destroy()
-    span = (last_done - first_submit) / 1e9
 
     def pct(x, q):
         return round(float(np.percentile(np.array(x) * 1e3, q)), 2)
 
+    def plain_run(arrivals):
+        lat = [0.0] * count
+        q, cv, done_all = deque(), threading.Condition(), [False]
+        t_start = time.perf_counter() + 0.05
+
+        def worker():
+            served = 0
+            while served < count:
+                with cv:
+                    while not q:
+                        cv.wait()
+                    k = q.popleft()
+                st, _, f, _ = B.dgs_solve_host(bufs[k % distinct], device=dev)
+                lat[k] = time.perf_counter() - (t_start + arrivals[k])
+                served += 1
+            done_all[0] = True
+
+        th = threading.Thread(target=worker)
+        th.start()
+        for k in range(count):
+            delay = t_start + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            with cv:
+                q.append(k)
+                cv.notify()
+        th.join()
+        span = max(t_start + arrivals[k] + lat[k] for k in range(count)) - (t_start + arrivals[0])
+        return {"solves_per_s": round(count / span, 2), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)}
+
+    def served_run(arrivals):
+        srv = B.Server(budget_bytes=budget)
+        w = srv.dgs_submit(bufs[0][:256, :256].copy())[1]  # warm-up (graph capture)
+        srv.dgs_server_wait(w)
+        tickets = [None] * count
+        t_start = time.perf_counter() + 0.05
+        for k in range(count):
+            delay = t_start + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.dgs_submit(bufs[k % distinct])[1]
+        lat, ok, first_submit, last_done, rows = [], True, None, 0, []
+        for k, t in enumerate(tickets):
+            st, _, f, _, tm = srv.dgs_server_wait(t, timeout_us=600_000_000)
+            ok = ok and st == B.DGS_OK and f == ref_f[k % distinct]
+            lat.append((tm["done_ns"] - tm["submit_ns"]) / 1e9)
+            rows.append((lat[-1], (tm["admit_ns"] - tm["submit_ns"]) / 1e6, (tm["done_ns"] - tm["admit_ns"]) / 1e6,
+                         req_n[k]))
+            first_submit = tm["submit_ns"] if first_submit is None else min(first_submit, tm["submit_ns"])
+            last_done = max(last_done, tm["done_ns"])
+        info = srv.dgs_server_get_info()[1]
+        srv.dgs_server_destroy()
+        span = (last_done - first_submit) / 1e9
+        rows.sort()
+        p99 = rows[min(len(rows) - 1, int(0.99 * len(rows)))]
+        return {"solves_per_s": round(count / span, 2), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "upload_ms_per_request": round(info["upload_ms"] / count, 3),
+                "step_ms_total": round(info["step_ms"], 1), "steps": info["steps"],
+                "p99_request": {"n": p99[3], "ms_to_admission": round(p99[1], 2),
+                                "ms_admission_to_result": round(p99[2], 2)},
+                "parity": "every objective equal to the plain solve of the same request" if ok else "MISMATCH"}
+
+    runs = []
+    for frac in rates:
+        for seed in seeds:
+            arrivals = inputs.poisson_arrivals(count, frac * capacity, seed=seed)
+            arrivals = arrivals - arrivals[0]
+            served = served_run(arrivals)
+            plain = plain_run(arrivals)
+            runs.append({"rate_fraction_of_plain_capacity": frac, "rate_per_s": round(frac * capacity, 2),
+                         "arrival_seed": seed, "served": served, "plain": plain})
     return {
-        "workload": f"{count} peer-shaped requests, n log-uniform in [{lo},{hi}] (seeded), Poisson arrivals at "
-                    f"{rate:.1f}/s (70% of the plain solver's measured capacity), pinned host-memory inputs, "
-                    f"{budget >> 30} GB admission budget",
-        "rate_per_s": round(rate, 2), "solves_per_s": round(count / span, 2),
-        "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
-        "plain": {"solves_per_s": round(count / plain_span, 2), "p50_ms": pct(lat_plain, 50),
-                  "p99_ms": pct(lat_plain, 99), "capacity_solves_per_s": round(capacity, 2),
-                  "how": "FIFO queue over the same arrivals, service = measured dgs_solve_host per request"},
-        "steps": info["steps"], "gpu_launches": info["kernel_launches"],
-        "server_upload_ms": round(info["upload_ms"], 1), "server_step_ms": round(info["step_ms"], 1),
-        "parity": "every objective equal to the plain solve of the same request" if ok else "MISMATCH",
+        "workload": f"{count} peer-shaped requests per run cycling over {distinct} seeded request buffers, n "
+                    f"log-uniform in [{lo},{hi}], Poisson arrivals, pinned host-memory inputs, {budget >> 30} GB "
+                    "admission budget; plain = one worker thread solving each request alone (dgs_solve_host), "
+                    "first come first served, live over the same arrivals",
+        "plain_capacity_solves_per_s": round(capacity, 2),
+        "runs": runs,
     }
 
 

@@ -751,7 +751,12 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
         S.launches += 1;
         if (o.profile) DGS_TRY(ev.end(stream));
-        DGS_TRY(enqueue_loop(stream, switching_body, &lc));
+        if (use_small_loop(S.w)) {
+            DGS_CUDA(launch_small_loop(S.w, S.ctl, stream), "switching loop");
+            S.launches += 1;
+        } else {
+            DGS_TRY(enqueue_loop(stream, switching_body, &lc));
+        }
     }
     DGS_CUDA(launch_finish_outputs(S.w, sigma_out, obj_on_device ? static_cast<int64_t*>(obj_dev) : nullptr,
                                    status_on_device ? static_cast<int32_t*>(status_dev) : nullptr, stream),

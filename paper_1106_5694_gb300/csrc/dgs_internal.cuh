@@ -358,6 +358,10 @@ cudaError_t launch_keys_to_slots(const Workspace& w, int32_t* ag, int32_t* aj, i
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& g, cudaStream_t s,
                                    unsigned long long handle = 0);
 int32_t controller_list_cap(int32_t n, int32_t mode);
+// The switching loop in one CTA for small n (see small_loop_kernel), and
+// whether a solve of this workspace takes it.
+bool use_small_loop(const Workspace& w);
+cudaError_t launch_small_loop(const Workspace& w, const CtlGlobal& g, cudaStream_t s);
 int32_t controller_smem_mode(int32_t n);
 size_t controller_smem_bytes(int32_t n);
 size_t full_evaluation_smem_bytes();

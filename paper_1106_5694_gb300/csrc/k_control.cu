@@ -29,6 +29,7 @@
 // update kernels re-evaluate the affected rows on the whole GPU, then the
 // controller is launched again and refreshes every slot not in C.
 #include <algorithm>
+#include <cstdlib>
 
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
@@ -767,6 +768,91 @@ __global__ void __launch_bounds__(512) row_tasks_kernel(Workspace w) {
     row_tasks_body<kStage>(w, blockIdx.x, gridDim.x);
 }
 
+// Row j of G re-evaluated in full by one warp (the row task of the
+// single-CTA switching loop): the same gains, tie-breaks and scatter into
+// the other rows' keys as row_task_compute, with lane-strided columns (each
+// lane sees its columns in ascending order, so its first maximum is its
+// lowest column, and the packed keys combine across lanes).
+__device__ __forceinline__ void row_task_warp(const Workspace& w, int32_t j) {
+    const int lane = threadIdx.x & 31;
+    const int32_t n = w.n;
+    const int32_t sjj = w.sigma[j];
+    const int32_t dj = w.diag[j];
+    const bool scatter = w.in_y[j];
+    const int32_t* arow = w.a + (size_t)sjj * w.lda;
+    const int32_t* atrow = w.at + (size_t)j * w.ldt;
+    int32_t bg = 0, bc = -1, bs = 0x7fffffff;
+    for (int32_t k = lane; k < n; k += 32) {
+        const int32_t sk = w.sigma[k];
+        const int32_t g = arow[k] + atrow[sk] - dj - w.diag[k];
+        const bool gt = g > bg, eq = g == bg;
+        bs = gt ? sk : (eq ? min(bs, sk) : bs);
+        bc = gt ? k : bc;
+        bg = max(bg, g);
+        if (scatter && g > 0 && k != j) {
+            if (g >= key_gain(w.key_a[k])) {
+                atomicMax(&w.key_a[k], pack_gain(g, (uint32_t)j));
+                atomicMax(&w.key_j[k], pack_gain(g, (uint32_t)sjj));
+            }
+        }
+    }
+    unsigned long long ka = bg > 0 ? pack_gain(bg, (uint32_t)bc) : 0ull;
+    unsigned long long kj = bg > 0 ? pack_gain(bg, (uint32_t)bs) : 0ull;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ka = umax64(ka, __shfl_xor_sync(0xffffffffu, ka, off));
+        kj = umax64(kj, __shfl_xor_sync(0xffffffffu, kj, off));
+    }
+    if (lane == 0 && ka) {
+        atomicMax(&w.key_a[j], ka);
+        atomicMax(&w.key_j[j], kj);
+    }
+}
+
+// The whole switching loop of Algorithm 3 in one CTA, for small n (the
+// per-launch cost of the five kernels of an iteration would dominate): per
+// iteration the rows marked by the last committing sweep are re-evaluated
+// (row tasks, one warp per row; identical keys to a full evaluation, see the
+// update kernels), the slots refreshed, then the controller's sweeps; until
+// the loop state stops running.  Bounded like the graph loop.
+template <typename EdgeT>
+__global__ void __launch_bounds__(kCtlThreads, 1) small_loop_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
+                                                                   uint32_t span, uint32_t stamp_wrap,
+                                                                   int32_t list_cap, int32_t compact_min) {
+    __shared__ int32_t s_go, s_count;
+    DeviceState* st = w.st;
+    const int32_t n = w.n;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (;;) {
+        mark_rescan_body(w, 0, 1);
+        __syncthreads();
+        if (tid == 0) {
+            const bool rows = st->status == kRunning && st->need_update;
+            s_count = rows ? st->rescan_count : 0;
+            if (rows) {
+                st->row_updates += 1;
+                st->rows_recomputed += s_count;
+            }
+        }
+        __syncthreads();
+        for (int32_t t = warp; t < s_count; t += kCtlThreads / 32) row_task_warp(w, w.rescan_list[t]);
+        __syncthreads();
+        prepare_edges_body(w, 0, 1);
+        __syncthreads();
+        controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min);
+        if (tid == 0) {
+            const int32_t it = ++st->loop_iterations;
+            if (st->status == kRunning && it > 16 * n + 4096) {
+                st->error = kErrInternal;
+                st->status = kError;
+            }
+            s_go = st->status == kRunning;
+        }
+        __syncthreads();
+        if (!s_go) break;
+    }
+}
+
 // The row-owner form of the full difference evaluation (Algorithm 2 for every
 // slot, the A-transpose variant): CTA b owns rows j = b, b + nblk, ... of G and
 // recomputes each from row sigma(j) of a and row j of the maintained at, with
@@ -1097,6 +1183,38 @@ size_t controller_smem_bytes(int32_t n) {
     const int32_t mode = controller_smem_mode(n);
     if (mode == 0) return 0;
     return ctl_fixed_bytes(n, mode) + 2 * (size_t)controller_list_cap(n, mode) + 16;
+}
+
+// DGS_SMALL_LOOP_N: the largest n whose switching loop runs in one CTA
+// (small_loop_kernel); 0 turns it off.  Only with the default update policy
+// (the test knob that forces an update path keeps the grid kernels).
+int32_t small_loop_max_n() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_SMALL_LOOP_N");
+        return e ? std::atoi(e) : 768;  // measured: faster up to n = 512, slower from n = 1024
+    }();
+    return v;
+}
+
+bool use_small_loop(const Workspace& w) {
+    return w.n <= small_loop_max_n() && controller_smem_mode(w.n) == 2 && env_update_policy() == 0 &&
+           w.row_owner_eval == 0;
+}
+
+cudaError_t launch_small_loop(const Workspace& w, const CtlGlobal& gs, cudaStream_t s) {
+    const int32_t mode = controller_smem_mode(w.n);
+    const size_t smem = controller_smem_bytes(w.n);
+    const int32_t cap = controller_list_cap(w.n, mode);
+    CtlScratch c{gs.res, gs.claimed, gs.estate, gs.edges, gs.acc};
+    const void* fn = reinterpret_cast<const void*>(small_loop_kernel<uint32_t>);
+    if (smem > 48 * 1024) {
+        cudaError_t e = ensure_smem_limit(fn, 14, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const bool short_wrap = env_short_wraps() != 0;
+    small_loop_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, short_wrap ? 4u : kRoundSpanMax,
+                                                              short_wrap ? 5u : 250u, cap, env_compact_min());
+    return cudaGetLastError();
 }
 
 cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cudaStream_t s, unsigned long long handle) {
