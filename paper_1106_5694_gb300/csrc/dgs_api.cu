@@ -812,6 +812,13 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
 
 }  // namespace
 
+namespace dgs {
+dgs_status solve_for_server(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
+                            const dgs_options* opt, dgs_stats* stats, cudaStream_t stream, dgs_status* final_status) {
+    return solve_impl(benefit, n, sigma_out, objective_out, opt, stats, stream, final_status);
+}
+}  // namespace dgs
+
 extern "C" {
 
 void dgs_default_options(dgs_options* o) {

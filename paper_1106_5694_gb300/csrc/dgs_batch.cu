@@ -26,6 +26,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -342,6 +343,19 @@ int64_t max_steps_for(int32_t n) {
     return 5 + ceil_div(16ll * n + 4096, kSwitchPerStep);
 }
 
+// Served requests of at least this size are solved alone (the solo
+// thread of the server) instead of in the batched engine; DGS_SERVER_SOLO_N
+// overrides it (0: every request is batched).
+int32_t solo_min_n() {
+    static const int32_t v = [] {
+        const char* e = std::getenv("DGS_SERVER_SOLO_N");
+        const int32_t x = e ? std::atoi(e) : 4096;
+        return x > 0 ? x : (1 << 30);
+    }();
+    return v;
+}
+bool solo_request(int32_t n) { return n >= solo_min_n(); }
+
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
         .count();
@@ -515,14 +529,20 @@ struct dgs_server {
     Engine eng;
     std::vector<Resident> slots;  // worker only
     static constexpr int kUploaders = 2;  // uploads of different requests overlap
-    std::thread worker, uploader[kUploaders];
+    static constexpr int kSolo = 3;       // large requests solved at once, each on its own stream
+    std::thread worker, uploader[kUploaders], solo[kSolo];
     cudaStream_t up_stream[kUploaders] = {};
+    cudaStream_t solo_stream[kSolo] = {};
     // everything below is guarded by mu
     std::mutex mu;
     std::condition_variable cv_work, cv_up, cv_done;
     std::deque<Request> queue;       // waiting for admission
     std::deque<Request> to_upload;   // admitted, matrix not yet on the device
     std::deque<Uploaded> ready;      // on the device, waiting for a slot
+    std::deque<Uploaded> solo_ready; // large requests on the device, waiting for the solo thread
+    std::condition_variable cv_solo;
+    int32_t solo_count = 0;          // large requests admitted, not finished
+    bool solo_stop = false;
     std::unordered_map<uint64_t, Result> results;
     std::unordered_map<uint64_t, int32_t> pending;  // ticket -> 0 queued / 1 admitted
     size_t used = 0;                 // budget taken by admitted requests
@@ -537,6 +557,19 @@ struct dgs_server {
     size_t h_sigma_cap = 0;
 
     explicit dgs_server(int32_t cap) : eng(cap, DGS_BATCH_MAX_N), slots(cap) {}
+
+    // Layout of a large request's memory: the n x n matrix, the result,
+    // the start.
+    static size_t solo_bytes(int32_t n) {
+        return ((size_t)n * n * 4 + 255) / 256 * 256 + 2 * (((size_t)n * 4 + 255) / 256 * 256);
+    }
+    static int32_t* solo_out(char* mem, int32_t n) {
+        return reinterpret_cast<int32_t*>(mem + ((size_t)n * n * 4 + 255) / 256 * 256);
+    }
+    static int32_t* solo_start(char* mem, int32_t n) {
+        return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(solo_out(mem, n)) +
+                                          ((size_t)n * 4 + 255) / 256 * 256);
+    }
 
     // A request's start (n int32) after its workspace and result.
     static int32_t* start_of(char* mem, int32_t n) {
@@ -575,8 +608,9 @@ struct dgs_server {
                 to_upload.pop_front();
             }
             const int64_t t0 = now_ns();
+            const bool solo_req = solo_request(r.n);
             char* mem = nullptr;
-            cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&mem), r.bytes, up);
+            cudaError_t e = pool_malloc_async(reinterpret_cast<void**>(&mem), solo_req ? solo_bytes(r.n) : r.bytes, up);
             if (e == cudaErrorMemoryAllocation) {  // the device has less free memory than the budget
                 cudaGetLastError();
                 Result res{};
@@ -584,13 +618,30 @@ struct dgs_server {
                 res.times.submit_ns = r.submit_ns;
                 res.times.admit_ns = res.times.done_ns = now_ns();
                 std::lock_guard<std::mutex> lk(mu);
-                --reserved;
+                if (solo_req) --solo_count;
+                else --reserved;
                 record_result(r.ticket, std::move(res), r.bytes);
                 cv_done.notify_all();
                 cv_work.notify_one();
                 continue;
             }
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && solo_req) {
+                // the matrix as it is (n x n), then the result and the start;
+                // the single solve re-pitches it itself when n % 4 != 0
+                const cudaMemcpyKind kind =
+                    (r.flags & DGS_SUBMIT_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+                e = cudaMemcpyAsync(mem, r.a, (size_t)r.n * r.n * 4, kind, up);
+                int32_t* start = solo_start(mem, r.n);
+                std::vector<int32_t> perm;
+                if (e == cudaSuccess && r.init == DGS_INIT_USER)
+                    e = cudaMemcpyAsync(start, r.init_tau, (size_t)r.n * 4, kind, up);
+                if (e == cudaSuccess && r.init == DGS_INIT_RANDOM) {
+                    perm.resize(r.n);
+                    random_start(r.n, r.seed, perm.data());
+                    e = cudaMemcpyAsync(start, perm.data(), (size_t)r.n * 4, cudaMemcpyHostToDevice, up);
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+            } else if (e == cudaSuccess) {
                 // the matrix, pitched (round_up(n, 4)) at the start of its workspace
                 Instance probe{};
                 carve_instance(mem, r.n, true, &probe);
@@ -638,7 +689,79 @@ struct dgs_server {
                 cv_work.notify_one();
                 return;
             }
-            ready.push_back(Uploaded{r, mem, t0});
+            if (solo_req) {
+                solo_ready.push_back(Uploaded{r, mem, t0});
+                cv_solo.notify_one();
+            } else {
+                ready.push_back(Uploaded{r, mem, t0});
+                cv_work.notify_one();
+            }
+        }
+    }
+
+    // Large requests (n >= solo_min_n()) are solved by kSolo threads, each as
+    // a single stream-ordered solve on its thread's stream, beside the
+    // batched steps of the small ones: a large instance needs many steps of
+    // the batched engine (each also steps every other resident instance),
+    // while alone it runs the single solve's kernels at full width.
+    void run_solo(int u) {
+        cudaSetDevice(device);
+        cudaStream_t ss = solo_stream[u];
+        int32_t* h_solo = nullptr;  // pinned staging for this thread's results
+        size_t h_solo_cap = 0;
+        struct Release {
+            int32_t*& p;
+            ~Release() {
+                if (p) cudaFreeHost(p);
+            }
+        } release{h_solo};
+        for (;;) {
+            Uploaded u;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_solo.wait(lk, [&] { return solo_stop || !solo_ready.empty(); });
+                if (solo_ready.empty()) return;
+                u = solo_ready.front();
+                solo_ready.pop_front();
+            }
+            const int32_t n = u.r.n;
+            int32_t* out = solo_out(u.mem, n);
+            dgs_options o;
+            dgs_default_options(&o);
+            const bool given = u.r.init == DGS_INIT_USER || u.r.init == DGS_INIT_RANDOM;
+            o.init = given ? DGS_INIT_USER : u.r.init;
+            o.init_sigma = given ? solo_start(u.mem, n) : nullptr;
+            o.max_sweeps = u.r.max_sweeps;
+            o.deadline_us = u.r.deadline_us;
+            o.reeval_rule = u.r.reeval_all ? DGS_REEVAL_ALL : DGS_REEVAL_BOX;
+            Result res{};
+            dgs_status outcome = DGS_OK;
+            dgs_status st = solve_for_server(reinterpret_cast<const int32_t*>(u.mem), n, out, &res.objective, &o,
+                                             &res.stats, ss, &outcome);
+            if (st == DGS_OK && h_solo_cap < (size_t)n) {
+                if (h_solo) cudaFreeHost(h_solo);
+                h_solo = nullptr;
+                h_solo_cap = 0;
+                if (cudaMallocHost(&h_solo, sizeof(int32_t) * n) == cudaSuccess) h_solo_cap = n;
+                else st = fail(cudaErrorMemoryAllocation, "result staging");
+            }
+            cudaError_t e = cudaSuccess;
+            if (st == DGS_OK) e = cudaMemcpyAsync(h_solo, out, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ss);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ss);
+            if (e != cudaSuccess) st = fail(e, "solo result");
+            res.status = st == DGS_OK ? outcome : st;
+            if (st == DGS_OK && (outcome == DGS_OK || outcome == DGS_TIMEOUT)) res.sigma.assign(h_solo, h_solo + n);
+            res.times.submit_ns = u.r.submit_ns;
+            res.times.admit_ns = u.admit_ns;
+            res.times.done_ns = now_ns();
+            cudaFreeAsync(u.mem, ss);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                --solo_count;
+                if (pending.count(u.r.ticket)) record_result(u.r.ticket, std::move(res), u.r.bytes);
+                else used -= u.r.bytes;  // already answered by a fatal error
+            }
+            cv_done.notify_all();
             cv_work.notify_one();
         }
     }
@@ -650,12 +773,14 @@ struct dgs_server {
             {
                 std::unique_lock<std::mutex> lk(mu);
                 // admission in arrival order while the budget and a slot allow
-                while (!stop && !queue.empty() && resident_count + reserved < eng.capacity() &&
+                while (!stop && !queue.empty() &&
+                       (solo_request(queue.front().n) || resident_count + reserved < eng.capacity()) &&
                        used + queue.front().bytes <= budget) {
                     const Request r = queue.front();
                     queue.pop_front();
                     used += r.bytes;
-                    ++reserved;
+                    if (solo_request(r.n)) ++solo_count;
+                    else ++reserved;
                     pending[r.ticket] = 1;
                     to_upload.push_back(r);
                     cv_up.notify_one();
@@ -664,7 +789,8 @@ struct dgs_server {
                     if (stop && reserved == 0) break;
                     cv_work.wait(lk, [&] {
                         return !ready.empty() || (stop && reserved == 0) ||
-                               (!stop && !queue.empty() && resident_count + reserved < eng.capacity() &&
+                               (!stop && !queue.empty() &&
+                                (solo_request(queue.front().n) || resident_count + reserved < eng.capacity()) &&
                                 used + queue.front().bytes <= budget);
                     });
                     continue;
@@ -819,12 +945,17 @@ dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_serv
     }
     for (int u = 0; u < dgs_server::kUploaders && e == cudaSuccess; ++u)
         e = cudaStreamCreateWithFlags(&sv->up_stream[u], cudaStreamNonBlocking);
+    for (int u = 0; u < dgs_server::kSolo && e == cudaSuccess; ++u)
+        e = cudaStreamCreateWithFlags(&sv->solo_stream[u], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         for (int u = 0; u < dgs_server::kUploaders; ++u)
             if (sv->up_stream[u]) cudaStreamDestroy(sv->up_stream[u]);
+        for (int u = 0; u < dgs_server::kSolo; ++u)
+            if (sv->solo_stream[u]) cudaStreamDestroy(sv->solo_stream[u]);
         delete sv;
         return fail(e, "upload stream");
     }
+    for (int u = 0; u < dgs_server::kSolo; ++u) sv->solo[u] = std::thread([sv, u] { sv->run_solo(u); });
     sv->worker = std::thread([sv] { sv->run(); });
     for (int u = 0; u < dgs_server::kUploaders; ++u) sv->uploader[u] = std::thread([sv, u] { sv->run_uploader(u); });
     *out = sv;
@@ -937,9 +1068,18 @@ void dgs_server_destroy(dgs_server* sv) {
     sv->cv_work.notify_all();
     for (auto& t : sv->uploader)
         if (t.joinable()) t.join();
+    {  // no more large requests arrive: the solo thread finishes those it has
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->solo_stop = true;
+    }
+    sv->cv_solo.notify_all();
+    for (auto& t : sv->solo)
+        if (t.joinable()) t.join();
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     if (sv->h_sigma) cudaFreeHost(sv->h_sigma);
+    for (int u = 0; u < dgs_server::kSolo; ++u)
+        if (sv->solo_stream[u]) cudaStreamDestroy(sv->solo_stream[u]);
     for (int u = 0; u < dgs_server::kUploaders; ++u)
         if (sv->up_stream[u]) cudaStreamDestroy(sv->up_stream[u]);
     delete sv;

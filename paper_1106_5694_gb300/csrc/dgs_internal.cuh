@@ -390,6 +390,10 @@ cudaError_t launch_slots_from_keys(const Workspace& w, cudaStream_t s);
 cudaError_t launch_sequential(const Workspace& w, cudaStream_t s);
 
 size_t carve_instance(char* base, int32_t n, bool need_copy, Instance* in);
+// One stream-ordered single solve (dgs_solve_ex) for the server's large
+// requests; *final_status gets the outcome when the stream reaches it.
+dgs_status solve_for_server(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
+                            const dgs_options* opt, dgs_stats* stats, cudaStream_t stream, dgs_status* final_status);
 // The random start of DGS_INIT_RANDOM (splitmix64 + Fisher-Yates) on the host.
 void random_start(int32_t n, uint64_t seed, int32_t* tau);
 

@@ -355,7 +355,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         // CC (Algorithm 4): the accepted set is the greedy one in priority
         // order (a slot is accepted when neither agent of its exchange was
         // claimed by an earlier accepted slot).  The list is taken in chunks
-        // of one edge per thread, in order: an edge touching an agent claimed
+        // of four edges per thread, in order: an edge touching an agent claimed
         // by an earlier chunk is rejected at once; the chunk's other edges
         // are decided among themselves by deterministic reservations (each
         // round, the remaining candidates reserve both agents with a key that
@@ -365,52 +365,76 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         // every round accepts at least one edge).  Claims of a chunk reach
         // the next through a barrier, so the result is the greedy one.
         {
+            constexpr int kPer = 4;  // edges per thread and chunk (a chunk is kPer * kCtlThreads positions)
             int32_t ev = 0;
-            for (int32_t c0 = 0; c0 < L; c0 += kCtlThreads) {
-                const int32_t p = c0 + tid;
-                const uint8_t es = p < L ? estate[p] : (uint8_t)0;
-                int32_t u = 0, v = 0;
-                bool cand = false;
-                if (es & kAlive) {
-                    const EdgeT e = E[p];
-                    u = C::u(e);
-                    v = C::v(e);
-                    cand = claimed[u] != stamp && claimed[v] != stamp;
+            for (int32_t c0 = 0; c0 < L; c0 += kPer * kCtlThreads) {
+                int32_t p[kPer], u[kPer], v[kPer];
+                uint8_t es[kPer];
+                bool cand[kPer];
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    p[k] = c0 + k * kCtlThreads + tid;
+                    es[k] = p[k] < L ? estate[p[k]] : (uint8_t)0;
+                    u[k] = 0;
+                    v[k] = 0;
+                    cand[k] = false;
+                    if (es[k] & kAlive) {
+                        const EdgeT e = E[p[k]];
+                        u[k] = C::u(e);
+                        v[k] = C::v(e);
+                        cand[k] = claimed[u[k]] != stamp && claimed[v[k]] != stamp;
+                    }
+                    any |= cand[k];
                 }
-                for (int32_t r = 0; __syncthreads_or(cand); ++r) {
-                    if (r > kCtlThreads) {  // every round accepts the first candidate
+                for (int32_t r = 0; __syncthreads_or(any); ++r) {
+                    if (r > kPer * kCtlThreads) {  // every round accepts the first candidate
                         if (tid == 0) {
                             st->error = kErrInternal;
                             st->status = kError;
                         }
-                        cand = false;
+#pragma unroll
+                        for (int k = 0; k < kPer; ++k) cand[k] = false;
+                        any = false;
                         continue;
                     }
                     if ((s_round & (span - 1u)) == 0u && s_round != 0u) {  // reservation keys wrap
                         for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
                         __syncthreads();
                     }
-                    const uint32_t key = round_base(s_round, span) | (uint32_t)p;
-                    if (cand) {
-                        if (key < res[u]) atomicMin(&res[u], key);
-                        if (key < res[v]) atomicMin(&res[v], key);
+                    const uint32_t base = round_base(s_round, span);
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k) {
+                        if (!cand[k]) continue;
+                        const uint32_t key = base | (uint32_t)p[k];
+                        if (key < res[u[k]]) atomicMin(&res[u[k]], key);
+                        if (key < res[v[k]]) atomicMin(&res[v[k]], key);
                     }
                     __syncthreads();
-                    if (cand && res[u] == key && res[v] == key) {
-                        claimed[u] = stamp;
-                        claimed[v] = stamp;
-                        accl.put(atomicAdd(&s_acc, 1), p);
-                        if (slot_s) {  // the re-evaluation record of its slot
-                            const int32_t t = slot_s[p];
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rkey + t));
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k) {
+                        const uint32_t key = base | (uint32_t)p[k];
+                        if (cand[k] && res[u[k]] == key && res[v[k]] == key) {
+                            claimed[u[k]] = stamp;
+                            claimed[v[k]] = stamp;
+                            accl.put(atomicAdd(&s_acc, 1), p[k]);
+                            if (slot_s) {  // the re-evaluation record of its slot
+                                const int32_t t = slot_s[p[k]];
+                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rkey + t));
+                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
+                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
+                            }
+                            ev |= (es[k] & kAppl) ? 1 : 0;
+                            cand[k] = false;
                         }
-                        ev |= (es & kAppl) ? 1 : 0;
-                        cand = false;
                     }
                     __syncthreads();  // this round's claims are visible
-                    if (cand && (claimed[u] == stamp || claimed[v] == stamp)) cand = false;  // rejected
+                    any = false;
+#pragma unroll
+                    for (int k = 0; k < kPer; ++k) {
+                        if (cand[k] && (claimed[u[k]] == stamp || claimed[v[k]] == stamp)) cand[k] = false;  // rejected
+                        any |= cand[k];
+                    }
                     if (tid == 0) s_round = s_round + 1u;
                 }
             }

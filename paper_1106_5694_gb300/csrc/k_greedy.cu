@@ -673,13 +673,10 @@ cudaError_t launch_b_greedy(const BatchTable& rows, const BatchQueues& q, cudaSt
 
 
 // DGS_GREEDY_ROUNDS=1: the locally-dominant rounds instead of deferred
-// acceptance (tests; the same assignment).
+// acceptance (tests; the same assignment).  Read at every call.
 int32_t greedy_rounds_env() {
-    static const int32_t v = [] {
-        const char* e = std::getenv("DGS_GREEDY_ROUNDS");
-        return (e && std::atoi(e) == 1) ? 1 : 0;
-    }();
-    return v;
+    const char* e = std::getenv("DGS_GREEDY_ROUNDS");
+    return (e && std::atoi(e) == 1) ? 1 : 0;
 }
 
 cudaError_t launch_greedy_da(const Workspace& w, cudaStream_t s) {

@@ -76,6 +76,25 @@ def test_greedy_matches_oracle(kind, n, seed):
     np.testing.assert_array_equal(sig.cpu().numpy(), oracle.greedy_init(a))
 
 
+@pytest.mark.parametrize("kind,n,seed", [("ties", 300, 1), ("peer", 2000, 2), ("uniform", 1500, 3), ("wide", 97, 4)])
+def test_greedy_rounds_fallback_equals_deferred_acceptance(kind, n, seed, monkeypatch):
+    """The fallback greedy start (locally-dominant rounds run as a device
+    loop) and deferred acceptance give the same assignment, the oracle's."""
+    a = _make(kind, n, seed)
+    ref = oracle.greedy_init(a)
+    st, sig = B.dgs_greedy_init(_cuda(a))
+    assert st == B.DGS_OK
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref)
+    monkeypatch.setenv("DGS_GREEDY_ROUNDS", "1")
+    st, sig_r = B.dgs_greedy_init(_cuda(a))
+    assert st == B.DGS_OK
+    np.testing.assert_array_equal(sig_r.cpu().numpy(), ref)
+    st, tau, f, stats = B.dgs_solve_ex(_cuda(a))
+    full = oracle.dgs_parallel(a)
+    assert st == B.DGS_OK and f == full.objective and stats["sweeps"] == full.sweeps
+    np.testing.assert_array_equal(tau.cpu().numpy(), full.tau)
+
+
 # ------------------------------------------------------------------ full solve
 SOLVE_CASES = [(k, n, s) for k in ("uniform", "ties", "peer", "geom", "wide")
                for n in (2, 3, 9, 33, 64, 129, 200) for s in (0, 1)] + \
