@@ -121,7 +121,12 @@ class Engine {
     }
 
     dgs_status init() {
-        B_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking), "stream");
+        // the batched steps carry many small instances: their stream has the
+        // highest priority, so that the server's solo solves (lowest
+        // priority) yield SMs to them
+        int least = 0, greatest = 0;
+        B_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+        B_CUDA(cudaStreamCreateWithPriority(&stream_, cudaStreamNonBlocking, greatest), "stream");
         B_CUDA(cudaMalloc(&d_inst_, sizeof(Instance) * cap_), "instance table");
         B_CUDA(cudaMalloc(&d_st_, sizeof(DeviceState) * cap_), "loop states");
         B_CUDA(cudaMemset(d_st_, 0, sizeof(DeviceState) * cap_), "loop states");
@@ -528,7 +533,7 @@ struct dgs_server {
     size_t budget = 0;
     Engine eng;
     std::vector<Resident> slots;  // worker only
-    static constexpr int kUploaders = 2;  // uploads of different requests overlap
+    static constexpr int kUploaders = 3;  // uploads of different requests overlap
     static constexpr int kSolo = 3;       // large requests solved at once, each on its own stream
     std::thread worker, uploader[kUploaders], solo[kSolo];
     cudaStream_t up_stream[kUploaders] = {};
@@ -945,8 +950,10 @@ dgs_status dgs_server_create(size_t budget_bytes, int32_t max_resident, dgs_serv
     }
     for (int u = 0; u < dgs_server::kUploaders && e == cudaSuccess; ++u)
         e = cudaStreamCreateWithFlags(&sv->up_stream[u], cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     for (int u = 0; u < dgs_server::kSolo && e == cudaSuccess; ++u)
-        e = cudaStreamCreateWithFlags(&sv->solo_stream[u], cudaStreamNonBlocking);
+        e = cudaStreamCreateWithPriority(&sv->solo_stream[u], cudaStreamNonBlocking, least);
     if (e != cudaSuccess) {
         for (int u = 0; u < dgs_server::kUploaders; ++u)
             if (sv->up_stream[u]) cudaStreamDestroy(sv->up_stream[u]);
