@@ -1,6 +1,6 @@
-"""Sizes beyond the oracle's reach: the greedy start's per-round path (taken
-when n is too large for the persistent kernel's per-CTA lists, here n =
-40000) and a full solve there, checked by properties that hold at any size.
+"""Sizes beyond the oracle's reach (n = 40000, and the maximum 2^17): the
+greedy start by deferred acceptance and a full solve there, checked by
+properties that hold at any size.
 
 The global greedy assignment (reading R1) is characterised without running
 it: under the strict order of pairs (benefit desc, agent asc, job asc), a
@@ -65,7 +65,7 @@ def test_greedy_characterisation_against_the_oracle_and_a_planted_swap():
 
 
 @pytest.mark.parametrize("n,hi", [(40000, 1000), (40003, 10**6)])
-def test_greedy_per_round_path_is_the_global_greedy(n, hi):
+def test_greedy_start_at_large_n_is_the_global_greedy(n, hi):
     g = torch.Generator(device="cuda")
     g.manual_seed(n)
     a = torch.randint(0, hi, (n, n), dtype=torch.int32, device="cuda", generator=g)
