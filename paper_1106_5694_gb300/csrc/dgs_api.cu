@@ -107,6 +107,12 @@ int32_t env_compact_min() {
     }();
     return v;
 }
+// DGS_CC_COLOUR: 0 turns the colouring passes over runs of quiet sweeps
+// off.  Read on every launch, so that a test can compare both in one process.
+int32_t env_colour_pass() {
+    const char* e = std::getenv("DGS_CC_COLOUR");
+    return (e && std::atoi(e) == 0) ? 0 : 1;
+}
 int32_t env_short_wraps() {
     static const int32_t v = [] {
         const char* e = std::getenv("DGS_SHORT_WRAPS");
@@ -478,7 +484,7 @@ struct LoopCtx {
 struct LoopKey {
     unsigned char w[sizeof(Workspace)];
     unsigned char ctl[sizeof(CtlGlobal)];
-    int32_t rows, strip, tma, pad;
+    int32_t rows, strip, tma, colour_pass;  // launch shapes and the knob the captured kernels bake in
 };
 
 LoopKey loop_key(const LoopCtx& c) {
@@ -490,6 +496,7 @@ LoopKey loop_key(const LoopCtx& c) {
     k.rows = sh.rows;
     k.strip = sh.strip;
     k.tma = sh.tma;
+    k.colour_pass = env_colour_pass();
     return k;
 }
 
@@ -795,8 +802,13 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
             cudaStreamSynchronize(stream) == cudaSuccess) {
             fprintf(stderr, "[dgs phases] greedy: last group %llu ns, group sum %llu ns, longest chain %llu, "
                             "most scans of a group %llu | controller cycles: entry %llu top %llu conflict check %llu "
-                            "post %llu event %llu sweeps %llu\n",
-                    ph[0], ph[1], ph[2], ph[3], ph[8], ph[9], ph[10], ph[13], ph[14], ph[15]);
+                            "post %llu event %llu sweeps %llu | live edges summed over sweeps %llu, listed %llu, "
+                            "accepted in quiet sweeps %llu | colouring passes %llu, cycles %llu (reservation "
+                            "rounds %llu, after them %llu), sweeps run %llu\n",
+                    ph[kPtDaLastNs], ph[kPtDaSumNs], ph[kPtDaChain], ph[kPtDaGroupScans], ph[kPtCtlEntry],
+                    ph[kPtCtlTop], ph[kPtCtlPass1], ph[kPtCtlPost], ph[kPtCtlEvent], ph[kPtCtlSweeps],
+                    ph[kPtCtlLiveSum], ph[kPtCtlListSum], ph[kPtCtlAccSum], ph[kPtCtlColourPasses], ph[kPtCtlColour],
+                    ph[kPtCtlColourIters], ph[kPtCtlColourTail], ph[kPtCtlColourRounds]);
         }
     }
     if (o.profile) {  // the event timings need the solve to have run

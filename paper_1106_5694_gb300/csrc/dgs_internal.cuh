@@ -222,9 +222,9 @@ enum : int32_t { kScanPass1 = 0, kScanGreedyDA = 1, kScanStart = 2, kScanSwitch 
 
 // Phase timer slots.
 enum : int32_t {
-    kPtDaLastNs = 0, kPtDaSumNs, kPtDaChain, kPtDaGroupScans,
-    kPtCtlEntry = 8, kPtCtlTop, kPtCtlPass1, kPtCtlPass2, kPtCtlUnd, kPtCtlPost, kPtCtlEvent, kPtCtlSweeps,
-    kPtCount = 16
+    kPtDaLastNs = 0, kPtDaSumNs, kPtDaChain, kPtDaGroupScans, kPtCtlLiveSum, kPtCtlListSum, kPtCtlAccSum,
+    kPtCtlEntry, kPtCtlTop, kPtCtlPass1, kPtCtlPost, kPtCtlEvent, kPtCtlSweeps, kPtCtlColour, kPtCtlColourPasses,
+    kPtCtlColourRounds, kPtCtlColourIters, kPtCtlColourTail, kPtCount
 };
 
 // ------------------------------------------------------------- key packing
@@ -499,6 +499,7 @@ cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
 // DGS_CTL_COMPACT_MIN: shortest edge list the controller compacts (default
 // 2048; tests lower it so that compaction runs on small instances).
 int32_t env_compact_min();
+int32_t env_colour_pass();
 // DGS_EXACT_KEYS=1 disables the packed 32-bit keys of the evaluation kernel.
 int32_t env_exact_keys();
 

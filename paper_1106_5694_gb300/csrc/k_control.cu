@@ -138,14 +138,222 @@ struct Codec<unsigned long long> {
 };
 
 
+// Re-evaluation records of the first kRecCap accepted edges of a sweep are
+// copied into shared memory while the sweep's conflict check still runs
+// (asynchronous copies, awaited before its last barrier), so that a quiet
+// sweep's refresh reads no global memory; later ones are only prefetched.
+constexpr int32_t kRecCap = 64, kRecBytes = 16 * kRecCap;
+__device__ __forceinline__ void fetch_record(unsigned char* rec, int32_t idx, const Workspace& w, int32_t t) {
+    if (rec != nullptr && idx < kRecCap) {
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(rec + 16 * idx));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(w.sl_rkey + t) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 8), "l"(w.sl_ru + t) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 12), "l"(w.sl_rv + t) : "memory");
+    } else {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rkey + t));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
+    }
+}
+
+// Colouring pass.  In a sweep in which no accepted exchange applies (a quiet
+// sweep) sigma does not change, so every accepted edge is stale and is only
+// re-evaluated: it dies or comes back, applicable, at its position.  Round k
+// of a run of such sweeps accepts the greedy set of the edges left after the
+// rounds before it, so a stale edge is accepted exactly in the round that
+// first-fit edge colouring in position order gives it (the smallest colour
+// that no earlier stale edge sharing one of its agents has), and an
+// applicable edge in the first round from its birth on that no earlier stale
+// edge sharing an agent holds; the first such round ends the run with an
+// event.  The pass colours the stale edges with colours below kColourCap by
+// reservation rounds (an edge is coloured once it is the first pending edge
+// at both its agents, from the colour masks of those agents, which then hold
+// exactly its earlier neighbours' colours), finds the first round E in which
+// an applicable edge is accepted and the first round R in which a re-
+// evaluated edge that lives on is born (its colour + 1), and re-evaluates the
+// edges of the F = min(E, R, kColourCap, sweeps left) rounds before both at
+// once, as F quiet sweeps would; each round's count is left in s_hist.
+// Colour masks use the claim array (cleared afterwards), colours the high
+// half of the edge states.  Rounds past the last one with an accepted edge
+// are not counted: with no edge left the run ends.  Returns F, or -1 on an
+// internal error.
+constexpr int32_t kColourCap = 8;
+
+template <typename EdgeT>
+__device__ __forceinline__ int32_t colour_pass_rounds(const Workspace& w, EdgeT* E, uint8_t* estate,
+                                                      const uint16_t* slot_s, uint32_t* res, uint8_t* mask,
+                                                      int32_t L, uint32_t span, uint32_t& s_round, int32_t& s_pE,
+                                                      int32_t& s_pR, int32_t& s_pF, int32_t* s_hist,
+                                                      int32_t max_sweeps, int32_t sweeps, int32_t& s_live,
+                                                      unsigned long long* s_pt) {
+    using C = Codec<EdgeT>;
+    const int tid = threadIdx.x;
+    const int32_t n = w.n;
+    for (int32_t i = tid; i < n; i += kCtlThreads) mask[i] = 0;
+    if (tid == 0) {
+        s_pE = kColourCap;
+        s_pR = kColourCap;
+        for (int k = 0; k < kColourCap; ++k) s_hist[k] = 0;
+    }
+    __syncthreads();
+    // The edges of the thread's first kHeld positions (tid + k kCtlThreads)
+    // and their states are held in registers for the whole pass: bit k of pm
+    // says pending, of am applicable; nibble k of cols is the outcome (c + 1
+    // coloured c, 15 closed).  Positions past them keep theirs in the high
+    // half of the edge states.
+    constexpr int kHeld = 8;
+    EdgeT he[kHeld];
+    uint32_t pm = 0, am = 0, cols = 0;
+#pragma unroll
+    for (int k = 0; k < kHeld; ++k) {
+        const int32_t p = tid + k * kCtlThreads;
+        const uint8_t es = p < L ? estate[p] : (uint8_t)0;
+        he[k] = (es & kAlive) ? E[p] : (EdgeT)0;
+        if (es & kAlive) pm |= 1u << k;
+        if (es & kAppl) am |= 1u << k;
+    }
+    const int32_t tail0 = kHeld * kCtlThreads;
+    // one pending edge, first half of a round: false if it closes (masks only
+    // grow: a full one leaves no colour, or round, below the cap), else it
+    // reserves both agents
+    auto reserve = [&](int32_t p, EdgeT e, bool appl, uint32_t base) -> bool {
+        const int32_t u = C::u(e), v = C::v(e);
+        const uint32_t mu = mask[u], mv = mask[v];
+        if (appl ? (mu | mv) == 0xFFu : (mu == 0xFFu || mv == 0xFFu)) return false;
+        const uint32_t key = base | (uint32_t)p;
+        if (key < res[u]) atomicMin(&res[u], key);
+        if (key < res[v]) atomicMin(&res[v], key);
+        return true;
+    };
+    // second half: -1 while an earlier edge at u or v is pending, else the
+    // outcome; the edge is then the only one holding u and v, so its mask
+    // updates are plain stores
+    auto settle = [&](int32_t p, EdgeT e, bool appl, uint32_t base) -> int32_t {
+        const int32_t u = C::u(e), v = C::v(e);
+        const uint32_t key = base | (uint32_t)p;
+        if (res[u] != key || res[v] != key) return -1;
+        const uint32_t fr = ~((uint32_t)mask[u] | (uint32_t)mask[v]) & 0xFFu;
+        if (appl) {
+            if (fr) atomicMin(&s_pE, __ffs(fr) - 1);
+            return 15;
+        }
+        if (!fr) return 15;
+        const int32_t c = __ffs(fr) - 1;
+        mask[u] |= (uint8_t)(1u << c);
+        mask[v] |= (uint8_t)(1u << c);
+        return c + 1;
+    };
+    for (int32_t r = 0;; ++r) {
+        if (r > L + 1) return -1;  // every round colours or closes the first pending edge
+        if ((s_round & (span - 1u)) == 0u && s_round != 0u) {  // reservation keys wrap
+            for (int32_t i = tid; i < n; i += kCtlThreads) res[i] = 0xFFFFFFFFu;
+            __syncthreads();
+        }
+        const uint32_t base = round_base(s_round, span);
+        bool pend = false;
+#pragma unroll
+        for (int k = 0; k < kHeld; ++k) {
+            if (!((pm >> k) & 1u)) continue;
+            if (reserve(tid + k * kCtlThreads, he[k], (am >> k) & 1u, base)) {
+                pend = true;
+            } else {
+                pm &= ~(1u << k);
+                cols |= 15u << (4 * k);
+            }
+        }
+        for (int32_t p = tail0 + tid; p < L; p += kCtlThreads) {
+            const uint8_t es = estate[p];
+            if (!(es & kAlive) || (es >> 4)) continue;
+            if (reserve(p, E[p], (es & kAppl) != 0, base)) pend = true;
+            else estate[p] = es | 0xF0;
+        }
+        if (s_pt && tid == 0) s_pt[kPtCtlColourIters] += 1;
+        if (!__syncthreads_or(pend)) break;
+#pragma unroll
+        for (int k = 0; k < kHeld; ++k) {
+            if (!((pm >> k) & 1u)) continue;
+            const int32_t nib = settle(tid + k * kCtlThreads, he[k], (am >> k) & 1u, base);
+            if (nib >= 0) {
+                pm &= ~(1u << k);
+                cols |= (uint32_t)nib << (4 * k);
+            }
+        }
+        for (int32_t p = tail0 + tid; p < L; p += kCtlThreads) {
+            const uint8_t es = estate[p];
+            if (!(es & kAlive) || (es >> 4)) continue;
+            const int32_t nib = settle(p, E[p], (es & kAppl) != 0, base);
+            if (nib >= 0) estate[p] = es | (uint8_t)(nib << 4);
+        }
+        if (tid == 0) s_round = s_round + 1u;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kHeld; ++k) {  // outcomes back to the edge states (the same thread reads them next)
+        const uint32_t nib = (cols >> (4 * k)) & 15u;
+        if (nib) estate[tid + k * kCtlThreads] |= (uint8_t)(nib << 4);
+    }
+    const long long t_tail = clock64();
+    for (int32_t p = tid; p < L; p += kCtlThreads) {
+        const int32_t nib = estate[p] >> 4;
+        if (nib < 1 || nib > kColourCap) continue;
+        atomicAdd(&s_hist[nib - 1], 1);
+        const int32_t t = slot_s ? (int32_t)slot_s[p] : w.ctl_slot[p];
+        const unsigned long long key = w.sl_rkey[t];
+        if (key && key_gain(key) > 0) atomicMin(&s_pR, nib);  // born in round colour + 1 = nib
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int32_t F = min(s_pE, s_pR);
+        if (max_sweeps > 0) F = min(F, max_sweeps - sweeps);
+        F = max(F, 0);
+        // a round with live edges accepts at least one (and an edge of colour c
+        // has neighbours of every colour below c): an empty round means that
+        // no edge is left, and the run ends before it
+        while (F > 0 && s_hist[F - 1] == 0) --F;
+        s_pF = F;
+    }
+    __syncthreads();
+    const int32_t F = s_pF;
+    int32_t died = 0;
+    for (int32_t p = tid; p < L; p += kCtlThreads) {
+        uint8_t es = estate[p];
+        const int32_t nib = es >> 4;
+        if (!nib) continue;
+        es &= 0x0F;
+        if (nib <= F) {  // accepted in round nib - 1 < F: re-evaluated
+            const int32_t t = slot_s ? (int32_t)slot_s[p] : w.ctl_slot[p];
+            const unsigned long long key = w.sl_rkey[t];
+            const int32_t gain = key ? key_gain(key) : 0;
+            const int32_t target = key ? key_index(key) : -1;
+            if (t < n) { w.ag_gain[t] = gain; w.ag_job[t] = target; }
+            else { w.jb_gain[t - n] = gain; w.jb_agent[t - n] = target; }
+            if (gain > 0) {
+                E[p] = C::make(w.sl_ru[t], w.sl_rv[t]);
+                es = kAlive | kAppl | kFreshBit;
+            } else {
+                es = 0;
+                ++died;
+            }
+        }
+        estate[p] = es;
+    }
+    if (died) atomicSub(&s_live, died);
+    for (int32_t i = tid; i < n; i += kCtlThreads) mask[i] = 0;  // claim stamps start clean
+    __syncthreads();
+    if (s_pt && tid == 0) s_pt[kPtCtlColourTail] += (unsigned long long)(clock64() - t_tail);
+    return F;
+}
+
 // Switching loop (see the file comment).
 // span: reservation-key period (power of two <= kRoundSpanMax); stamp_wrap:
 // claim-stamp period (<= 255).  Both are shortened only by a test knob.
 // list_cap: entries of the accepted list held in shared memory.
+// colour_pass: runs of quiet sweeps go through colouring passes (shared-
+// memory mode 2 only); 0 turns them off.
 template <typename EdgeT>
 __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem_mode, const CtlScratch& g,
                                                 uint32_t span, uint32_t stamp_wrap, int32_t list_cap,
-                                                int32_t compact_min) {
+                                                int32_t compact_min, int32_t colour_pass) {
     using C = Codec<EdgeT>;
     DeviceState* st = w.st;
     if (st->status != kRunning) return;
@@ -153,6 +361,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     __shared__ int32_t warp_sums[33];
     __shared__ int32_t s_L, s_live, s_stop, s_acc, s_app, s_y, s_sweeps, s_event;
     __shared__ int32_t s_max_sweeps, s_trace_cap;
+    __shared__ int32_t s_pass_ok, s_pE, s_pR, s_pF, s_hist[kColourCap];
     __shared__ uint32_t s_round;
     __shared__ uint32_t s_stamp;
     __shared__ unsigned long long s_gain, s_deadline;
@@ -166,9 +375,12 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     EdgeT* E = static_cast<EdgeT*>(g.edges);
     uint16_t* lists_s = nullptr;
     uint16_t* slot_s = nullptr;  // slot of each edge position (shared-memory modes)
+    unsigned char* rec = nullptr;  // re-evaluation records (shared-memory modes)
     if (smem_mode >= 1) {
         size_t off = 0;
-        res = reinterpret_cast<uint32_t*>(smem_raw);
+        rec = smem_raw;
+        off += kRecBytes;
+        res = reinterpret_cast<uint32_t*>(smem_raw + off);
         off += 4 * (size_t)n;
         if (smem_mode == 2) {
             E = reinterpret_cast<EdgeT*>(smem_raw + off);
@@ -186,11 +398,19 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
     TwoTier accl{lists_s, cap, g.acc_g};
     unsigned long long* pt = (tid == 0) ? w.phase_ns : nullptr;
     long long tp = clock64();
-#define DGS_CT(slot)                                            \
-    if (pt) {                                                   \
-        const long long now = clock64();                        \
-        atomicAdd(pt + (slot), (unsigned long long)(now - tp)); \
-        tp = now;                                               \
+    // diagnostics (DGS_PHASE_TIMERS=1): thread 0 sums into shared memory and
+    // adds the sums to global memory once per launch, so that the counters
+    // add no global round trips to the loops they time
+    __shared__ unsigned long long s_pt[kPtCount];
+    if (pt)
+        for (int k = 0; k < kPtCount; ++k) s_pt[k] = 0ull;
+#define DGS_PT(slot, v) \
+    if (pt) s_pt[slot] += (unsigned long long)(v);
+#define DGS_CT(slot)                     \
+    if (pt) {                            \
+        const long long now = clock64(); \
+        s_pt[slot] += (unsigned long long)(now - tp); \
+        tp = now;                        \
     }
 
     // ---------------------------------------------------------------- entry
@@ -211,6 +431,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             s_f = st->f;
             s_round = 0;
             s_stamp = 0;
+            s_pass_ok = 0;  // a colouring pass follows a quiet sweep
         }
         // Warp wp lists the slots of its own range [lo, hi) (ranges are
         // multiples of 32 long and ascend with wp): it sums the edge counts
@@ -307,7 +528,9 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         __syncthreads();
         DGS_CT(kPtCtlTop)
         if (s_stop) break;
-        if (pt) atomicAdd(pt + kPtCtlSweeps, 1ull);
+        DGS_PT(kPtCtlSweeps, 1)
+        DGS_PT(kPtCtlLiveSum, s_live)
+        DGS_PT(kPtCtlListSum, L)
         // An edge that dies in a quiet sweep never lives again in this launch.
         // Once fewer than half of the L listed positions are live, compact the
         // list in place, keeping the priority order (positions are
@@ -352,6 +575,41 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             __syncthreads();
         }
         const uint8_t stamp = (uint8_t)s_stamp;
+        // Colouring pass (after a quiet sweep; see colour_pass_rounds).  It
+        // runs F >= 1 sweeps at once, or none when an applicable edge is
+        // accepted in this very sweep; then this sweep goes on as usual.
+        // (mode 2 holds n <= 32767, so only 32-bit edges take this path)
+        if (sizeof(EdgeT) == 4 && colour_pass && smem_mode == 2 && s_pass_ok) {
+            const int32_t F = colour_pass_rounds<EdgeT>(w, E, estate, slot_s, res, claimed, L, span, s_round, s_pE,
+                                                        s_pR, s_pF, s_hist, s_max_sweeps, s_sweeps, s_live,
+                                                        pt ? s_pt : nullptr);
+            if (F < 0) {  // internal error
+                if (tid == 0) {
+                    st->error = kErrInternal;
+                    st->status = kError;
+                }
+                break;
+            }
+            if (tid == 0) {
+                for (int32_t k = 0; k < F; ++k) {
+                    const int32_t sw = s_sweeps + k;
+                    if (sw < s_trace_cap) {
+                        if (st->trace_accepted) st->trace_accepted[sw] = s_hist[k];
+                        if (st->trace_applied) st->trace_applied[sw] = 0;
+                        if (st->trace_objective) st->trace_objective[sw] = s_f;
+                    }
+                }
+                s_sweeps = s_sweeps + F;
+                DGS_PT(kPtCtlColourPasses, 1)
+                DGS_PT(kPtCtlColourRounds, F)
+                // another pass may follow at once only if this one met no
+                // bound inside its window
+                s_pass_ok = (F == kColourCap && s_pE >= kColourCap && s_pR >= kColourCap) ? 1 : 0;
+            }
+            __syncthreads();
+            DGS_CT(kPtCtlColour)
+            if (F > 0) continue;
+        }
         // CC (Algorithm 4): the accepted set is the greedy one in priority
         // order (a slot is accepted when neither agent of its exchange was
         // claimed by an earlier accepted slot).  The list is taken in chunks
@@ -365,11 +623,11 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         // every round accepts at least one edge).  Claims of a chunk reach
         // the next through a barrier, so the result is the greedy one.
         {
+            int32_t ev = 0;
             // edges per thread and chunk (a chunk is kPer * kCtlThreads
             // positions); four per thread crossed fewer barriers but was
             // slower (uniform n = 10000: 22.2 ms against 18.8 ms), so one
             constexpr int kPer = 1;
-            int32_t ev = 0;
             for (int32_t c0 = 0; c0 < L; c0 += kPer * kCtlThreads) {
                 int32_t p[kPer], u[kPer], v[kPer];
                 uint8_t es[kPer];
@@ -395,6 +653,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                         if (tid == 0) {
                             st->error = kErrInternal;
                             st->status = kError;
+                            s_stop = 1;
                         }
 #pragma unroll
                         for (int k = 0; k < kPer; ++k) cand[k] = false;
@@ -425,13 +684,9 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                         if (cand[k] && res[u[k]] == key && res[v[k]] == key) {
                             claimed[u[k]] = stamp;
                             claimed[v[k]] = stamp;
-                            accl.put(atomicAdd(&s_acc, 1), p[k]);
-                            if (slot_s) {  // the re-evaluation record of its slot
-                                const int32_t t = slot_s[p[k]];
-                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rkey + t));
-                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_ru + t));
-                                asm volatile("prefetch.global.L1 [%0];" ::"l"(w.sl_rv + t));
-                            }
+                            const int32_t idx = atomicAdd(&s_acc, 1);
+                            accl.put(idx, p[k]);
+                            if (slot_s) fetch_record(rec, idx, w, slot_s[p[k]]);  // its slot's re-evaluation
                             ev |= (es[k] & kAppl) ? 1 : 0;
                             cand[k] = false;
                         }
@@ -447,10 +702,11 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                 }
             }
             if (ev) s_event = 1;
+            if (rec) asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
         }
         DGS_CT(kPtCtlPass1)
-        if (st->status != kRunning) break;
+        if (s_stop) break;  // an internal error of the conflict check
         const int32_t nacc = s_acc;
         if (s_event) {
             // parallel switch: accepted exchanges are agent-disjoint; those
@@ -535,13 +791,17 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         for (int32_t q = tid; q < nacc; q += kCtlThreads) {
             const int32_t p = accl.get(q);
             const int32_t t = slot_s ? (int32_t)slot_s[p] : w.ctl_slot[p];
-            const unsigned long long key = w.sl_rkey[t];
+            const bool held = rec != nullptr && q < kRecCap;
+            const unsigned long long key =
+                held ? *reinterpret_cast<const unsigned long long*>(rec + 16 * q) : w.sl_rkey[t];
             const int32_t gain = key ? key_gain(key) : 0;
             const int32_t target = key ? key_index(key) : -1;
             if (t < n) { w.ag_gain[t] = gain; w.ag_job[t] = target; }
             else { w.jb_gain[t - n] = gain; w.jb_agent[t - n] = target; }
             if (gain > 0) {
-                E[p] = C::make(w.sl_ru[t], w.sl_rv[t]);
+                const int32_t ru = held ? *reinterpret_cast<const int32_t*>(rec + 16 * q + 8) : w.sl_ru[t];
+                const int32_t rv = held ? *reinterpret_cast<const int32_t*>(rec + 16 * q + 12) : w.sl_rv[t];
+                E[p] = C::make(ru, rv);
                 estate[p] = kAlive | kAppl | kFreshBit;
             } else {
                 estate[p] = 0;
@@ -549,6 +809,8 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             }
         }
         if (died) atomicSub(&s_live, died);
+        if (tid == 0) s_pass_ok = 1;
+        DGS_PT(kPtCtlAccSum, nacc)
         if (tid == 0 && s_sweeps < s_trace_cap) {
             const int32_t sw = s_sweeps;
             if (st->trace_accepted) st->trace_accepted[sw] = nacc;
@@ -560,6 +822,10 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         DGS_CT(kPtCtlPost)
     }
 #undef DGS_CT
+#undef DGS_PT
+    if (pt)
+        for (int k = 0; k < kPtCount; ++k)
+            if (s_pt[k]) atomicAdd(pt + k, s_pt[k]);
     if (tid == 0) {
         st->sweeps = s_sweeps;
         st->edge_count = s_live;
@@ -576,8 +842,8 @@ template <typename EdgeT>
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
                                                                    uint32_t span, uint32_t stamp_wrap,
                                                                    int32_t list_cap, int32_t compact_min,
-                                                                   unsigned long long cond) {
-    controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min);
+                                                                   int32_t colour_pass, unsigned long long cond) {
+    controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min, colour_pass);
     if (cond != 0 && threadIdx.x == 0) {
         DeviceState* st = w.st;
         const int32_t it = ++st->loop_iterations;
@@ -850,7 +1116,8 @@ __device__ __forceinline__ void row_task_warp(const Workspace& w, int32_t j) {
 template <typename EdgeT>
 __global__ void __launch_bounds__(kCtlThreads, 1) small_loop_kernel(Workspace w, int32_t smem_mode, CtlScratch g,
                                                                    uint32_t span, uint32_t stamp_wrap,
-                                                                   int32_t list_cap, int32_t compact_min) {
+                                                                   int32_t list_cap, int32_t compact_min,
+                                                                   int32_t colour_pass) {
     __shared__ int32_t s_go, s_count;
     DeviceState* st = w.st;
     const int32_t n = w.n;
@@ -871,7 +1138,7 @@ __global__ void __launch_bounds__(kCtlThreads, 1) small_loop_kernel(Workspace w,
         __syncthreads();
         prepare_edges_body(w, 0, 1);
         __syncthreads();
-        controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min);
+        controller_body<EdgeT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min, colour_pass);
         if (tid == 0) {
             const int32_t it = ++st->loop_iterations;
             if (st->status == kRunning && it > 16 * n + 4096) {
@@ -1145,10 +1412,11 @@ __global__ void prepare_edges_batched_kernel(BatchTable t) {
 }
 
 __global__ void __launch_bounds__(kCtlThreads, 1) controller_batched_kernel(BatchTable t, uint32_t span,
-                                                                           uint32_t stamp_wrap, int32_t compact_min) {
+                                                                           uint32_t stamp_wrap, int32_t compact_min,
+                                                                           int32_t colour_pass) {
     for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t, int32_t) {
         const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc};
-        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min);
+        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min, colour_pass);
     });
 }
 
@@ -1193,8 +1461,8 @@ __global__ void advance_batched_kernel(BatchTable t, int32_t from_stage) {
 constexpr size_t kCtlSmemLimit = 227 * 1024 - 1024;
 
 static size_t ctl_fixed_bytes(int32_t n, int32_t mode) {
-    // res (4n) + slot of each position (4n) + claimed (n) + estate (2n) [+ 32-bit edges (8n)]
-    return 11 * (size_t)n + (mode == 2 ? 8 * (size_t)n : 0);
+    // records + res (4n) + slot of each position (4n) + claimed (n) + estate (2n) [+ 32-bit edges (8n)]
+    return kRecBytes + 11 * (size_t)n + (mode == 2 ? 8 * (size_t)n : 0);
 }
 
 int32_t controller_smem_mode(int32_t n) {
@@ -1245,7 +1513,8 @@ cudaError_t launch_small_loop(const Workspace& w, const CtlGlobal& gs, cudaStrea
     }
     const bool short_wrap = env_short_wraps() != 0;
     small_loop_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, short_wrap ? 4u : kRoundSpanMax,
-                                                              short_wrap ? 5u : 250u, cap, env_compact_min());
+                                                              short_wrap ? 5u : 250u, cap, env_compact_min(),
+                                                              env_colour_pass());
     return cudaGetLastError();
 }
 
@@ -1265,11 +1534,12 @@ cudaError_t launch_controller_impl(const Workspace& w, const CtlGlobal& gs, cuda
     const uint32_t span = short_wrap ? 4u : kRoundSpanMax;
     const uint32_t stamp_wrap = short_wrap ? 5u : 250u;
     const int32_t cmin = env_compact_min();
+    const int32_t cp = env_colour_pass();
     if (narrow)
-        controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin, handle);
+        controller_kernel<uint32_t><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin, cp, handle);
     else
         controller_kernel<unsigned long long><<<1, kCtlThreads, smem, s>>>(w, mode, c, span, stamp_wrap, cap, cmin,
-                                                                          handle);
+                                                                          cp, handle);
     return cudaGetLastError();
 }
 
@@ -1380,7 +1650,8 @@ cudaError_t launch_b_controller(const BatchTable& one, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const bool short_wrap = env_short_wraps() != 0;
     controller_batched_kernel<<<dgs::device_sms(), kCtlThreads, smem, s>>>(one, short_wrap ? 4u : kRoundSpanMax,
-                                                            short_wrap ? 5u : 250u, env_compact_min());
+                                                            short_wrap ? 5u : 250u, env_compact_min(),
+                                                            env_colour_pass());
     return cudaGetLastError();
 }
 

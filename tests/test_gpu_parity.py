@@ -95,6 +95,47 @@ def test_greedy_rounds_fallback_equals_deferred_acceptance(kind, n, seed, monkey
     np.testing.assert_array_equal(tau.cpu().numpy(), full.tau)
 
 
+_FF_REF = {}
+
+
+@pytest.mark.parametrize("colour", ["0", "1"])
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 1500, 3), ("wide", 1500, 5), ("ties", 700, 1), ("peer", 1200, 2),
+                                         ("wide", 300, 6)])
+def test_colouring_pass_matches_oracle(kind, n, seed, colour, monkeypatch):
+    """Runs of quiet sweeps taken by colouring passes (DGS_CC_COLOUR=1, the
+    default) or one sweep at a time (0): the same sweeps, per-sweep accepted
+    counts and objectives, and assignment as the oracle.  The wide-range
+    inputs give long quiet runs with many passes; n = 300 runs in the
+    single-CTA loop."""
+    a = _make(kind, n, seed)
+    key = (kind, n, seed)
+    if key not in _FF_REF:
+        _FF_REF[key] = oracle.dgs_parallel(a, trace_cap=100000)
+    ref = _FF_REF[key]
+    monkeypatch.setenv("DGS_CC_COLOUR", colour)
+    tr = _trace_tensors(max(ref.sweeps, 1))
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), trace=tr)
+    assert st == B.DGS_OK, B.dgs_status_string(st)
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective and stats["sweeps"] == ref.sweeps
+    k = ref.sweeps
+    np.testing.assert_array_equal(tr[0][:k].cpu().numpy(), ref.trace_accepted)
+    np.testing.assert_array_equal(tr[1][:k].cpu().numpy(), ref.trace_applied)
+    np.testing.assert_array_equal(tr[2][:k].cpu().numpy(), ref.trace_objective)
+
+
+@pytest.mark.parametrize("cap", [1, 3, 9, 40, 200])
+def test_colouring_pass_stops_at_the_sweep_cap(cap):
+    """A pass never runs past the sweep cap: the capped solve is the oracle's
+    prefix on a long quiet run."""
+    a = _make("wide", 1000, 8)
+    ref = oracle.dgs_parallel(a, max_sweeps=cap)
+    st, sig, f, stats = B.dgs_solve_ex(_cuda(a), max_sweeps=cap)
+    assert st == (B.DGS_TIMEOUT if ref.status == oracle.TIMEOUT else B.DGS_OK)
+    np.testing.assert_array_equal(sig.cpu().numpy(), ref.tau)
+    assert f == ref.objective and stats["sweeps"] == ref.sweeps
+
+
 # ------------------------------------------------------------------ full solve
 SOLVE_CASES = [(k, n, s) for k in ("uniform", "ties", "peer", "geom", "wide")
                for n in (2, 3, 9, 33, 64, 129, 200) for s in (0, 1)] + \
