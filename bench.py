@@ -44,6 +44,9 @@ def parse_args():
     p.add_argument("--n", type=int, default=10000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and served measurements")
+    p.add_argument("--serving-leg", action="store_true",
+                   help="internal: run only the serving measurement and print its JSON (the benchmark runs it "
+                        "this way in a fresh process)")
     p.add_argument("--curve", action="store_true",
                    help="runtime against n on GEOM instances from the random start (the paper's evaluation "
                         "workload), GPU and oracle, instead of the benchmark line")
@@ -447,7 +450,7 @@ def run_ours(args):
                                                    cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         except Exception as exc:
             extra["other_sizes"] = {"error": f"{type(exc).__name__}: {exc}"}
-        for key, fn in (("batched", run_batched), ("serving", run_serving)):
+        for key, fn in (("batched", run_batched), ("serving", run_serving_fresh)):
             try:
                 extra[key] = fn(dev)
             except Exception as exc:  # reported, never hides the main measurement
@@ -777,6 +780,12 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
         span = max(t_start + arrivals[k] + lat[k] for k in range(count)) - (t_start + arrivals[0])
         return {"solves_per_s": round(count / span, 2), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)}
 
+    def stages(tm):
+        """Where a served request spent its time, in ms."""
+        t = [tm["submit_ns"], tm["admit_ns"], tm["upload_ns"], tm["ready_ns"], tm["start_ns"], tm["done_ns"]]
+        names = ["waiting_for_admission", "waiting_for_an_uploader", "upload", "waiting_for_a_slot", "solve"]
+        return {f"ms_{k}": round((t[i + 1] - t[i]) / 1e6, 2) for i, k in enumerate(names)}
+
     def served_run(arrivals):
         srv = B.Server(budget_bytes=budget)
         w = srv.dgs_submit(bufs[0][:256, :256].copy())[1]  # warm-up (graph capture)
@@ -793,8 +802,7 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
             st, _, f, _, tm = srv.dgs_server_wait(t, timeout_us=600_000_000)
             ok = ok and st == B.DGS_OK and f == ref_f[k % distinct]
             lat.append((tm["done_ns"] - tm["submit_ns"]) / 1e9)
-            rows.append((lat[-1], (tm["admit_ns"] - tm["submit_ns"]) / 1e6, (tm["done_ns"] - tm["admit_ns"]) / 1e6,
-                         req_n[k]))
+            rows.append((lat[-1], req_n[k], tm))
             first_submit = tm["submit_ns"] if first_submit is None else min(first_submit, tm["submit_ns"])
             last_done = max(last_done, tm["done_ns"])
         info = srv.dgs_server_get_info()[1]
@@ -805,17 +813,23 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
         return {"solves_per_s": round(count / span, 2), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                 "upload_ms_per_request": round(info["upload_ms"] / count, 3),
                 "step_ms_total": round(info["step_ms"], 1), "steps": info["steps"],
-                "p99_request": {"n": p99[3], "ms_to_admission": round(p99[1], 2),
-                                "ms_admission_to_result": round(p99[2], 2)},
+                "p99_request": {"n": p99[1], **stages(p99[2])},
                 "parity": "every objective equal to the plain solve of the same request" if ok else "MISMATCH"}
+
+    import gc
 
     runs = []
     for frac in rates:
         for seed in seeds:
             arrivals = inputs.poisson_arrivals(count, frac * capacity, seed=seed)
             arrivals = arrivals - arrivals[0]
-            served = served_run(arrivals)
-            plain = plain_run(arrivals)
+            gc.collect()
+            gc.disable()  # no collector pauses inside either arm's timed run
+            try:
+                served = served_run(arrivals)
+                plain = plain_run(arrivals)
+            finally:
+                gc.enable()
             runs.append({"rate_fraction_of_plain_capacity": frac, "rate_per_s": round(frac * capacity, 2),
                          "arrival_seed": seed, "served": served, "plain": plain})
     return {
@@ -925,8 +939,39 @@ def run_curve(args):
                       "oracle_cores": 1}), flush=True)
 
 
+def run_serving_fresh(dev):
+    """The serving measurement in a fresh process on the same device: its
+    latency tail is sensitive to the state the earlier measurements leave in
+    this one (device and pinned memory pools, host threads, garbage), and a
+    server runs in a process of its own in practice."""
+    env = dict(os.environ)
+    env["CUDA_VISIBLE_DEVICES"] = str(torch_visible_index(dev))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--serving-leg"], env=env,
+                       capture_output=True, text=True, timeout=1800)
+    for line in reversed(r.stdout.splitlines()):
+        if line.startswith("{"):
+            out = json.loads(line)
+            out["process"] = "fresh process (spawned by the benchmark)"
+            return out
+    raise RuntimeError(f"serving leg exited {r.returncode}: {r.stderr[-500:]}")
+
+
+def torch_visible_index(dev):
+    """The physical index of local device `dev` as CUDA_VISIBLE_DEVICES names it."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[dev]
+    return dev
+
+
 def main():
     args = parse_args()
+    if args.serving_leg:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps(run_serving(0)), flush=True)
+        return
     if args.curve:
         run_curve(args)
         return

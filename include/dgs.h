@@ -29,7 +29,8 @@
  *     dgs_stats and dgs_options.status_out -- are valid once the stream has
  *     reached the end of the solve (for example after
  *     cudaStreamSynchronize); outputs in host memory are written then by a
- *     host callback on the stream.  The return value reports only what is
+ *     host callback on the stream, so host memory passed for them must stay
+ *     valid until the stream has reached that point.  The return value reports only what is
  *     known when the work is enqueued (invalid arguments, allocation or
  *     launch failures); the outcome of the solve itself (DGS_OK,
  *     DGS_TIMEOUT, DGS_ERR_RANGE, DGS_ERR_INVALID for a USER start that is
@@ -330,9 +331,13 @@ DGS_API dgs_status dgs_solve_batched(const int32_t* const* benefits, const int32
 typedef struct dgs_server dgs_server;
 #define DGS_SUBMIT_HOST 1
 typedef struct {
-    int64_t submit_ns;  /* steady-clock times of submission, admission and */
-    int64_t admit_ns;   /* completion (the step that finished the instance) */
-    int64_t done_ns;
+    int64_t submit_ns;  /* steady-clock times: submission, */
+    int64_t admit_ns;   /* admission (budget and a slot granted), */
+    int64_t done_ns;    /* completion (result ready to be taken), */
+    int64_t upload_ns;  /* start of the matrix's upload, */
+    int64_t ready_ns;   /* matrix on the device, */
+    int64_t start_ns;   /* solve started (placed in a slot of the batched */
+                        /* engine, or taken by a solo thread) */
 } dgs_request_times;
 typedef struct {
     int32_t resident;        /* instances on the device now */

@@ -90,7 +90,8 @@ class dgs_stats(ctypes.Structure):
 
 
 class dgs_request_times(ctypes.Structure):
-    _fields_ = [("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+    _fields_ = [("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("upload_ns", ctypes.c_int64), ("ready_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64)]
 
 
 class dgs_server_info(ctypes.Structure):
@@ -252,36 +253,57 @@ def _wait(benefit, stream):
     (stream if stream is not None else torch.cuda.current_stream(benefit.device)).synchronize()
 
 
+# Host memory that the library's stream callbacks of solves enqueued with
+# wait=False still have to write (objective, stats), each entry kept with an
+# event recorded after its solve until that event has completed: a caller may
+# drop the Pending at once.
+_IN_FLIGHT = []
+
+
+def _keep_until_done(benefit, stream, objs):
+    _IN_FLIGHT[:] = [x for x in _IN_FLIGHT if not x[0].query()]
+    ev = torch.cuda.Event()
+    ev.record(stream if stream is not None else torch.cuda.current_stream(benefit.device))
+    _IN_FLIGHT.append((ev, objs))
+
+
 class Pending:
     """A stream-ordered solve in flight (wait=False): result() waits for the
     stream and returns what the waiting form returns."""
 
-    def __init__(self, st, benefit, stream, out, f, stats):
+    def __init__(self, st, benefit, stream, out, f, stats=None, options=None, stats_dict=True, wait=True):
         self._st, self._benefit, self._stream = st, benefit, stream
-        self._out, self._f, self._stats = out, f, stats
+        self._out, self._f, self._stats, self._options = out, f, stats, options
+        self._stats_dict = stats_dict
+        if st == DGS_OK and not wait:
+            _keep_until_done(benefit, stream, (f, stats, options))
 
     def result(self):
-        if self._st != DGS_OK:
-            return self._st, self._out, int(self._f.value), self._stats.as_dict()
-        _wait(self._benefit, self._stream)
-        return int(self._stats.status), self._out, int(self._f.value), self._stats.as_dict()
+        if self._st == DGS_OK:
+            _wait(self._benefit, self._stream)
+        if self._stats is None:
+            if self._stats_dict:
+                return self._st, self._out, int(self._f.value), {}
+            return self._st, self._out, int(self._f.value)
+        st = int(self._stats.status) if self._st == DGS_OK else self._st
+        return st, self._out, int(self._f.value), self._stats.as_dict()
 
 
 def dgs_solve(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, wait=True):
     """dgs_solve (stream-ordered): returns (status of the call, sigma_out,
     objective).  With wait (default) the stream is synchronised first, so the
-    objective is final; the solve's own outcome (range error, ...) is not
-    reported by this entry point: after a device-side error every sigma_out
-    entry is -1, and dgs_solve_ex reports the outcome."""
+    objective is final; with wait=False a Pending whose result() does that.
+    The solve's own outcome (range error, ...) is not reported by this entry
+    point: after a device-side error every sigma_out entry is -1, and
+    dgs_solve_ex reports the outcome."""
     n = _n(benefit)
     if sigma_out is None:
         sigma_out = torch.empty(n, dtype=torch.int32, device=benefit.device)
     f = ctypes.c_int64(0)
     st = load().dgs_solve(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), ctypes.byref(f),
                           _stream(benefit, stream))
-    if wait and st == DGS_OK:
-        _wait(benefit, stream)
-    return st, sigma_out, int(f.value)
+    pending = Pending(st, benefit, stream, sigma_out, f, stats_dict=False, wait=wait)
+    return pending.result() if wait else pending
 
 
 def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, stream=None, wait=True,
@@ -292,8 +314,8 @@ def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, s
     the solve's outcome (dgs_stats.status); with wait=False a Pending whose
     result() does that.  objective_out / status_out: optional CUDA tensors
     (int64[1] / int32[1]) the device writes instead of host memory (the
-    returned objective is then 0); stats=False passes no stats (the call then
-    needs no host callback; the returned status is the call's).
+    returned objective is then 0); stats=False passes no stats (the returned
+    status is then the call's).
 
     Keyword options: init, init_sigma (int32 CUDA tensor), seed (random
     start), reeval (DGS_REEVAL_BOX / DGS_REEVAL_ALL), algorithm
@@ -313,11 +335,7 @@ def dgs_solve_ex(benefit: torch.Tensor, sigma_out: torch.Tensor | None = None, s
     s = dgs_stats()
     st = load().dgs_solve_ex(_dev(benefit, "benefit"), n, _dev(sigma_out, "sigma_out"), fp,
                              ctypes.byref(o), ctypes.byref(s) if stats else None, _stream(benefit, stream))
-    if not stats:
-        if wait and st == DGS_OK:
-            _wait(benefit, stream)
-        return st, sigma_out, int(f.value), {}
-    pending = Pending(st, benefit, stream, sigma_out, f, s)
+    pending = Pending(st, benefit, stream, sigma_out, f, s if stats else None, options=o, wait=wait)
     return pending.result() if wait else pending
 
 
@@ -468,7 +486,7 @@ class Server:
                 ctypes.byref(s), ctypes.byref(tm))
         if st != DGS_PENDING:
             self._keep.pop(ticket, None)
-        times = {"submit_ns": tm.submit_ns, "admit_ns": tm.admit_ns, "done_ns": tm.done_ns}
+        times = {k: getattr(tm, k) for k, _ in dgs_request_times._fields_}
         return st, out, int(f.value), s.as_dict(), times
 
     def dgs_poll(self, ticket: int):

@@ -507,11 +507,12 @@ struct dgs_server {
         uint64_t seed;
         int32_t max_sweeps;
         int64_t deadline_us;
+        int64_t admit_ns;
     };
     struct Uploaded {
         Request r;
         char* mem;
-        int64_t admit_ns;
+        int64_t upload_ns, ready_ns;
     };
     struct Resident {
         uint64_t ticket = 0;
@@ -519,7 +520,7 @@ struct dgs_server {
         size_t bytes = 0;
         int32_t n = 0;
         int32_t* out = nullptr;
-        int64_t submit_ns = 0, admit_ns = 0;
+        dgs_request_times times{};
     };
     struct Result {
         dgs_status status;
@@ -533,7 +534,10 @@ struct dgs_server {
     size_t budget = 0;
     Engine eng;
     std::vector<Resident> slots;  // worker only
-    static constexpr int kUploaders = 3;  // uploads of different requests overlap
+    // uploads of different requests overlap; small requests are uploaded
+    // first, and uploader 0 takes only small ones, so that a small request
+    // never waits behind the copies of large matrices
+    static constexpr int kUploaders = 4;
     static constexpr int kSolo = 3;       // large requests solved at once, each on its own stream
     std::thread worker, uploader[kUploaders], solo[kSolo];
     cudaStream_t up_stream[kUploaders] = {};
@@ -542,7 +546,7 @@ struct dgs_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_up, cv_done;
     std::deque<Request> queue;       // waiting for admission
-    std::deque<Request> to_upload;   // admitted, matrix not yet on the device
+    std::deque<Request> up_small, up_large;  // admitted, matrix not yet on the device
     std::deque<Uploaded> ready;      // on the device, waiting for a slot
     std::deque<Uploaded> solo_ready; // large requests on the device, waiting for the solo thread
     std::condition_variable cv_solo;
@@ -590,7 +594,8 @@ struct dgs_server {
         }
         pending.clear();
         queue.clear();
-        to_upload.clear();
+        up_small.clear();
+        up_large.clear();
     }
 
     void record_result(uint64_t ticket, Result&& res, size_t bytes) {  // caller holds mu
@@ -607,10 +612,12 @@ struct dgs_server {
             Request r;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                cv_up.wait(lk, [&] { return stop || !to_upload.empty(); });
-                if (to_upload.empty()) return;  // stopping
-                r = to_upload.front();
-                to_upload.pop_front();
+                const auto any = [&] { return !up_small.empty() || (u != 0 && !up_large.empty()); };
+                cv_up.wait(lk, [&] { return stop || any(); });
+                if (!any()) return;  // stopping
+                std::deque<Request>& q = up_small.empty() ? up_large : up_small;
+                r = q.front();
+                q.pop_front();
             }
             const int64_t t0 = now_ns();
             const bool solo_req = solo_request(r.n);
@@ -621,7 +628,9 @@ struct dgs_server {
                 Result res{};
                 res.status = DGS_ERR_OOM;
                 res.times.submit_ns = r.submit_ns;
-                res.times.admit_ns = res.times.done_ns = now_ns();
+                res.times.admit_ns = r.admit_ns;
+                res.times.upload_ns = t0;
+                res.times.done_ns = now_ns();
                 std::lock_guard<std::mutex> lk(mu);
                 if (solo_req) --solo_count;
                 else --reserved;
@@ -695,10 +704,10 @@ struct dgs_server {
                 return;
             }
             if (solo_req) {
-                solo_ready.push_back(Uploaded{r, mem, t0});
+                solo_ready.push_back(Uploaded{r, mem, t0, now_ns()});
                 cv_solo.notify_one();
             } else {
-                ready.push_back(Uploaded{r, mem, t0});
+                ready.push_back(Uploaded{r, mem, t0, now_ns()});
                 cv_work.notify_one();
             }
         }
@@ -729,6 +738,7 @@ struct dgs_server {
                 u = solo_ready.front();
                 solo_ready.pop_front();
             }
+            const int64_t start_ns = now_ns();
             const int32_t n = u.r.n;
             int32_t* out = solo_out(u.mem, n);
             dgs_options o;
@@ -757,7 +767,10 @@ struct dgs_server {
             res.status = st == DGS_OK ? outcome : st;
             if (st == DGS_OK && (outcome == DGS_OK || outcome == DGS_TIMEOUT)) res.sigma.assign(h_solo, h_solo + n);
             res.times.submit_ns = u.r.submit_ns;
-            res.times.admit_ns = u.admit_ns;
+            res.times.admit_ns = u.r.admit_ns;
+            res.times.upload_ns = u.upload_ns;
+            res.times.ready_ns = u.ready_ns;
+            res.times.start_ns = start_ns;
             res.times.done_ns = now_ns();
             cudaFreeAsync(u.mem, ss);
             {
@@ -781,14 +794,15 @@ struct dgs_server {
                 while (!stop && !queue.empty() &&
                        (solo_request(queue.front().n) || resident_count + reserved < eng.capacity()) &&
                        used + queue.front().bytes <= budget) {
-                    const Request r = queue.front();
+                    Request r = queue.front();
                     queue.pop_front();
+                    r.admit_ns = now_ns();
                     used += r.bytes;
                     if (solo_request(r.n)) ++solo_count;
                     else ++reserved;
                     pending[r.ticket] = 1;
-                    to_upload.push_back(r);
-                    cv_up.notify_one();
+                    (solo_request(r.n) ? up_large : up_small).push_back(r);
+                    cv_up.notify_all();
                 }
                 if (resident_count == 0 && ready.empty()) {
                     if (stop && reserved == 0) break;
@@ -855,8 +869,11 @@ struct dgs_server {
         R.n = u.r.n;
         R.bytes = u.r.bytes;
         R.mem = u.mem;
-        R.submit_ns = u.r.submit_ns;
-        R.admit_ns = u.admit_ns;
+        R.times.submit_ns = u.r.submit_ns;
+        R.times.admit_ns = u.r.admit_ns;
+        R.times.upload_ns = u.upload_ns;
+        R.times.ready_ns = u.ready_ns;
+        R.times.start_ns = now_ns();
         R.out = reinterpret_cast<int32_t*>(u.mem + carve_instance(nullptr, u.r.n, true, nullptr));
         const bool given = u.r.init == DGS_INIT_USER || u.r.init == DGS_INIT_RANDOM;
         eng.place(k, R.mem, R.n, true, nullptr, R.out, given ? DGS_INIT_USER : u.r.init, u.r.max_sweeps,
@@ -885,8 +902,7 @@ struct dgs_server {
                 B_CUDA(cudaStreamSynchronize(s), "read result");
                 res.sigma.assign(h_sigma, h_sigma + R.n);
             }
-            res.times.submit_ns = R.submit_ns;
-            res.times.admit_ns = R.admit_ns;
+            res.times = R.times;
             res.times.done_ns = now_ns();
             cudaFreeAsync(R.mem, s);
             eng.vacate(k);
@@ -1065,11 +1081,14 @@ void dgs_server_destroy(dgs_server* sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
         sv->queue.clear();
-        for (const auto& r : sv->to_upload) {  // admitted, never uploaded: dropped
-            sv->used -= r.bytes;
-            --sv->reserved;
+        for (auto* q : {&sv->up_small, &sv->up_large}) {  // admitted, never uploaded: dropped
+            for (const auto& r : *q) {
+                sv->used -= r.bytes;
+                if (solo_request(r.n)) --sv->solo_count;
+                else --sv->reserved;
+            }
+            q->clear();
         }
-        sv->to_upload.clear();
     }
     sv->cv_up.notify_all();
     sv->cv_work.notify_all();

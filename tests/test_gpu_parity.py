@@ -206,6 +206,32 @@ def test_sweep_cap_matches_oracle_prefix(cap):
     assert f == ref.objective and stats["sweeps"] == ref.sweeps
 
 
+def test_unwaited_solves_keep_their_host_outputs():
+    """Solves enqueued with wait=False and their Pending dropped at once: the
+    host memory their stream callbacks write (objective, stats) stays alive
+    until the stream gets there, and later results are right."""
+    import ctypes
+    import gc
+
+    a = _make("peer", 256, 3)
+    at = _cuda(a)
+    ref = oracle.dgs_parallel(a)
+    sig = torch.empty(256, dtype=torch.int32, device="cuda")
+    for k in range(120):
+        B.dgs_solve_ex(at, sigma_out=sig, wait=False, stats=(k % 2 == 0))
+        B.dgs_solve(at, sigma_out=sig, wait=False)
+        junk = [ctypes.c_int64(-1) for _ in range(64)]  # take over freed host memory
+        del junk
+        if k % 16 == 0:
+            gc.collect()
+    torch.cuda.synchronize()
+    st, tau, f, stats = B.dgs_solve_ex(at, wait=False).result()
+    assert st == B.DGS_OK and f == ref.objective and stats["sweeps"] == ref.sweeps
+    np.testing.assert_array_equal(tau.cpu().numpy(), ref.tau)
+    st, tau, f = B.dgs_solve(at, wait=False).result()
+    assert st == B.DGS_OK and f == ref.objective
+
+
 def test_errors():
     a = _make("uniform", 20, 0)
     bad = a.copy()
