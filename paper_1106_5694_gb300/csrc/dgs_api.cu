@@ -484,7 +484,7 @@ struct LoopCtx {
 struct LoopKey {
     unsigned char w[sizeof(Workspace)];
     unsigned char ctl[sizeof(CtlGlobal)];
-    int32_t rows, strip, tma, colour_pass;  // launch shapes and the knob the captured kernels bake in
+    int32_t rows, strip, tma, colour_pass, small_threads, pad;  // launch shapes and knobs the kernels bake in
 };
 
 LoopKey loop_key(const LoopCtx& c) {
@@ -497,6 +497,7 @@ LoopKey loop_key(const LoopCtx& c) {
     k.strip = sh.strip;
     k.tma = sh.tma;
     k.colour_pass = env_colour_pass();
+    k.small_threads = small_loop_threads();
     return k;
 }
 

@@ -500,6 +500,7 @@ cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
 // 2048; tests lower it so that compaction runs on small instances).
 int32_t env_compact_min();
 int32_t env_colour_pass();
+int32_t small_loop_threads();
 // DGS_EXACT_KEYS=1 disables the packed 32-bit keys of the evaluation kernel.
 int32_t env_exact_keys();
 
