@@ -191,6 +191,35 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()
 
 
+def row_task_roofline(stats, n: int, workload: str, peak: float, peak_src: str):
+    """The incremental re-evaluation of a committing sweep (row tasks: each
+    recomputed row j of G reads row sigma(j) of a and row j of its transpose,
+    8n bytes): bytes per update from this solve's counters, time per launch
+    from the committed launch list of the same workload
+    (profiles/solve_n<n>_<workload>_launches.md; ncu times, cold-cache and
+    serialised, so the fraction is a lower bound).  None without that list."""
+    path = os.path.join(ROOT, "profiles", f"solve_n{n}_{workload}_launches.md")
+    if not os.path.exists(path) or not stats.get("row_updates"):
+        return None
+    m = re.search(r"\|\s*`row_tasks_kernel[^`]*`\s*\|\s*(\d+)\s*\|\s*([\d.]+)\s*\|", open(path).read())
+    m_solves = re.search(r"^(\w+) solves", open(path).read(), re.M)
+    if not m:
+        return None
+    launches, total_us = int(m.group(1)), float(m.group(2))
+    solves = {"One": 1, "Two": 2, "Three": 3, "Four": 4}.get(m_solves.group(1), 1) if m_solves else 1
+    us_per_solve = total_us / solves
+    rows = stats["rows_recomputed"]
+    bytes_per_solve = 8 * n * rows
+    gbs = bytes_per_solve / (us_per_solve * 1e-6) / 1e9
+    return {"kernel": "row_tasks_kernel", "work": "incremental re-evaluation of the rows a commit changed",
+            "bound": "hbm", "updates_per_solve": stats["row_updates"], "rows_per_solve": rows,
+            "algorithmic_bytes_per_update": round(bytes_per_solve / stats["row_updates"]),
+            "us_per_update": round(us_per_solve / stats["row_updates"], 2), "achieved": round(gbs, 1),
+            "peak": round(peak, 1), "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": peak_src,
+            "time_source": f"ncu launch list {os.path.relpath(path, ROOT)} ({launches} launches over {solves} "
+                           "solves, cold-cache and serialised)"}
+
+
 def kernel_traffic(kernel: str, n: int, workload: str):
     """dram bytes per launch of `kernel` from its committed ncu summary
     (profiles/<kernel>_n<n>_<workload>.md), if that summary was taken on the
@@ -396,6 +425,8 @@ def run_ours(args):
         f"rows{c['rows_per_thread']}_strip{c['strip']}{'_tma' if c['tma'] else ''}": round(c["ms"], 4)
         for c in tuning.get("candidates", [])}
 
+    roofline_rows = row_task_roofline(stats, n, args.workload, peak, peak_src)
+
     # the row-owner (A-transpose) form of the same evaluation, on the same
     # instance: same result, 8n^2 bytes touched against 4n^2 algorithmic
     try:
@@ -473,7 +504,7 @@ def run_ours(args):
         "config": workload_config(args.workload, n, seed),
         "ms_median": round(statistics.median(step_ms), 4), "ms_best": round(min(step_ms), 4),
         "ms_call_to_return": round(statistics.mean(call_ms), 4),
-        "roofline": roofline, "roofline_evaluation": roofline_eval,
+        "roofline": roofline, "roofline_evaluation": roofline_eval, "roofline_row_tasks": roofline_rows,
         "roofline_evaluation_row_owner": roofline_row_owner, "cpu_baseline": cpu,
         "e2e": {"value": round(job_ms_per_solve(e2e, world), 3), "unit": "ms", "h2d_bytes_per_step": 4 * n * n,
                 "d2h_bytes_per_step": 4 * n},
@@ -541,7 +572,7 @@ def run_other_sizes(dev, peak, steps=3, cpu=False):
                 ok_p = bool(st_p == p["status"] and f_p == p["objective"] and stats_p["sweeps"] == p["sweeps"] and
                             sha(sig_p.cpu().numpy().astype(np.int32)) == p["tau_sha256"])
                 parity = ok_p if parity is None else (parity and ok_p)
-        ms, ev = [], []
+        ms, ev, call = [], [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for k in range(steps if n > 1000 else 20):
             flush.fill_(k)
@@ -549,13 +580,15 @@ def run_other_sizes(dev, peak, steps=3, cpu=False):
             st, sig, f2, stats = B.dgs_solve_ex(at, sigma_out=sig, profile=1)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            ms.append(e0.elapsed_time(e1))
+            ms.append(stats["solve_ms"])  # device time: first kernel to last (events in the solve)
+            call.append(e0.elapsed_time(e1))  # also the host's enqueue and the profile mode's waits
             ev.append(stats["evaluation_ms"])
         t_ev = statistics.mean(ev)
         alg = 4 * n * n + 24 * n
         row = {"workload": f"{kind.replace('uniform1000', 'uniform [0,1000)')} n={n}",
                "ms": round(statistics.mean(ms), 4), "ms_median": round(statistics.median(ms), 4),
-               "ms_best": round(min(ms), 4), "kernel_launches": stats["kernel_launches"],
+               "ms_best": round(min(ms), 4), "ms_call_to_result": round(statistics.mean(call), 4),
+               "kernel_launches": stats["kernel_launches"],
                "sweeps": stats["sweeps"], "sweeps_per_s": round(stats["sweeps"] / (statistics.mean(ms) * 1e-3), 1),
                "swaps_applied": stats["swaps_applied"], "objective": f2,
                "evaluation_ms": round(t_ev, 4),
@@ -957,11 +990,17 @@ def run_serving_fresh(dev):
 
 
 def torch_visible_index(dev):
-    """The physical index of local device `dev` as CUDA_VISIBLE_DEVICES names it."""
+    """The index of local device `dev` (a torch.device or an int) as
+    CUDA_VISIBLE_DEVICES names it."""
+    import torch
+
+    idx = dev.index if isinstance(dev, torch.device) else int(dev)
+    if idx is None:
+        idx = torch.cuda.current_device()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
-        return vis.split(",")[dev]
-    return dev
+        return vis.split(",")[idx]
+    return idx
 
 
 def main():
