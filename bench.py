@@ -99,8 +99,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []  # (perf_counter at arrival, line)
         self.reader = None
@@ -114,7 +115,7 @@ class ClockSampler:
 
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", str(self.period_ms),
                  "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -151,7 +152,7 @@ class ClockSampler:
         inside = [ln for t, ln in self.lines if b <= t <= e]
         after = [ln for t, ln in self.lines if t > e][:1]
         text = "".join(inside + after)
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in text.splitlines():
             parts = [x.strip() for x in line.split(",")]
@@ -162,10 +163,16 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                power.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "sm_mhz_min": min(sm) if sm else None,
+                "power_w_median": statistics.median(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
@@ -476,16 +483,21 @@ def run_ours(args):
     except Exception as exc:
         extra["sequential"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_batched:
+        # serving first: its latency tail is the measurement most sensitive to
+        # the device's state after long heavy runs (the other sizes' solves)
+        try:
+            extra["serving"] = run_serving_fresh(dev)
+        except Exception as exc:  # reported, never hides the main measurement
+            extra["serving"] = {"error": f"{type(exc).__name__}: {exc}"}
         try:
             extra["other_sizes"] = run_other_sizes(dev, measured_hbm_peak()[0],
                                                    cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         except Exception as exc:
             extra["other_sizes"] = {"error": f"{type(exc).__name__}: {exc}"}
-        for key, fn in (("batched", run_batched), ("serving", run_serving_fresh)):
-            try:
-                extra[key] = fn(dev)
-            except Exception as exc:  # reported, never hides the main measurement
-                extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            extra["batched"] = run_batched(dev)
+        except Exception as exc:
+            extra["batched"] = {"error": f"{type(exc).__name__}: {exc}"}
         b = extra.get("batched", {})
         if "_objs" in b:
             if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -851,6 +863,10 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
 
     import gc
 
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(vis) if vis.isdigit() else torch.cuda.current_device(), period_ms=500)
+    sampler.start()
+    t_runs = time.perf_counter()
     runs = []
     for frac in rates:
         for seed in seeds:
@@ -865,7 +881,10 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
                 gc.enable()
             runs.append({"rate_fraction_of_plain_capacity": frac, "rate_per_s": round(frac * capacity, 2),
                          "arrival_seed": seed, "served": served, "plain": plain})
+    sampler.mark(t_runs, time.perf_counter())
+    clocks = sampler.stop()
     return {
+        "clocks": clocks,
         "workload": f"{count} peer-shaped requests per run cycling over {distinct} seeded request buffers, n "
                     f"log-uniform in [{lo},{hi}], Poisson arrivals, pinned host-memory inputs, {budget >> 30} GB "
                     "admission budget; plain = one worker thread solving each request alone (dgs_solve_host), "

@@ -1489,14 +1489,12 @@ size_t controller_smem_bytes(int32_t n) {
 }
 
 // DGS_SMALL_LOOP_N: the largest n whose switching loop runs in one CTA
-// (small_loop_kernel); 0 turns it off.  Only with the default update policy
-// (the test knob that forces an update path keeps the grid kernels).
+// (small_loop_kernel); 0 turns it off (read on every call).  Only with the
+// default update policy (the test knob that forces an update path keeps the
+// grid kernels).
 int32_t small_loop_max_n() {
-    static const int32_t v = [] {
-        const char* e = std::getenv("DGS_SMALL_LOOP_N");
-        return e ? std::atoi(e) : 768;  // measured: faster up to n = 512, slower from n = 1024
-    }();
-    return v;
+    const char* e = std::getenv("DGS_SMALL_LOOP_N");
+    return e ? std::atoi(e) : 768;  // measured: faster up to n = 512, slower from n = 1024
 }
 
 bool use_small_loop(const Workspace& w) {
