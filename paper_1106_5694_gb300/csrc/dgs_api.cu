@@ -759,7 +759,12 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
         DGS_CUDA(launch_full_evaluation(S.w, 0, stream), "evaluation");
         S.launches += 1;
         if (o.profile) DGS_TRY(ev.end(stream));
-        if (use_small_loop(S.w)) {
+        // the single-CTA loop re-evaluates changed rows on one SM: fine after
+        // the greedy start (few exchanges per commit), not after a random or
+        // given start, whose commits change hundreds of rows (GEOM n = 512,
+        // random start: 5.2 ms in one CTA against 1.7 ms on the grid; n = 128:
+        // 0.52 against 0.78 ms)
+        if (use_small_loop(S.w) && (o.init == DGS_INIT_GREEDY || S.w.n <= 128)) {
             DGS_CUDA(launch_small_loop(S.w, S.ctl, stream), "switching loop");
             S.launches += 1;
         } else {
