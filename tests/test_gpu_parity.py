@@ -320,25 +320,26 @@ sys.path.insert(0, {root!r})
 from paper_1106_5694_gb300 import binding as B, inputs
 out = []
 for kind, n, seed in {cases!r}:
-    a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
+    a = inputs.peer_shaped(n, seed) if kind == "peer" else \
+        inputs.uniform(n, -(10**8), 10**8, seed) if kind == "wide" else inputs.uniform(n, 0, 1000, seed)
     st, sig, f, stats = B.dgs_solve_ex(torch.from_numpy(a).cuda(), evaluation={evaluation!r})
     out.append([st, f, stats["sweeps"], sig.cpu().tolist()])
 print(json.dumps(out))
 """
 
 
-def _run_knob_cases(env, evaluation=0):
+def _run_knob_cases(env, evaluation=0, cases=None):
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    cases = [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 640, 4)]
+    cases = cases or [("uniform", 300, 1), ("peer", 257, 2), ("uniform", 513, 3), ("peer", 640, 4)]
     code = _KNOB_SCRIPT.format(root=root, cases=cases, evaluation=evaluation)
     r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **env), capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr
     got = json.loads(r.stdout.strip().splitlines()[-1])
     for (kind, n, seed), (st, f, sweeps, tau) in zip(cases, got):
-        a = inputs.peer_shaped(n, seed) if kind == "peer" else inputs.uniform(n, 0, 1000, seed)
+        a = _make(kind, n, seed)
         ref = oracle.dgs_parallel(a)
         assert st == B.DGS_OK and f == ref.objective and sweeps == ref.sweeps
         assert tau == ref.tau.tolist()
@@ -373,6 +374,16 @@ def test_internal_paths_agree_with_oracle(env):
     it with other launch shapes (rows per thread, strip length, TMA gathers),
     must not change any result."""
     _run_knob_cases(env)
+
+
+@pytest.mark.parametrize("env", [{"DGS_SHORT_WRAPS": "1"}, {"DGS_SHORT_WRAPS": "1", "DGS_CTL_COMPACT_MIN": "1"},
+                                 {"DGS_SMALL_LOOP_THREADS": "256"}, {"DGS_SMALL_LOOP_THREADS": "1024"}])
+def test_colouring_passes_under_knobs_agree_with_oracle(env):
+    """Long quiet runs (wide-range values; the single-CTA loop at n = 700, the
+    graph loop at n = 1300) under reservation keys and claim stamps that wrap
+    every few rounds, compaction at every chance, or other widths of the
+    single-CTA loop: the oracle's results."""
+    _run_knob_cases(env, cases=[("wide", 700, 7), ("wide", 1300, 8)])
 
 
 # ------------------------- the row-owner (A-transpose) evaluation kernel
