@@ -314,6 +314,10 @@ __device__ __forceinline__ int32_t da_propose(const Workspace& w, int32_t i, boo
             // the four best jobs whose holders this agent beats
             ++scans;
             unsigned long long t[4] = {0ull, 0ull, 0ull, 0ull};
+            // the whole row is requested into L2 at once (prefetches hold no
+            // registers), so that the batches below wait for L2, not DRAM
+            for (int32_t c = gt * 32; c < n; c += 32 * kGroup)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + c));
             constexpr int kB = 2;  // 16-byte loads of the row (and 32 bytes of holder keys each) in flight
             for (int32_t c0 = gt * 4; c0 < n; c0 += 4 * kGroup * kB) {
                 int4 v[kB];
