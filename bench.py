@@ -791,6 +791,13 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
         ref_f.append(f)
     capacity = count / sum(svc[k % distinct] for k in range(count))
     torch.cuda.set_device(dev)
+    # the server's first pass, like the plain solver's above: its request
+    # memory (other sizes than a single solve's workspace) comes from the
+    # same pool, which then holds every size once
+    warm = B.Server(budget_bytes=budget)
+    for t in [warm.dgs_submit(a)[1] for a in bufs]:
+        warm.dgs_server_wait(t, timeout_us=600_000_000)
+    warm.dgs_server_destroy()
 
     def pct(x, q):
         return round(float(np.percentile(np.array(x) * 1e3, q)), 2)
