@@ -21,6 +21,12 @@
 #include "../../include/dgs.h"
 #include "dgs_internal.cuh"
 
+namespace dgs {
+// pass 1 over a band of tile rows (k_greedy.cu)
+cudaError_t launch_greedy_pass1_rows(const Workspace& w, int32_t cols, int32_t row_tile0, int32_t row_tile1,
+                                     cudaStream_t s);
+}  // namespace dgs
+
 
 namespace dgs {
 int32_t env_update_policy() {
@@ -85,6 +91,21 @@ cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
         pool = g_pools[dev];
     }
     return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// One copy stream per device for host-to-device bands (created once, kept for
+// the process; the stream is safe to share between calling threads).
+cudaStream_t copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (streams[dev] == nullptr && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
 }
 
 int32_t device_sms() {
@@ -585,9 +606,26 @@ dgs_status sequential_pass_body(void* p, cudaStream_t cs, unsigned long long h) 
 // The greedy start: pass 1, then deferred acceptance in one cooperative
 // launch; where that launch is refused, pass 1 again with the column keys and
 // the locally-dominant rounds as a device-side loop (the same assignment).
-dgs_status run_greedy(Solve& S, EventPair* timer) {
-    DGS_CUDA(launch_greedy_pass1_cols(S.w, 0, S.s), "greedy pass 1");
-    S.launches += 1;
+// A matrix that arrives in row bands (dgs_solve_host): event k is recorded
+// once rows [64 k tile_rows, 64 (k + 1) tile_rows) are on the device.
+struct HostBands {
+    const cudaEvent_t* ev;
+    int32_t count;
+    int32_t tile_rows;
+};
+
+dgs_status run_greedy(Solve& S, EventPair* timer, const HostBands* bands = nullptr) {
+    if (bands == nullptr) {
+        DGS_CUDA(launch_greedy_pass1_cols(S.w, 0, S.s), "greedy pass 1");
+        S.launches += 1;
+    } else {  // pass 1 of each band as soon as it has landed, while later ones are still copied
+        for (int32_t k = 0; k < bands->count; ++k) {
+            DGS_CUDA(cudaStreamWaitEvent(S.s, bands->ev[k], 0), "wait for a band of the matrix");
+            DGS_CUDA(launch_greedy_pass1_rows(S.w, 0, k * bands->tile_rows, (k + 1) * bands->tile_rows, S.s),
+                     "greedy pass 1");
+            S.launches += 1;
+        }
+    }
     if (timer) DGS_TRY(timer->begin(S.s));
     const cudaError_t pe = launch_greedy_da(S.w, S.s);
     if (pe == cudaSuccess) {
@@ -690,7 +728,8 @@ struct PinnedStart {
 // the caller launches around the solve (counted in the stats).
 dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int64_t* objective_out,
                       const dgs_options* opt, dgs_stats* stats, cudaStream_t stream,
-                      dgs_status* final_status = nullptr, int64_t extra_launches = 0) {
+                      dgs_status* final_status = nullptr, int64_t extra_launches = 0,
+                      const HostBands* bands = nullptr) {
     DGS_TRY(check_common(benefit, n));
     if (sigma_out == nullptr || objective_out == nullptr) return DGS_ERR_INVALID;
     dgs_options o;
@@ -714,6 +753,12 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     EventPair whole;
     if (o.profile) DGS_TRY(whole.begin(stream));
     Solve S(stream);
+    if (bands != nullptr &&
+        (o.init != DGS_INIT_GREEDY || n % 4 != 0 || (reinterpret_cast<uintptr_t>(benefit) % 16) != 0)) {
+        // the whole matrix first: the start, or the re-pitched copy, reads it before pass 1
+        DGS_CUDA(cudaStreamWaitEvent(stream, bands->ev[bands->count - 1], 0), "wait for the matrix");
+        bands = nullptr;
+    }
     DGS_TRY(S.setup(benefit, n, true));
     S.w.row_owner_eval = o.evaluation == DGS_EVAL_ROW_OWNER ? 1 : 0;
     // the random start is drawn on the host and enters as the caller's start
@@ -742,7 +787,7 @@ dgs_status solve_impl(const int32_t* benefit, int32_t n, int32_t* sigma_out, int
     }
     EventPair gev;
     if (o.init == DGS_INIT_GREEDY) {
-        DGS_TRY(run_greedy(S, o.profile ? &gev : nullptr));
+        DGS_TRY(run_greedy(S, o.profile ? &gev : nullptr, bands));
     } else {
         DGS_CUDA(launch_greedy_pass1(S.w, stream), "pass 1");  // transpose + range check
         S.launches += 1;
@@ -872,16 +917,52 @@ dgs_status dgs_solve_host(const int32_t* benefit_host, int32_t n, int32_t* sigma
     int32_t* a_dev = reinterpret_cast<int32_t*>(buf + obytes);
     int32_t* out_dev = reinterpret_cast<int32_t*>(buf);
     dgs_status st = DGS_OK, outcome = DGS_OK;
-    e = cudaMemcpyAsync(a_dev, benefit_host, abytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) st = cuda_fail(e, "copy benefit to device");
-    if (st == DGS_OK) st = solve_impl(a_dev, n, out_dev, objective_out, options, stats, s, &outcome);
+    // A large matrix from the greedy start is copied in row bands on a copy
+    // stream, and greedy pass 1 takes each band as it lands: the copy (bound
+    // by the host link) hides pass 1.
+    constexpr int32_t kBands = 8;
+    cudaEvent_t ev[kBands + 1] = {};
+    HostBands bands{ev + 1, 0, 0};
+    const bool greedy = options == nullptr || options->init == DGS_INIT_GREEDY;
+    cudaStream_t cs = (greedy && n % 4 == 0 && n >= 2048) ? copy_stream() : nullptr;
+    if (cs != nullptr) {
+        const int32_t tiles = (n + 63) / 64;
+        bands.tile_rows = (tiles + kBands - 1) / kBands;
+        bands.count = (tiles + bands.tile_rows - 1) / bands.tile_rows;
+        for (int32_t k = 0; k <= bands.count && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);  // the buffer exists in the caller's stream order
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+        for (int32_t k = 0; k < bands.count && e == cudaSuccess; ++k) {
+            const size_t r0 = (size_t)k * bands.tile_rows * 64;
+            const size_t r1 = std::min<size_t>((size_t)n, r0 + (size_t)bands.tile_rows * 64);
+            e = cudaMemcpyAsync(a_dev + r0 * n, benefit_host + r0 * n, (r1 - r0) * n * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + k], cs);
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "copy benefit to device");
+    } else {
+        e = cudaMemcpyAsync(a_dev, benefit_host, abytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy benefit to device");
+    }
+    if (st == DGS_OK)
+        st = solve_impl(a_dev, n, out_dev, objective_out, options, stats, s, &outcome, 0,
+                        cs != nullptr ? &bands : nullptr);
     if (st == DGS_OK) {
         e = cudaMemcpyAsync(sigma_out_host, out_dev, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy result to host");
     }
+    if (cs != nullptr) {
+        // the copy stream's bands precede the free (the caller's stream waited
+        // for all of them, or waits now if the solve failed to enqueue)
+        if (bands.count > 0 && ev[bands.count] != nullptr) cudaStreamWaitEvent(s, ev[bands.count], 0);
+        cudaStreamSynchronize(cs);
+    }
     cudaFreeAsync(buf, s);
     cudaStreamSynchronize(s);
+    for (cudaEvent_t x : ev)
+        if (x != nullptr) cudaEventDestroy(x);
     return st == DGS_OK ? outcome : st;
 }
 

@@ -116,9 +116,10 @@ __device__ __forceinline__ void greedy_pass1_body(const Workspace& w, int32_t ti
     }
 }
 
+// tiles tile0 .. tiles_total - 1 (row-major: a band of whole tile rows)
 __global__ void __launch_bounds__(256) greedy_pass1_kernel(Workspace w, int32_t tiles_x, int32_t tiles_total,
-                                                           int32_t cols) {
-    greedy_pass1_body(w, tiles_x, tiles_total, blockIdx.x, gridDim.x, nullptr, cols != 0);
+                                                           int32_t cols, int32_t tile0) {
+    greedy_pass1_body(w, tiles_x, tiles_total, tile0 + blockIdx.x, gridDim.x, nullptr, cols != 0);
 }
 
 // Match every mutually-best (agent, job) pair.
@@ -606,12 +607,21 @@ cudaError_t launch_range_check(const Workspace& w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_greedy_pass1_cols(const Workspace& w, int32_t cols, cudaStream_t s) {
+// Pass 1 over the rows of tile rows [row_tile0, row_tile1) (64 rows each):
+// the bands of a matrix that arrives in pieces can be processed as they land.
+cudaError_t launch_greedy_pass1_rows(const Workspace& w, int32_t cols, int32_t row_tile0, int32_t row_tile1,
+                                     cudaStream_t s) {
     const int32_t tx = (w.n + kT - 1) / kT;
-    const int32_t total = tx * tx;
-    const int32_t grid = total < dgs::device_sms() * 8 ? total : dgs::device_sms() * 8;
-    greedy_pass1_kernel<<<grid, 256, 0, s>>>(w, tx, total, cols);
+    const int32_t t0 = row_tile0 * tx, t1 = (row_tile1 < tx ? row_tile1 : tx) * tx;
+    const int32_t count = t1 - t0;
+    if (count <= 0) return cudaSuccess;
+    const int32_t grid = count < dgs::device_sms() * 8 ? count : dgs::device_sms() * 8;
+    greedy_pass1_kernel<<<grid, 256, 0, s>>>(w, tx, t1, cols, t0);
     return cudaGetLastError();
+}
+
+cudaError_t launch_greedy_pass1_cols(const Workspace& w, int32_t cols, cudaStream_t s) {
+    return launch_greedy_pass1_rows(w, cols, 0, (w.n + kT - 1) / kT, s);
 }
 
 cudaError_t launch_greedy_pass1(const Workspace& w, cudaStream_t s) { return launch_greedy_pass1_cols(w, 1, s); }

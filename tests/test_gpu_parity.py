@@ -272,6 +272,22 @@ def test_host_entry_point_matches_device():
     assert f_h == f_d
 
 
+@pytest.mark.parametrize("kind,n,init", [("peer", 2048, "greedy"), ("uniform", 2500, "greedy"),
+                                         ("peer", 2052, "greedy"), ("peer", 2050, "greedy"),
+                                         ("uniform", 2100, "random"), ("ties", 4096, "greedy")])
+def test_host_entry_point_in_bands_matches_device(kind, n, init):
+    """dgs_solve_host copies a large matrix in row bands on a copy stream and
+    starts greedy pass 1 on each band as it lands (n a multiple of 4, greedy
+    start; otherwise one copy): the result equals the device-resident solve."""
+    a = _make(kind, n, 5)
+    opts = {} if init == "greedy" else {"init": B.DGS_INIT_RANDOM, "seed": 7}
+    st_h, sig_h, f_h, stats_h = B.dgs_solve_host(a, **opts)
+    st_d, sig_d, f_d, stats_d = B.dgs_solve_ex(_cuda(a), **opts)
+    assert st_h == st_d == B.DGS_OK
+    np.testing.assert_array_equal(sig_h, sig_d.cpu().numpy())
+    assert f_h == f_d and stats_h["sweeps"] == stats_d["sweeps"]
+
+
 def test_deterministic_repeat():
     a = _make("uniform", 700, 11)
     outs = [B.dgs_solve(_cuda(a)) for _ in range(3)]
