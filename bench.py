@@ -865,7 +865,7 @@ def run_serving(dev, count=512, lo=256, hi=16384, budget=40 << 30, rates=(0.7, 1
         info = srv.dgs_server_get_info()[1]
         srv.dgs_server_destroy()
         span = (last_done - first_submit) / 1e9
-        rows.sort()
+        rows.sort(key=lambda r: r[0])  # by latency (ties: any order)
         p99 = rows[min(len(rows) - 1, int(0.99 * len(rows)))]
         return {"solves_per_s": round(count / span, 2), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                 "upload_ms_per_request": round(info["upload_ms"] / count, 3),
