@@ -350,9 +350,9 @@ __device__ __forceinline__ int32_t colour_pass_rounds(const Workspace& w, EdgeT*
 // span: reservation-key period (power of two <= kRoundSpanMax); stamp_wrap:
 // claim-stamp period (<= 255).  Both are shortened only by a test knob.
 // list_cap: entries of the accepted list held in shared memory.
-// colour_pass: runs of quiet sweeps go through colouring passes (shared-
-// memory mode 2 only); 0 turns them off.
-template <typename EdgeT, int kT = kCtlThreads>
+// colour_pass: runs of quiet sweeps go through colouring passes (only
+// while the edges are in shared memory); 0 turns them off.
+template <typename EdgeT, int kT = kCtlThreads, bool kEdgesToShared = true>
 __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem_mode, const CtlScratch& g,
                                                 uint32_t span, uint32_t stamp_wrap, int32_t list_cap,
                                                 int32_t compact_min, int32_t colour_pass) {
@@ -396,6 +396,22 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         off += (size_t)n;
         estate = smem_raw + off;
     }
+    // Mode 1 keeps the edge array in global memory, but a list of at most
+    // edges_s_cap() (about n / 2) positions fits in the upper half of slot_s
+    // (positions below n use only its lower half): a launch whose list is
+    // that short, or is compacted to that length, moves its edges there.
+    // kEdgesToShared = false (the batched controller, which otherwise spills
+    // more registers, and the single-CTA loop, which runs in mode 2 only)
+    // leaves them in global memory.
+    const bool es_mode = kEdgesToShared && smem_mode == 1 && sizeof(EdgeT) == 4;
+    auto edges_s = [&]() -> EdgeT* {
+        return reinterpret_cast<EdgeT*>((reinterpret_cast<uintptr_t>(slot_s + n) + 3u) & ~static_cast<uintptr_t>(3u));
+    };
+    auto edges_s_cap = [&]() -> int32_t {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(edges_s());
+        const uintptr_t hi = reinterpret_cast<uintptr_t>(slot_s + 2 * (size_t)n);
+        return hi > lo ? (int32_t)((hi - lo) / sizeof(EdgeT)) : 0;
+    };
     const int32_t cap = lists_s ? list_cap : 0;
     TwoTier accl{lists_s, cap, g.acc_g};
     unsigned long long* pt = (tid == 0) ? w.phase_ns : nullptr;
@@ -464,6 +480,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             if (lane == 31) warp_sums[32] = incl;
         }
         __syncthreads();
+        if (es_mode && warp_sums[32] <= edges_s_cap()) E = edges_s();  // the whole list fits in shared memory
         int32_t pos0 = warp_sums[wp];
         const uint32_t below = (1u << lane) - 1u;
         for (int32_t cb = c_lo; cb < c_hi; cb += 32) {
@@ -540,6 +557,11 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         // order), so that later sweeps scan live edges only; the reservation
         // keys restart with the new positions.
         if (s_live * 2 < L && L >= compact_min) {
+            // (mode 1: into shared memory when the live edges fit there)
+            const int32_t es_cap = es_mode ? edges_s_cap() : 0;
+            const bool to_s = es_mode && E != edges_s();  // edges still in global memory
+            EdgeT* const Ed = (to_s && s_live <= es_cap) ? edges_s() : E;
+            const bool bounded = es_mode && Ed == edges_s();
             int32_t base = 0;
             for (int32_t c0 = 0; c0 < L; c0 += kT) {
                 const int32_t p = c0 + tid;
@@ -550,7 +572,7 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
                 int32_t total;
                 const int32_t pos = base + block_scan<kT>(alive ? 1 : 0, warp_sums, &total);  // every read is done
                 if (alive) {
-                    E[pos] = e;
+                    if (!bounded || pos < es_cap) Ed[pos] = e;
                     estate[pos] = es;
                     w.ctl_slot[pos] = slot;
                     if (slot_s) slot_s[pos] = (uint16_t)slot;
@@ -562,9 +584,16 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
             if (tid == 0) {
                 s_L = base;
                 s_round = 0u;
+                if (bounded && base > es_cap) {  // the live count disagreed with the list
+                    st->error = kErrInternal;
+                    st->status = kError;
+                    s_stop = 1;
+                }
             }
             __syncthreads();
+            if (s_stop) break;
             L = s_L;
+            E = Ed;
         }
         if (s_stamp >= stamp_wrap) {  // claim stamps wrap: clear them once
             for (int32_t i = tid; i < n; i += kT) claimed[i] = 0;
@@ -580,9 +609,10 @@ __device__ __forceinline__ void controller_body(const Workspace& w, int32_t smem
         // Colouring pass (after a quiet sweep; see colour_pass_rounds).  It
         // runs F >= 1 sweeps at once, or none when an applicable edge is
         // accepted in this very sweep; then this sweep goes on as usual.
-        // (mode 2 holds n <= 32767, so only 32-bit edges take this path)
+        // (modes 1 and 2 hold n <= 32767, so only 32-bit edges take this path)
         // (short lists: a pass costs more than the sweeps it saves)
-        if (sizeof(EdgeT) == 4 && colour_pass && smem_mode == 2 && s_pass_ok && L > kColourMinList) {
+        if (sizeof(EdgeT) == 4 && colour_pass && (smem_mode == 2 || (es_mode && E == edges_s())) && s_pass_ok &&
+            L > kColourMinList) {
             const int32_t F = colour_pass_rounds<EdgeT, kT>(w, E, estate, slot_s, res, claimed, L, span, s_round, s_pE,
                                                         s_pR, s_pF, s_hist, s_max_sweeps, s_sweeps, s_live,
                                                         pt ? s_pt : nullptr);
@@ -1141,7 +1171,7 @@ __global__ void __launch_bounds__(kT, 1) small_loop_kernel(Workspace w, int32_t 
         __syncthreads();
         prepare_edges_body(w, 0, 1);
         __syncthreads();
-        controller_body<EdgeT, kT>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min, colour_pass);
+        controller_body<EdgeT, kT, false>(w, smem_mode, g, span, stamp_wrap, list_cap, compact_min, colour_pass);
         if (tid == 0) {
             const int32_t it = ++st->loop_iterations;
             if (st->status == kRunning && it > 16 * n + 4096) {
@@ -1419,7 +1449,8 @@ __global__ void __launch_bounds__(kCtlThreads, 1) controller_batched_kernel(Batc
                                                                            int32_t colour_pass) {
     for_each_entry(t, kStageSwitch, [&](const Instance& in, int32_t, int32_t) {
         const CtlScratch c{in.ctl.res, in.ctl.claimed, in.ctl.estate, in.ctl.edges, in.ctl.acc};
-        controller_body<uint32_t>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min, colour_pass);
+        controller_body<uint32_t, kCtlThreads, false>(in.w, in.ctl_mode, c, span, stamp_wrap, in.ctl_cap, compact_min,
+                                                      colour_pass);
     });
 }
 

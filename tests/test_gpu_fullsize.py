@@ -68,3 +68,39 @@ def test_fullsize_solve_equals_stored_oracle_result(w):
     assert stats["sweeps"] == w["sweeps"]
     assert stats["swaps_applied"] == w["swaps_applied"]
     assert _sha(sig.cpu().numpy().astype(np.int32)) == w["tau_sha256"]
+
+
+_MODE1_SCRIPT = r"""
+import sys, json, hashlib, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1106_5694_gb300 import binding as B, inputs
+a = inputs.uniform({n}, 0, 10**6, 0)
+st, sig, f, stats = B.dgs_solve_ex(torch.from_numpy(a).cuda())
+s = hashlib.sha256(np.ascontiguousarray(sig.cpu().numpy().astype(np.int32)).tobytes()).hexdigest()
+print(json.dumps([st, f, stats["sweeps"], stats["swaps_applied"], s]))
+"""
+
+
+@pytest.mark.parametrize("name", ["uniform_n4096_seed0", "uniform_n10000_seed0"])
+def test_controller_edges_in_global_memory_equal_stored_oracle_result(name):
+    """The controller with its edge array in global memory (DGS_CTL_MODE=1,
+    the placement every n above about 12100 gets), which moves a list short
+    enough into shared memory and then also runs colouring passes over it:
+    the oracle's complete result on the uniform workloads, and at n = 10000
+    the phase counters show that passes ran."""
+    import re
+    import subprocess
+    import sys
+    w = {x["name"]: x for x in _workloads()}[name]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DGS_CTL_MODE="1", DGS_PHASE_TIMERS="1")
+    r = subprocess.run([sys.executable, "-c", _MODE1_SCRIPT.format(root=root, n=w["n"])], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    st, f, sweeps, swaps, sha = json.loads(r.stdout.strip().splitlines()[-1])
+    assert st == B.DGS_OK
+    assert (f, sweeps, swaps, sha) == (w["objective"], w["sweeps"], w["swaps_applied"], w["tau_sha256"])
+    m = re.search(r"colouring passes (\d+)", r.stderr)
+    assert m is not None, r.stderr
+    if w["n"] == 10000:
+        assert int(m.group(1)) > 0

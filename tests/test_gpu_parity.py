@@ -381,7 +381,9 @@ def _run_knob_cases(env, evaluation=0, cases=None):
                                   "DGS_UPDATE_POLICY": "1"},
                                  {"DGS_EVAL_ROWS": "16", "DGS_EVAL_STRIP": "32"},
                                  {"DGS_CTL_COMPACT_MIN": "1"}, {"DGS_CTL_COMPACT_MIN": "1", "DGS_CTL_MODE": "0"},
-                                 {"DGS_CTL_COMPACT_MIN": "1", "DGS_SHORT_WRAPS": "1"}])
+                                 {"DGS_CTL_COMPACT_MIN": "1", "DGS_SHORT_WRAPS": "1"},
+                                 {"DGS_CTL_COMPACT_MIN": "1", "DGS_CTL_MODE": "1"},
+                                 {"DGS_CTL_COMPACT_MIN": "1", "DGS_CTL_MODE": "1", "DGS_SHORT_WRAPS": "1"}])
 def test_internal_paths_agree_with_oracle(env):
     """Forcing the full-evaluation or row-task update path, placing the
     controller's scratch in global memory, making its reservation keys and
@@ -393,7 +395,8 @@ def test_internal_paths_agree_with_oracle(env):
 
 
 @pytest.mark.parametrize("env", [{"DGS_SHORT_WRAPS": "1"}, {"DGS_SHORT_WRAPS": "1", "DGS_CTL_COMPACT_MIN": "1"},
-                                 {"DGS_SMALL_LOOP_THREADS": "256"}, {"DGS_SMALL_LOOP_THREADS": "1024"}])
+                                 {"DGS_SMALL_LOOP_THREADS": "256"}, {"DGS_SMALL_LOOP_THREADS": "1024"},
+                                 {"DGS_CTL_MODE": "1"}, {"DGS_CTL_MODE": "1", "DGS_CTL_COMPACT_MIN": "1"}])
 def test_colouring_passes_under_knobs_agree_with_oracle(env):
     """Long quiet runs (wide-range values; the single-CTA loop at n = 700, the
     graph loop at n = 1300) under reservation keys and claim stamps that wrap
