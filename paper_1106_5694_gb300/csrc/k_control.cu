@@ -1491,9 +1491,9 @@ __global__ void advance_batched_kernel(BatchTable t, int32_t from_stage) {
 
 // Controller scratch placement.  Mode 2: reservations, 32-bit edges, list
 // heads, claims and edge states in shared memory; mode 1: edges in global
-// memory (the single-graph controller moves a list of up to about n / 2
-// positions into the spare half of the slot array); mode 0: everything in
-// global memory.
+// memory (the controller kernel of a single solve moves a list of up to
+// about n / 2 positions into the spare half of the slot array); mode 0:
+// everything in global memory.
 constexpr size_t kCtlSmemLimit = 227 * 1024 - 1024;
 
 static size_t ctl_fixed_bytes(int32_t n, int32_t mode) {
